@@ -1,0 +1,217 @@
+"""Seeded synthetic inputs: the benchmark distributions of Sec. 6 of Axtmann et
+al. (Uniform, Exponential, RootDup, TwoDup, EightDup, AlmostSorted, Zipf,
+Sorted, ReverseSorted, Zero) for the element types of the same section.
+
+This module holds none of the sorting method's arithmetic; it only makes
+inputs.  It is written with plain torch integer ops so the same code runs on
+the CPU (tests, oracle inputs) and on the GPU (large benchmark inputs) and
+yields identical bits on both.
+
+Random numbers come from splitmix64 (Steele, Lea and Flood, OOPSLA 2014) used
+as a counter-based generator: draw i of stream s is the (i+1)-th output of a
+splitmix64 sequence whose state starts at ``seed ^ stream_constant(s)``.
+
+Storage formats (what the GPU library and ``to_numpy`` see):
+  u32 -> torch.int32 (n,)   bit pattern of the unsigned value
+  u64 -> torch.int64 (n,)   bit pattern of the unsigned value
+  f64 -> torch.float64 (n,)
+  pair -> torch.int64 (n, 2): key, value
+  rec100 -> torch.uint8 (n, 100): 10-byte key, 90-byte payload
+"""
+import math
+
+import numpy as np
+import torch
+
+DEFAULT_SEED = 0x1B54A32D192ED03
+GOLDEN = 0x9E3779B97F4A7C15
+MIX1 = 0xBF58476D1CE4E5B9
+MIX2 = 0x94D049BB133111EB
+
+INT_DISTS = ("uniform", "exponential", "rootdup", "twodup", "eightdup",
+             "almostsorted", "zipf", "sorted", "reversesorted", "zero")
+F64_DISTS = ("uniform", "normal")
+REC_DISTS = ("uniform", "rootdup")
+ELEM_BYTES = {"u32": 4, "u64": 8, "f64": 8, "pair": 16, "rec100": 100}
+
+
+def _s64(x):
+    """Python int (mod 2^64) -> signed int64 value with the same bits."""
+    x &= (1 << 64) - 1
+    return x - (1 << 64) if x >= (1 << 63) else x
+
+
+def _lsr(z, s):
+    """Logical right shift of int64 bit patterns."""
+    return (z >> s) & ((1 << (64 - s)) - 1)
+
+
+def splitmix64(idx, seed):
+    """Counter-based splitmix64: output number idx (0-based) of the stream
+    whose state starts at ``seed``.  idx is an int64 tensor; returns int64
+    bit patterns."""
+    z = idx * _s64(GOLDEN) + _s64(seed + GOLDEN)
+    z = (z ^ _lsr(z, 30)) * _s64(MIX1)
+    z = (z ^ _lsr(z, 27)) * _s64(MIX2)
+    return z ^ _lsr(z, 31)
+
+
+def splitmix64_py(i, seed):
+    """Pure-Python splitmix64 (same definition), for checking the tensor one."""
+    m = (1 << 64) - 1
+    z = (seed + (i + 1) * GOLDEN) & m
+    z = ((z ^ (z >> 30)) * MIX1) & m
+    z = ((z ^ (z >> 27)) * MIX2) & m
+    return z ^ (z >> 31)
+
+
+def _stream(seed, s):
+    return (seed ^ (s * 0xD1B54A32D192ED03)) & ((1 << 64) - 1)
+
+
+def _draw(n, seed, stream, device):
+    idx = torch.arange(n, dtype=torch.int64, device=device)
+    return splitmix64(idx, _stream(seed, stream))
+
+
+def _umod(x, n):
+    """Unsigned (x mod 2^64) mod n for int64 bit patterns, 0 < n < 2^62."""
+    if n & (n - 1) == 0:
+        return x & (n - 1)
+    hi = _lsr(x, 1) % n
+    return (hi * 2 + (x & 1)) % n
+
+
+def _zipf_cdf(nvals=1_000_000, s=0.75):
+    w = np.arange(1, nvals + 1, dtype=np.float64) ** (-s)
+    c = np.cumsum(w)
+    return c / c[-1]
+
+
+def _int_values(dist, n, width, seed, device):
+    """Values of an integer distribution as int64 tensors in [0, 2^width)."""
+    top = 1 << width
+    i = torch.arange(n, dtype=torch.int64, device=device)
+    if dist == "uniform":
+        r = _draw(n, seed, 1, device)
+        return r if width == 64 else _lsr(r, 64 - width)
+    if dist == "exponential":
+        # pick e uniform in [0, log2 n), value uniform in [2^e, 2^(e+1))
+        lg = max(1, int(math.floor(math.log2(max(n, 2)))))
+        e = _umod(_draw(n, seed, 2, device), lg)
+        r = _lsr(_draw(n, seed, 3, device), 1)
+        return (torch.ones_like(e) << e) + (r & ((torch.ones_like(e) << e) - 1))
+    if dist == "rootdup":
+        return i % max(1, math.isqrt(n))
+    if dist == "twodup":
+        return _umod(i * i + n // 2, n)
+    if dist == "eightdup":
+        x = i * i
+        x = x * x
+        x = x * x
+        return _umod(x + n // 2, n)
+    if dist == "almostsorted":
+        a = i.clone()
+        swaps = math.isqrt(n)
+        if n >= 2 and swaps > 0:
+            p = _umod(_draw(swaps, seed, 4, "cpu"), n - 1).tolist()
+            cur = {}
+            for q in p:  # adjacent swaps applied in sequence
+                x, y = cur.get(q, q), cur.get(q + 1, q + 1)
+                cur[q], cur[q + 1] = y, x
+            pos = torch.tensor(list(cur.keys()), dtype=torch.int64)
+            val = torch.tensor(list(cur.values()), dtype=torch.int64)
+            a[pos.to(device)] = val.to(device)
+        return a
+    if dist == "zipf":
+        cdf = torch.from_numpy(_zipf_cdf()).to(device)
+        u = _lsr(_draw(n, seed, 5, device), 11).to(torch.float64) * 2.0 ** -53
+        v = torch.searchsorted(cdf, u, right=True) + 1
+        return torch.clamp(v, max=cdf.numel())
+    if dist in ("sorted", "reversesorted"):
+        # sorted uniform input, stratified: value i lies in [i*w, (i+1)*w)
+        w = min(max(1, top // max(n, 1)), 1 << 62)
+        r = _draw(n, seed, 6, device)
+        v = i * w + _umod(r, w) if w > 1 else i
+        return v if dist == "sorted" else v.flip(0)
+    if dist == "zero":
+        return torch.zeros(n, dtype=torch.int64, device=device)
+    raise ValueError("unknown distribution %r" % dist)
+
+
+def generate(dist, dtype, n, seed=DEFAULT_SEED, device="cpu"):
+    """Return a seeded synthetic input in the storage format above."""
+    if dtype == "u64":
+        return _int_values(dist, n, 64, seed, device)
+    if dtype == "u32":
+        v = _int_values(dist, n, 32, seed, device)
+        return (v - ((v >> 31) & 1) * (1 << 32)).to(torch.int32)
+    if dtype == "f64":
+        if dist == "uniform":
+            r = _draw(n, seed, 7, device)
+            return _lsr(r, 11).to(torch.float64) * 2.0 ** -53
+        if dist == "normal":  # Box-Muller
+            u1 = (_lsr(_draw(n, seed, 8, device), 11) + 1).to(torch.float64) * 2.0 ** -53
+            u2 = _lsr(_draw(n, seed, 9, device), 11).to(torch.float64) * 2.0 ** -53
+            return torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)
+        raise ValueError("f64 distributions: %s" % (F64_DISTS,))
+    if dtype == "pair":
+        k = _int_values(dist, n, 64, seed, device)
+        v = torch.arange(n, dtype=torch.int64, device=device)
+        return torch.stack([k, v], dim=1).contiguous()
+    if dtype == "rec100":
+        out = torch.empty((n, 100), dtype=torch.uint8, device=device)
+        if dist == "uniform":
+            hi = _draw(n, seed, 10, device)
+            lo = _draw(n, seed, 11, device)
+        elif dist == "rootdup":
+            # key = 80-bit big-endian value (i mod 2^14): 2 zero bytes + u64
+            hi = torch.arange(n, dtype=torch.int64, device=device) % (1 << 14)
+            lo = None
+        else:
+            raise ValueError("rec100 distributions: %s" % (REC_DISTS,))
+        if lo is None:
+            out[:, 0:2] = 0
+            for b in range(8):
+                out[:, 2 + b] = (_lsr(hi, 8 * (7 - b)) & 0xFF).to(torch.uint8)
+        else:
+            for b in range(8):
+                out[:, b] = (_lsr(hi, 8 * (7 - b)) & 0xFF).to(torch.uint8)
+            out[:, 8] = (_lsr(lo, 56) & 0xFF).to(torch.uint8)
+            out[:, 9] = (_lsr(lo, 48) & 0xFF).to(torch.uint8)
+        idx = torch.arange(n, dtype=torch.int64, device=device)
+        for b in range(8):  # payload bytes 10..17: original index
+            out[:, 10 + b] = (_lsr(idx, 8 * b) & 0xFF).to(torch.uint8)
+        for w in range(11):  # payload bytes 18..99: seeded filler
+            r = _draw(n, seed, 20 + w, device)
+            for b in range(8):
+                j = 18 + 8 * w + b
+                if j < 100:
+                    out[:, j] = (_lsr(r, 8 * b) & 0xFF).to(torch.uint8)
+        return out
+    raise ValueError("unknown dtype %r" % dtype)
+
+
+def to_numpy(t, dtype):
+    """Storage tensor -> numpy array in the oracle's conventions."""
+    a = t.detach().cpu().contiguous().numpy()
+    if dtype == "u32":
+        return a.view(np.uint32)
+    if dtype in ("u64", "pair"):
+        return a.view(np.uint64)
+    return a
+
+
+def from_numpy(a, dtype, device="cpu"):
+    """numpy array in the oracle's conventions -> storage tensor."""
+    a = np.ascontiguousarray(a)
+    if dtype == "u32":
+        a = a.view(np.int32)
+    elif dtype in ("u64", "pair"):
+        a = a.view(np.int64)
+    return torch.from_numpy(a.copy()).to(device)
+
+
+def count(t, dtype):
+    """Number of elements of a storage tensor."""
+    return t.shape[0]
