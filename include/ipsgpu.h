@@ -1,0 +1,181 @@
+/*
+ * ipsgpu.h -- C ABI of the GB300 (sm_103a) in-place samplesort library.
+ *
+ * The library sorts arrays that already live in device memory, in place,
+ * following the in-place parallel super scalar samplesort (IPS4o) and its
+ * radix variant (IPS2Ra) of Axtmann, Witt, Ferizovic and Sanders,
+ * "Engineering In-place (Shared-memory) Sorting Algorithms":
+ *   problem statement        Sec. 2 (sort A[0..n-1] in place by '<')
+ *   partitioning step        Sec. 3.1 (sampling, classification into
+ *                            b-element buffer blocks, block permutation with
+ *                            per-bucket read/write pointers, cleanup)
+ *   recursion and base case  Sec. 3.2, Sec. 5
+ *   radix variant            Sec. 5 (IPS2Ra: radix extractor on unsigned keys)
+ *   sorter object            Sec. 6.6 (setup separated from sorting)
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are DEVICE pointers of the current CUDA device; the
+ *     caller owns them.  Data arrays must be aligned to their element size
+ *     (4 bytes for rec100) and must not be accessed by other work while a
+ *     call on them is in flight.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous with respect to the host unless a
+ *     function says it synchronizes.  ipsgpu_sort synchronizes `stream`
+ *     once per recursion level (it reads bucket boundaries back to plan the
+ *     next level) and returns after the last kernel has been enqueued.
+ *   - Return values are status codes (IPSGPU_OK = 0).  Errors detected by
+ *     kernels (a bounded wait that ran out, an inconsistent count) are kept
+ *     in a device status word of the sorter and reported by ipsgpu_status.
+ *   - A sorter may be used by one host thread at a time.
+ */
+#ifndef IPSGPU_H
+#define IPSGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Element types (Sec. 6 "data types").  Key order:
+ *   U32, U64   numeric
+ *   F64        IEEE-754 bits b mapped to (b>>63) ? ~b : b|2^63, compared as
+ *              unsigned; this is '<' on non-NaN values with -0.0 before +0.0
+ *   PAIR_U64   16 bytes {u64 key, u64 value}; key only
+ *   REC100     100 bytes; the first 10 bytes compared lexicographically as
+ *              unsigned bytes; 90 bytes of payload                          */
+typedef enum {
+    IPSGPU_U32 = 0,
+    IPSGPU_U64 = 1,
+    IPSGPU_F64 = 2,
+    IPSGPU_PAIR_U64 = 3,
+    IPSGPU_REC100 = 4
+} ipsgpu_dtype;
+
+/* Classifier of the partitioning step: the branchless splitter tree of IPS4o
+ * (Sec. 2, Algorithm 1) or the radix extractor of IPS2Ra (Sec. 5; U32, U64
+ * and PAIR_U64 keys only). */
+typedef enum { IPSGPU_SAMPLESORT = 0, IPSGPU_RADIX = 1 } ipsgpu_algo;
+
+enum {
+    IPSGPU_OK = 0,
+    IPSGPU_E_INVAL = 1,       /* bad argument (NULL, misaligned, too large)   */
+    IPSGPU_E_UNSUPPORTED = 2, /* dtype/algorithm combination not supported    */
+    IPSGPU_E_NOMEM = 3,       /* device or pinned host allocation failed      */
+    IPSGPU_E_CUDA = 4,        /* a CUDA runtime call failed                   */
+    IPSGPU_E_TIMEOUT = 5,     /* a bounded device wait gave up                */
+    IPSGPU_E_BUSY = 6,        /* server: request cannot be admitted now       */
+    IPSGPU_E_INTERNAL = 7     /* a kernel found an inconsistent count         */
+};
+
+/* Tuning parameters; a zero field takes its default.
+ *   k                 max buckets per level incl. equality buckets (256,
+ *                     Sec. 5; power of two in [4, 256])
+ *   block_bytes       bytes per block (512; the paper's 2 KiB shrinks so that
+ *                     k buffer blocks fit in one SM's shared memory)
+ *   alpha_scale       oversampling alpha = alpha_scale * log2(n') (0.2, Sec. 5)
+ *   base_case         largest segment sorted by the shared-memory base case
+ *                     (elements; default: as many as fit, 24576 for 8-byte
+ *                     elements)
+ *   seed              seed of the sampling generator (splitmix64)
+ *   algo              ipsgpu_algo
+ *   spin_limit        iterations of a bounded device wait before it gives up
+ *                     with IPSGPU_E_TIMEOUT (default 1<<22, ~0.5 s)
+ *   arena_bytes       device scratch for leftover buffer blocks and cleanup
+ *                     staging (default 256 MiB)                            */
+typedef struct {
+    uint32_t k;
+    uint32_t block_bytes;
+    float alpha_scale;
+    uint32_t base_case;
+    uint64_t seed;
+    int32_t algo;
+    uint32_t spin_limit;
+    uint64_t arena_bytes;
+} ipsgpu_params;
+
+typedef struct ipsgpu_sorter ipsgpu_sorter;
+
+/* Create a sorter for one element type (the "sorter object" of Sec. 6.6).
+ * Allocates every piece of device scratch the sorter will ever use; the
+ * amount depends on the parameters only, never on n (see
+ * ipsgpu_scratch_bytes).  params may be NULL (all defaults).  The sorter is
+ * bound to the CUDA device current at creation.
+ * Errors: E_INVAL (bad params, out NULL), E_UNSUPPORTED (RADIX with F64 or
+ * REC100), E_NOMEM, E_CUDA. */
+int ipsgpu_sorter_create(const ipsgpu_params *params, int dtype, ipsgpu_sorter **out);
+
+/* Free a sorter and its scratch (synchronizes the device first). */
+int ipsgpu_sorter_destroy(ipsgpu_sorter *s);
+
+/* Device scratch bytes a sorter with these parameters allocates: a constant
+ * times k * block_bytes per stripe/segment slot, independent of n. */
+uint64_t ipsgpu_scratch_bytes(const ipsgpu_params *params, int dtype);
+
+/* Sort d_data[0..n) in place, ascending in the key order of the sorter's
+ * dtype (Sec. 2 problem statement; Sec. 3 and 5).  Detects non-decreasing
+ * inputs (returns) and non-increasing ones (reverses them) first (Sec. 5).
+ * For U32/U64/F64 the result is the unique sorted sequence; for PAIR_U64
+ * and REC100 records with equal keys may appear in any order.
+ * Errors: E_INVAL, E_CUDA; kernel-side errors via ipsgpu_status. */
+int ipsgpu_sort(ipsgpu_sorter *s, void *d_data, uint64_t n, void *stream);
+
+/* One partitioning step with given splitters (Sec. 3.1.2 - 3.1.4): classify
+ * every element with the branchless tree over the sorted splitters
+ * d_splitters[0..num_splitters) (elements of the sorter's dtype, only their
+ * keys are read), then move the elements in place so that bucket j occupies
+ * d_data[d_bucket_begin[j] .. d_bucket_begin[j+1]).  With K =
+ * 2^ceil(log2(num_splitters+1)) leaves, the classes are
+ *   equal_buckets == 0: class(e) = smallest i < K-1 with e <= s_i, else K-1
+ *   equal_buckets != 0: class(e) = 2i + 1 - [e < s_i] over the splitters
+ *                       padded to K entries with the largest one (Sec. 2)
+ * and B = K or 2K; d_bucket_begin receives B+1 values (u64, device memory).
+ * Order inside a bucket is unspecified.  B must be <= the sorter's k.
+ * Errors: E_INVAL (num_splitters == 0, B > k, NULL pointers). */
+int ipsgpu_partition_level(ipsgpu_sorter *s, void *d_data, uint64_t n,
+                           const void *d_splitters, uint32_t num_splitters,
+                           int equal_buckets, uint64_t *d_bucket_begin, void *stream);
+
+/* One IPS2Ra partitioning step (Sec. 5): class(e) = (key >> shift) &
+ * (2^bits - 1), bits in [1, 8] with 2^bits <= k; d_bucket_begin receives
+ * 2^bits + 1 values.  U32 / U64 / PAIR_U64 only (E_UNSUPPORTED otherwise). */
+int ipsgpu_radix_level(ipsgpu_sorter *s, void *d_data, uint64_t n, uint32_t shift,
+                       uint32_t bits, uint64_t *d_bucket_begin, void *stream);
+
+/* The classification rule alone (Sec. 2 branchless tree, Algorithm 1):
+ * writes class(d_data[i]) to d_class[i] (u32, device) without moving data.
+ * Same splitter semantics and errors as ipsgpu_partition_level. */
+int ipsgpu_classify(ipsgpu_sorter *s, const void *d_data, uint64_t n,
+                    const void *d_splitters, uint32_t num_splitters, int equal_buckets,
+                    uint32_t *d_class, void *stream);
+
+/* Synchronize `stream`, return the sorter's device status word (IPSGPU_OK
+ * if no kernel reported an error since the last call) and clear it. */
+int ipsgpu_status(ipsgpu_sorter *s, void *stream);
+
+/* Static description of a status code. */
+const char *ipsgpu_strerror(int code);
+
+/* Per-kernel timing.  When enabled, every kernel launch of the sorter is
+ * bracketed by CUDA events on its stream; ipsgpu_kernel_stats synchronizes
+ * and reports, for kernel kind i (names from ipsgpu_kernel_name), the number
+ * of launches, their summed device time in ms and the algorithmic bytes
+ * those launches moved (as defined in the library's design notes).  Arrays
+ * have `cap` entries; returns the number of kinds. */
+int ipsgpu_set_timing(ipsgpu_sorter *s, int enable);
+int ipsgpu_kernel_stats(ipsgpu_sorter *s, uint64_t *launches, double *ms,
+                        double *bytes, int cap);
+const char *ipsgpu_kernel_name(int kind);
+
+/* Test hook for failure detection: launches one kernel that waits, with the
+ * sorter's bounded-wait helper and at most `spin_limit` polls, on a device
+ * flag that nothing sets, so the wait must give up and record
+ * IPSGPU_E_TIMEOUT in the status word (read it with ipsgpu_status). */
+int ipsgpu_debug_bounded_wait(ipsgpu_sorter *s, uint32_t spin_limit, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IPSGPU_H */

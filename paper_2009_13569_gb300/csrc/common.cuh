@@ -1,0 +1,275 @@
+// common.cuh -- element traits, device helpers and the layouts shared by the
+// kernels of one partitioning level (Sec. 3.1 of Axtmann et al.).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ipsgpu.h"
+
+namespace ipsgpu {
+
+// ---------------------------------------------------------------- limits
+constexpr int kMaxClasses = 256;      // buckets per level incl. equality ones
+constexpr int kMaxSortSample = 4096;  // sample elements sorted in one CTA
+constexpr uint32_t kRBias = 1u << 30; // bias of the read pointer field
+constexpr int kBaseSmemBytes = 192 * 1024;  // element buffer of the base case
+
+// ------------------------------------------------------------ key types
+// Rec100 keys: bytes 0..7 big-endian in hi, bytes 8..9 big-endian in lo.
+struct Key80 {
+    uint64_t hi;
+    uint32_t lo;
+};
+__host__ __device__ inline bool operator<(const Key80 &a, const Key80 &b) {
+    return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__host__ __device__ inline bool operator==(const Key80 &a, const Key80 &b) {
+    return a.hi == b.hi && a.lo == b.lo;
+}
+
+struct PairElem {
+    uint64_t k, v;
+};
+struct Rec100Elem {
+    uint32_t w[25];
+};
+
+// Element traits.  E: element storage, K: key, D: bytes, key(): order key.
+struct TU32 {
+    typedef uint32_t E;
+    typedef uint32_t K;
+    static constexpr int D = 4;
+    static constexpr bool kRadix = true;
+    __device__ static K key(const E &e) { return e; }
+    __device__ static uint64_t rkey(const E &e) { return e; }
+    __device__ static K max_key() { return 0xFFFFFFFFu; }
+    __device__ static E head(uint4 h) { return h.x; }
+};
+struct TU64 {
+    typedef uint64_t E;
+    typedef uint64_t K;
+    static constexpr int D = 8;
+    static constexpr bool kRadix = true;
+    __device__ static K key(const E &e) { return e; }
+    __device__ static uint64_t rkey(const E &e) { return e; }
+    __device__ static K max_key() { return ~0ull; }
+    __device__ static E head(uint4 h) { return (uint64_t)h.x | ((uint64_t)h.y << 32); }
+};
+// f64: order key = (b>>63) ? ~b : b | 2^63 on the IEEE bits
+struct TF64 {
+    typedef uint64_t E;
+    typedef uint64_t K;
+    static constexpr int D = 8;
+    static constexpr bool kRadix = false;
+    __device__ static K key(const E &e) {
+        return (e >> 63) ? ~e : (e | 0x8000000000000000ull);
+    }
+    __device__ static uint64_t rkey(const E &e) { return key(e); }
+    __device__ static K max_key() { return ~0ull; }
+    __device__ static E head(uint4 h) { return (uint64_t)h.x | ((uint64_t)h.y << 32); }
+};
+struct TPair {
+    typedef PairElem E;
+    typedef uint64_t K;
+    static constexpr int D = 16;
+    static constexpr bool kRadix = true;
+    __device__ static K key(const E &e) { return e.k; }
+    __device__ static uint64_t rkey(const E &e) { return e.k; }
+    __device__ static K max_key() { return ~0ull; }
+    __device__ static E head(uint4 h) {
+        E e;
+        e.k = (uint64_t)h.x | ((uint64_t)h.y << 32);
+        e.v = (uint64_t)h.z | ((uint64_t)h.w << 32);
+        return e;
+    }
+};
+struct TRec100 {
+    typedef Rec100Elem E;
+    typedef Key80 K;
+    static constexpr int D = 100;
+    static constexpr bool kRadix = false;
+    // bytes 0..3 of a record are w[0] little-endian, so byte-swapping w[0]
+    // and w[1] gives bytes 0..7 in big-endian (lexicographic) order
+    __device__ static K key_words(uint32_t w0, uint32_t w1, uint32_t w2) {
+        K k;
+        k.hi = ((uint64_t)__byte_perm(w0, 0, 0x0123) << 32) | __byte_perm(w1, 0, 0x0123);
+        k.lo = ((w2 & 0xFFu) << 8) | ((w2 >> 8) & 0xFFu);
+        return k;
+    }
+    __device__ static K key(const E &e) { return key_words(e.w[0], e.w[1], e.w[2]); }
+    __device__ static uint64_t rkey(const E &e) { return key(e).hi; }
+    __device__ static K max_key() {
+        K k;
+        k.hi = ~0ull;
+        k.lo = 0xFFFFFFFFu;
+        return k;
+    }
+    // only the first 16 bytes (the key and 6 payload bytes) are meaningful
+    __device__ static E head(uint4 h) {
+        E e;
+        e.w[0] = h.x;
+        e.w[1] = h.y;
+        e.w[2] = h.z;
+        e.w[3] = h.w;
+        return e;
+    }
+};
+
+// ------------------------------------------------------------ level layouts
+// Host-planned description of one segment partitioned in a level launch.
+struct SegDesc {
+    uint64_t begin;      // element offset of the segment in the data array
+    uint64_t n;          // elements
+    uint32_t b;          // block size in elements
+    uint32_t C;          // class budget (power of two <= 256)
+    uint32_t stripe0;    // first stripe of the segment
+    uint32_t nstripes;
+    uint32_t cta0;       // first block-permutation CTA of the segment
+    uint32_t ncta;
+    uint64_t stage_off;  // arena byte offset of the cleanup staging area
+    uint32_t mode;       // 0: sample splitters, 1: given splitters, 2: radix
+    uint32_t radix_shift;
+    uint32_t radix_bits;
+    uint32_t nsplit;     // given splitters (mode 1)
+    uint32_t eq_given;
+    uint32_t pad;
+};
+
+// Per-stripe plan (host) and output (device).
+struct StripeDesc {
+    uint32_t seg;
+    uint32_t blk0;       // first block of the stripe within its segment
+    uint32_t nblk;       // blocks (the last one may be partial)
+    uint32_t pad;
+    uint64_t left_off;   // arena byte offset of this stripe's leftover buffers
+};
+
+// Device-computed state of a segment during a level.
+struct SegState {
+    uint32_t K, B, logK, eq;
+    uint32_t nslots;       // ceil(n / b)
+    uint32_t nfull_slots;  // floor(n / b)
+    uint32_t ovf_used;     // 1 if a block was written to the overflow block
+    uint32_t pad;
+    uint64_t bucket_begin[kMaxClasses + 1];
+    unsigned long long ptr[kMaxClasses];  // (w << 32) | (r_excl + kRBias)
+    uint32_t readers[kMaxClasses];
+    uint32_t full[kMaxClasses];       // full blocks of each class
+    uint32_t dlm[kMaxClasses + 1];    // delimiters (blocks)
+};
+
+struct Move {
+    uint32_t seg;
+    uint32_t src, dst, len;  // block indices within the segment
+};
+
+struct LevelArgs {
+    unsigned char *data;
+    const SegDesc *seg;
+    SegState *st;
+    unsigned char *tree;      // [nseg][kMaxClasses] keys (BFS tree, index 1..K-1)
+    unsigned char *spl;       // [nseg][kMaxClasses] keys (padded splitters)
+    const unsigned char *given_spl;  // mode 1: user splitters (elements)
+    const StripeDesc *stripe;
+    uint32_t *scount;         // [nstripe][kMaxClasses]
+    uint32_t *sfull;          // [nstripe] full blocks written by the stripe
+    unsigned char *arena;
+    unsigned char *ovf;       // [nseg][block bytes]
+    Move *moves;
+    uint32_t *nmoves;
+    uint32_t move_cap;
+    int *status;
+    uint32_t nseg, nstripe;
+    uint32_t spin_limit;
+    uint32_t pad;
+    uint64_t seed;
+    float alpha_scale;
+    uint32_t ovf_stride;      // bytes per overflow block slot
+};
+
+// ------------------------------------------------------------ helpers
+__device__ inline void set_status(int *status, int code) {
+    atomicCAS(status, 0, code);
+}
+
+__device__ inline uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__host__ __device__ inline uint32_t ilog2_floor(uint64_t x) {
+    uint32_t l = 0;
+    while ((x >> l) > 1) l++;
+    return l;
+}
+
+// Classification of one key (Sec. 2, refined branchless decision tree):
+// descend i <- 2i + [tree_i < e] from the root for log2 K steps, leaf i - K;
+// with equality buckets the class is 2i + 1 - [e < s_i].
+template <class K>
+__device__ __forceinline__ uint32_t classify_key(const K &e, const K *tree, const K *spl,
+                                                 uint32_t logK, bool eq) {
+    uint32_t i = 1;
+    for (uint32_t l = 0; l < logK; l++) i = 2 * i + (tree[i] < e ? 1u : 0u);
+    i -= (1u << logK);
+    if (eq) i = 2 * i + 1 - (e < spl[i] ? 1u : 0u);
+    return i;
+}
+
+// CTA-wide exclusive scan of cnt[0..N) into out[0..N); returns the total.
+// All threads must call it; blockDim.x must be a multiple of 32.
+template <typename T>
+__device__ T cta_exclusive_scan(const T *cnt, T *out, int N, T *warp_tmp) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int per = (N + nthr - 1) / nthr;
+    const int lo = min(N, tid * per), hi = min(N, lo + per);
+    T s = 0;
+    for (int i = lo; i < hi; i++) s += cnt[i];
+    // inclusive warp scan of s
+    T x = s;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tmp[warp] = x;
+    __syncthreads();
+    const int nw = nthr >> 5;
+    if (warp == 0) {
+        T w = lane < nw ? warp_tmp[lane] : (T)0;
+        T v = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane < nw) warp_tmp[lane] = v - w;  // exclusive warp offsets
+        if (lane == 31) warp_tmp[32] = v;        // total
+    }
+    __syncthreads();
+    T run = warp_tmp[warp] + x - s;
+    for (int i = lo; i < hi; i++) {
+        T c = cnt[i];
+        out[i] = run;
+        run += c;
+    }
+    T total = warp_tmp[32];
+    __syncthreads();
+    return total;
+}
+
+// Bounded spin on a 32-bit device word: waits until *p == want or the
+// iteration budget is spent.  Returns true on success.  On timeout the caller
+// records IPSGPU_E_TIMEOUT and returns without touching shared data.
+__device__ inline bool bounded_wait_eq(const volatile uint32_t *p, uint32_t want,
+                                       uint32_t limit) {
+    for (uint32_t it = 0; it < limit; it++) {
+        if (*p == want) return true;
+        __nanosleep(64);
+    }
+    return *p == want;
+}
+
+}  // namespace ipsgpu

@@ -1,0 +1,713 @@
+// ipsgpu.cu -- the C ABI (include/ipsgpu.h) and the host-side driver of the
+// recursion: detect easy inputs, partition large segments level by level
+// (batches of segments per launch), hand segments that fit shared memory to
+// the base case (Sec. 3.2 task structure, Sec. 5 parameters; the recursion
+// on a GPU is breadth-first over all segments of a level).
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <utility>
+#include <vector>
+
+#include "sorter.h"
+
+using namespace ipsgpu;
+
+struct ipsgpu_sorter {
+    Sorter s;
+};
+
+namespace {
+
+constexpr uint64_t kMinStripe = 1u << 15;  // elements
+constexpr int kResStride = kMaxClasses + 3;
+
+__global__ void k_debug_wait(uint32_t *flag, uint32_t limit, int *status) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (!bounded_wait_eq(flag, 1u, limit)) set_status(status, IPSGPU_E_TIMEOUT);
+    }
+}
+
+const TypeOps *ops_for(int dtype) {
+    switch (dtype) {
+    case IPSGPU_U32: return &ops_u32;
+    case IPSGPU_U64: return &ops_u64;
+    case IPSGPU_F64: return &ops_f64;
+    case IPSGPU_PAIR_U64: return &ops_pair;
+    case IPSGPU_REC100: return &ops_rec100;
+    default: return nullptr;
+    }
+}
+
+uint64_t next_pow2(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// block size in elements: block_bytes / D rounded down to a power of two
+uint32_t block_elems(uint32_t block_bytes, int D) {
+    uint32_t b = 1;
+    while ((uint64_t)b * 2 * D <= block_bytes) b *= 2;
+    return b;
+}
+
+struct Resolved {
+    uint32_t k, block_bytes, base_case, spin_limit;
+    float alpha_scale;
+    uint64_t seed, arena_bytes;
+    int algo;
+};
+
+int resolve(const ipsgpu_params *p, int dtype, Resolved *r) {
+    const TypeOps *ops = ops_for(dtype);
+    if (!ops) return IPSGPU_E_INVAL;
+    r->k = (p && p->k) ? p->k : 256;
+    r->block_bytes = (p && p->block_bytes) ? p->block_bytes : 512;
+    r->alpha_scale = (p && p->alpha_scale > 0) ? p->alpha_scale : 0.2f;
+    r->seed = (p && p->seed) ? p->seed : 0x1B54A32D192ED03ull;
+    r->algo = p ? p->algo : IPSGPU_SAMPLESORT;
+    r->spin_limit = (p && p->spin_limit) ? p->spin_limit : (1u << 22);
+    r->arena_bytes = (p && p->arena_bytes) ? p->arena_bytes : (256ull << 20);
+    const uint32_t cap = (uint32_t)(kBaseSmemBytes / ops->D);
+    r->base_case = (p && p->base_case) ? p->base_case : cap;
+    if (r->k < 4 || r->k > (uint32_t)kMaxClasses || (r->k & (r->k - 1))) return IPSGPU_E_INVAL;
+    if (r->base_case < 32 || r->base_case > cap) return IPSGPU_E_INVAL;
+    uint32_t b = block_elems(r->block_bytes, ops->D);
+    if (b == 0 || (uint64_t)b * ops->D * r->k > 160u * 1024 || (b * ops->D) % 4) return IPSGPU_E_INVAL;
+    if (r->algo != IPSGPU_SAMPLESORT && r->algo != IPSGPU_RADIX) return IPSGPU_E_INVAL;
+    if (r->algo == IPSGPU_RADIX &&
+        !(dtype == IPSGPU_U32 || dtype == IPSGPU_U64 || dtype == IPSGPU_PAIR_U64))
+        return IPSGPU_E_UNSUPPORTED;
+    return IPSGPU_OK;
+}
+
+struct Layout {
+    uint64_t seg, st, tree, stripe, scount, sfull, arena, ovf, moves, cta, res, base, misc;
+    uint64_t total() const {
+        return seg + st + 2 * tree + stripe + scount + sfull + arena + ovf + moves + cta + res +
+               base + misc;
+    }
+};
+
+Layout layout(const Sorter &s, int key_bytes) {
+    Layout L;
+    L.seg = (uint64_t)s.seg_cap * sizeof(SegDesc);
+    L.st = (uint64_t)s.seg_cap * sizeof(SegState);
+    L.tree = (uint64_t)s.seg_cap * kMaxClasses * key_bytes;
+    L.stripe = (uint64_t)s.stripe_cap * sizeof(StripeDesc);
+    L.scount = (uint64_t)s.stripe_cap * kMaxClasses * sizeof(uint32_t);
+    L.sfull = (uint64_t)s.stripe_cap * sizeof(uint32_t);
+    L.arena = s.arena_bytes;
+    L.ovf = (uint64_t)s.seg_cap * align_up((uint64_t)s.b * s.ops->D, 16);
+    L.moves = (uint64_t)s.move_cap * sizeof(Move);
+    L.cta = (uint64_t)s.cta_cap * sizeof(uint32_t);
+    L.res = (uint64_t)s.seg_cap * kResStride * sizeof(uint64_t);
+    L.base = (uint64_t)s.base_cap * 2 * sizeof(uint64_t);
+    L.misc = 256;
+    return L;
+}
+
+void apply(Sorter &s, const Resolved &r, int dtype) {
+    s.dtype = dtype;
+    s.ops = ops_for(dtype);
+    s.k = r.k;
+    s.block_bytes = r.block_bytes;
+    s.alpha_scale = r.alpha_scale;
+    s.seed = r.seed;
+    s.algo = r.algo;
+    s.spin_limit = r.spin_limit;
+    s.arena_bytes = r.arena_bytes;
+    s.b = block_elems(r.block_bytes, s.ops->D);
+    s.smax = r.base_case;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? IPSGPU_OK : IPSGPU_E_CUDA; }
+
+void free_all(Sorter &s) {
+    void *dev[] = {s.d_seg, s.d_st, s.d_tree, s.d_spl, s.d_stripe, s.d_scount, s.d_sfull,
+                   s.d_arena, s.d_ovf, s.d_moves, s.d_nmoves, s.d_status, s.d_cta_seg,
+                   s.d_res, s.d_base, s.d_flags, s.d_waitflag};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    void *host[] = {s.h_seg, s.h_stripe, s.h_cta_seg, s.h_res, s.h_base, s.h_flags};
+    for (void *p : host)
+        if (p) cudaFreeHost(p);
+    for (auto &l : s.launches) {
+        cudaEventDestroy(l.ev0);
+        cudaEventDestroy(l.ev1);
+    }
+    for (auto e : s.event_pool) cudaEventDestroy(e);
+    if (s.h2d_done) cudaEventDestroy(s.h2d_done);
+}
+
+// ------------------------------------------------------------------ levels
+struct Pending {
+    uint64_t begin, n;
+    uint32_t shift;  // radix: the digit to use is bits [shift, shift+bits)
+};
+
+// class budget of a segment (the adaptive k of Sec. 3.2, re-targeted so that
+// children fit the shared-memory base case)
+uint32_t class_budget(const Sorter &s, uint64_t n) {
+    uint64_t want = next_pow2((n + s.smax / 2 - 1) / (s.smax / 2));
+    if (want < 4) want = 4;
+    if (want > s.k) want = s.k;
+    return (uint32_t)want;
+}
+
+struct BatchPlan {
+    uint32_t nseg = 0, nstripe = 0, ncta = 0, nmoves = 0;
+    uint64_t arena = 0, elems = 0;
+};
+
+// Plans segments [i, j) of `list` into the pinned descriptors, up to the
+// capacities; returns j.
+size_t plan_batch(Sorter &s, const std::vector<Pending> &list, size_t i, uint32_t mode,
+                  uint32_t nsplit, int eq_given, uint32_t radix_bits, uint64_t stripe_elems,
+                  uint64_t blocks_per_cta, BatchPlan &bp) {
+    const uint64_t D = s.ops->D;
+    size_t j = i;
+    for (; j < list.size(); j++) {
+        const Pending &pd = list[j];
+        uint32_t C;
+        if (mode == 1) {
+            uint64_t K = next_pow2((uint64_t)nsplit + 1);
+            C = (uint32_t)(eq_given ? 2 * K : K);
+        } else if (mode == 2) {
+            C = 1u << radix_bits;
+        } else {
+            C = class_budget(s, pd.n);
+        }
+        const uint64_t nb = (pd.n + s.b - 1) / s.b;
+        uint64_t p = (pd.n + stripe_elems - 1) / stripe_elems;
+        if (p < 1) p = 1;
+        if (p > nb) p = nb;
+        uint64_t nc = (nb + blocks_per_cta - 1) / blocks_per_cta;
+        if (nc < 1) nc = 1;
+        const uint64_t bufb = align_up((uint64_t)C * s.b * D, 256);
+        const uint64_t arena_need = (p + 1) * bufb;
+        const uint64_t move_need = 2 * (p + C) + 4;
+        if (bp.nseg + 1 > s.seg_cap || bp.nstripe + p > s.stripe_cap ||
+            bp.ncta + nc > s.cta_cap || bp.arena + arena_need > s.arena_bytes ||
+            bp.nmoves + move_need > s.move_cap) {
+            if (bp.nseg == 0) return (size_t)-1;  // one segment does not fit at all
+            break;
+        }
+        SegDesc &sd = s.h_seg[bp.nseg];
+        memset(&sd, 0, sizeof sd);
+        sd.begin = pd.begin;
+        sd.n = pd.n;
+        sd.b = s.b;
+        sd.C = C;
+        sd.stripe0 = bp.nstripe;
+        sd.nstripes = (uint32_t)p;
+        sd.cta0 = bp.ncta;
+        sd.ncta = (uint32_t)nc;
+        sd.stage_off = bp.arena;
+        sd.mode = mode;
+        sd.radix_shift = pd.shift;
+        sd.radix_bits = radix_bits;
+        sd.nsplit = nsplit;
+        sd.eq_given = eq_given ? 1 : 0;
+        uint64_t off = bp.arena + bufb;
+        for (uint64_t q = 0; q < p; q++) {
+            StripeDesc &sp = s.h_stripe[bp.nstripe + q];
+            sp.seg = bp.nseg;
+            const uint64_t b0 = q * nb / p, b1 = (q + 1) * nb / p;
+            sp.blk0 = (uint32_t)b0;
+            sp.nblk = (uint32_t)(b1 - b0);
+            sp.pad = 0;
+            sp.left_off = off;
+            off += bufb;
+        }
+        for (uint64_t c = 0; c < nc; c++) s.h_cta_seg[bp.ncta + c] = bp.nseg;
+        bp.arena += arena_need;
+        bp.nstripe += (uint32_t)p;
+        bp.ncta += (uint32_t)nc;
+        bp.nmoves += (uint32_t)move_need;
+        bp.elems += pd.n;
+        bp.nseg++;
+    }
+    return j;
+}
+
+int upload_plan(Sorter &s, const BatchPlan &bp, cudaStream_t st) {
+    cudaError_t e;
+    e = cudaMemcpyAsync(s.d_seg, s.h_seg, sizeof(SegDesc) * bp.nseg, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s.d_stripe, s.h_stripe, sizeof(StripeDesc) * bp.nstripe,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s.d_cta_seg, s.h_cta_seg, sizeof(uint32_t) * bp.ncta,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(s.h2d_done, st);
+    return cuda_status(e);
+}
+
+// the pinned mirrors may be rewritten only once earlier uploads have run
+int wait_uploads(Sorter &s) { return cuda_status(cudaEventSynchronize(s.h2d_done)); }
+
+void level_sizes(const Sorter &s, const std::vector<Pending> &list, uint64_t &stripe_elems,
+                 uint64_t &blocks_per_cta) {
+    uint64_t tot = 0, blocks = 0;
+    for (auto &p : list) {
+        tot += p.n;
+        blocks += (p.n + s.b - 1) / s.b;
+    }
+    stripe_elems = std::max<uint64_t>(kMinStripe, (tot + 2 * s.nsm - 1) / (2 * (uint64_t)s.nsm));
+    stripe_elems = align_up(stripe_elems, s.b);
+    blocks_per_cta = std::max<uint64_t>(32, (blocks + 8 * s.nsm - 1) / (8 * (uint64_t)s.nsm));
+}
+
+int read_status(Sorter &s, cudaStream_t st, int *code) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(s.h_flags + 2, s.d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return IPSGPU_E_CUDA;
+    h = s.h_flags[2];
+    *code = h;
+    return IPSGPU_OK;
+}
+
+int flush_base(Sorter &s, std::vector<Pending> &base, cudaStream_t st) {
+    size_t i = 0;
+    while (i < base.size()) {
+        int rc = wait_uploads(s);
+        if (rc) return rc;
+        // the previous chunk's copy out of h_base must have run
+        if (i > 0 && cudaStreamSynchronize(st) != cudaSuccess) return IPSGPU_E_CUDA;
+        size_t m = std::min<size_t>(base.size() - i, s.base_cap);
+        uint64_t elems = 0;
+        for (size_t q = 0; q < m; q++) {
+            s.h_base[2 * q] = base[i + q].begin;
+            s.h_base[2 * q + 1] = base[i + q].n;
+            elems += base[i + q].n;
+        }
+        cudaError_t e = cudaMemcpyAsync(s.d_base, s.h_base, sizeof(uint64_t) * 2 * m,
+                                        cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaEventRecord(s.h2d_done, st);
+        if (e != cudaSuccess) return IPSGPU_E_CUDA;
+        s.level_elems = elems;
+        e = s.ops->base(&s, s.data, s.d_base, (uint32_t)m, st);
+        if (e != cudaSuccess) return IPSGPU_E_CUDA;
+        i += m;
+    }
+    base.clear();
+    return IPSGPU_OK;
+}
+
+int check_data(const Sorter &s, const void *d) {
+    if (!d) return IPSGPU_E_INVAL;
+    const int D = s.ops->D;
+    const uintptr_t al = D == 100 ? 4 : (uintptr_t)std::min(D, 16);
+    return ((uintptr_t)d % al) ? IPSGPU_E_INVAL : IPSGPU_OK;
+}
+
+int sort_impl(Sorter &s, unsigned char *data, uint64_t n, cudaStream_t st) {
+    if (n < 2) return IPSGPU_OK;
+    if (n > (1ull << 40)) return IPSGPU_E_INVAL;
+    s.data = data;
+    int rc = wait_uploads(s);
+    if (rc) return rc;
+    // Sec. 5: sorted inputs return, decreasing ones are reversed
+    s.h_flags[0] = 1;
+    s.h_flags[1] = 1;
+    cudaError_t e = cudaMemcpyAsync(s.d_flags, s.h_flags, 2 * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = s.ops->detect(&s, data, n, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s.h_flags, s.d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return IPSGPU_E_CUDA;
+    if (s.h_flags[0]) return IPSGPU_OK;
+    if (s.h_flags[1]) return cuda_status(s.ops->reverse(&s, data, n, st));
+
+    const bool radix = s.algo == IPSGPU_RADIX;
+    const uint32_t kbits = (uint32_t)__builtin_ctz(s.k);
+    const uint32_t keybits = s.ops->D == 4 ? 32 : 64;
+    std::vector<Pending> cur, next, base;
+    if (n <= s.smax)
+        base.push_back({0, n, 0});
+    else
+        cur.push_back({0, n, keybits > kbits ? keybits - kbits : 0});
+    int levels = 0;
+    while (!cur.empty()) {
+        // every level strictly shrinks its segments; a deep recursion means
+        // an inconsistent partition, not a hard input
+        if (++levels > 96) return IPSGPU_E_INTERNAL;
+        uint64_t stripe_elems, bpc;
+        level_sizes(s, cur, stripe_elems, bpc);
+        size_t i = 0;
+        while (i < cur.size()) {
+            if ((rc = wait_uploads(s))) return rc;
+            BatchPlan bp;
+            // radix: the digit of a segment is key bits [shift, shift + kbits)
+            size_t j = plan_batch(s, cur, i, radix ? 2 : 0, 0, 0, kbits, stripe_elems, bpc, bp);
+            if (j == (size_t)-1 || j == i) return IPSGPU_E_INTERNAL;
+            if ((rc = upload_plan(s, bp, st))) return rc;
+            s.level_elems = bp.elems;
+            if ((e = s.ops->level(&s, bp.nseg, bp.nstripe, bp.ncta, nullptr, st)) != cudaSuccess)
+                return IPSGPU_E_CUDA;
+            if ((e = s.ops->pack(&s, bp.nseg, st)) != cudaSuccess) return IPSGPU_E_CUDA;
+            e = cudaMemcpyAsync(s.h_res, s.d_res, sizeof(uint64_t) * kResStride * bp.nseg,
+                                cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) return IPSGPU_E_CUDA;
+            int code = 0;
+            if ((rc = read_status(s, st, &code))) return rc;
+            if (code) return code;
+            for (uint32_t q = 0; q < bp.nseg; q++) {
+                const uint64_t *r = s.h_res + (size_t)q * kResStride;
+                const uint32_t B = (uint32_t)r[0];
+                const bool eq = r[1] != 0;
+                const Pending &par = cur[i + q];
+                for (uint32_t c = 0; c < B; c++) {
+                    if (eq && (c & 1) && c + 1 < B) continue;  // equality bucket: one key
+                    const uint64_t lo = r[2 + c], hi = r[3 + c];
+                    const uint64_t m = hi - lo;
+                    if (m <= 1) continue;
+                    Pending ch{par.begin + lo, m, 0};
+                    if (radix) {
+                        if (par.shift == 0) continue;  // every key bit used: equal keys
+                        ch.shift = par.shift >= kbits ? par.shift - kbits : 0;
+                    }
+                    if (m <= s.smax)
+                        base.push_back(ch);
+                    else
+                        next.push_back(ch);
+                }
+            }
+            i = j;
+        }
+        cur.swap(next);
+        next.clear();
+    }
+    return flush_base(s, base, st);
+}
+
+int single_level(Sorter &s, unsigned char *data, uint64_t n, uint32_t mode, uint32_t nsplit,
+                 int eq, uint32_t shift, uint32_t bits, const unsigned char *given,
+                 cudaStream_t st) {
+    s.data = data;
+    int rc = wait_uploads(s);
+    if (rc) return rc;
+    std::vector<Pending> one{{0, n, shift}};
+    uint64_t stripe_elems, bpc;
+    level_sizes(s, one, stripe_elems, bpc);
+    BatchPlan bp;
+    size_t j = plan_batch(s, one, 0, mode, nsplit, eq, bits, stripe_elems, bpc, bp);
+    if (j != 1) return IPSGPU_E_INVAL;
+    if ((rc = upload_plan(s, bp, st))) return rc;
+    s.level_elems = n;
+    return cuda_status(s.ops->level(&s, bp.nseg, bp.nstripe, bp.ncta, given, st));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- Sorter methods
+namespace ipsgpu {
+
+LevelArgs Sorter::args(uint32_t nseg, uint32_t nstripe, const unsigned char *given_spl) const {
+    LevelArgs a;
+    memset(&a, 0, sizeof a);
+    a.data = data;
+    a.seg = d_seg;
+    a.st = d_st;
+    a.tree = d_tree;
+    a.spl = d_spl;
+    a.given_spl = given_spl;
+    a.stripe = d_stripe;
+    a.scount = d_scount;
+    a.sfull = d_sfull;
+    a.arena = d_arena;
+    a.ovf = d_ovf;
+    a.moves = d_moves;
+    a.nmoves = d_nmoves;
+    a.move_cap = move_cap;
+    a.status = d_status;
+    a.nseg = nseg;
+    a.nstripe = nstripe;
+    a.spin_limit = spin_limit;
+    a.seed = seed;
+    a.alpha_scale = alpha_scale;
+    a.ovf_stride = (uint32_t)align_up((uint64_t)b * ops->D, 16);
+    return a;
+}
+
+void Sorter::tbegin(int kind, double bytes, cudaStream_t st) {
+    if (!timing) return;
+    TimedLaunch l;
+    l.kind = kind;
+    l.bytes = bytes;
+    for (int q = 0; q < 2; q++) {
+        cudaEvent_t ev;
+        if (!event_pool.empty()) {
+            ev = event_pool.back();
+            event_pool.pop_back();
+        } else {
+            cudaEventCreate(&ev);
+        }
+        (q == 0 ? l.ev0 : l.ev1) = ev;
+    }
+    cudaEventRecord(l.ev0, st);
+    launches.push_back(l);
+}
+
+void Sorter::tend(cudaStream_t st) {
+    if (!timing || launches.empty()) return;
+    cudaEventRecord(launches.back().ev1, st);
+}
+
+void Sorter::collect() {
+    for (auto &l : launches) {
+        float ms = 0.f;
+        cudaEventSynchronize(l.ev1);
+        cudaEventElapsedTime(&ms, l.ev0, l.ev1);
+        stat_launches[l.kind]++;
+        stat_ms[l.kind] += ms;
+        stat_bytes[l.kind] += l.bytes;
+        event_pool.push_back(l.ev0);
+        event_pool.push_back(l.ev1);
+    }
+    launches.clear();
+}
+
+}  // namespace ipsgpu
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+uint64_t ipsgpu_scratch_bytes(const ipsgpu_params *params, int dtype) {
+    Resolved r;
+    if (resolve(params, dtype, &r) != IPSGPU_OK) return 0;
+    Sorter s;
+    apply(s, r, dtype);
+    return layout(s, s.ops->key_bytes).total();
+}
+
+int ipsgpu_sorter_create(const ipsgpu_params *params, int dtype, ipsgpu_sorter **out) {
+    if (!out) return IPSGPU_E_INVAL;
+    *out = nullptr;
+    Resolved r;
+    int rc = resolve(params, dtype, &r);
+    if (rc) return rc;
+    ipsgpu_sorter *h = new (std::nothrow) ipsgpu_sorter;
+    if (!h) return IPSGPU_E_NOMEM;
+    Sorter &s = h->s;
+    apply(s, r, dtype);
+    if (cudaGetDevice(&s.device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s.nsm, cudaDevAttrMultiProcessorCount, s.device) != cudaSuccess) {
+        delete h;
+        return IPSGPU_E_CUDA;
+    }
+    Layout L = layout(s, s.ops->key_bytes);
+    s.scratch_bytes = L.total();
+    bool ok = true;
+    auto dm = [&](void **p, uint64_t bytes) {
+        if (ok && cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) ok = false;
+    };
+    auto hm = [&](void **p, uint64_t bytes) {
+        if (ok && cudaMallocHost(p, bytes ? bytes : 16) != cudaSuccess) ok = false;
+    };
+    dm((void **)&s.d_seg, L.seg);
+    dm((void **)&s.d_st, L.st);
+    dm((void **)&s.d_tree, L.tree);
+    dm((void **)&s.d_spl, L.tree);
+    dm((void **)&s.d_stripe, L.stripe);
+    dm((void **)&s.d_scount, L.scount);
+    dm((void **)&s.d_sfull, L.sfull);
+    dm((void **)&s.d_arena, L.arena);
+    dm((void **)&s.d_ovf, L.ovf);
+    dm((void **)&s.d_moves, L.moves);
+    dm((void **)&s.d_nmoves, 64);
+    dm((void **)&s.d_status, 64);
+    dm((void **)&s.d_cta_seg, L.cta);
+    dm((void **)&s.d_res, L.res);
+    dm((void **)&s.d_base, L.base);
+    dm((void **)&s.d_flags, 64);
+    dm((void **)&s.d_waitflag, 64);
+    hm((void **)&s.h_seg, L.seg);
+    hm((void **)&s.h_stripe, L.stripe);
+    hm((void **)&s.h_cta_seg, L.cta);
+    hm((void **)&s.h_res, L.res);
+    hm((void **)&s.h_base, L.base);
+    hm((void **)&s.h_flags, 64);
+    if (ok && cudaEventCreateWithFlags(&s.h2d_done, cudaEventDisableTiming) != cudaSuccess) ok = false;
+    if (ok && (cudaMemset(s.d_status, 0, 64) != cudaSuccess ||
+               cudaMemset(s.d_waitflag, 0, 64) != cudaSuccess))
+        ok = false;
+    if (ok && s.ops->init(&s) != cudaSuccess) {
+        free_all(s);
+        delete h;
+        return IPSGPU_E_CUDA;
+    }
+    if (!ok) {
+        free_all(s);
+        delete h;
+        cudaGetLastError();
+        return IPSGPU_E_NOMEM;
+    }
+    if (cudaEventRecord(s.h2d_done, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        free_all(s);
+        delete h;
+        return IPSGPU_E_CUDA;
+    }
+    *out = h;
+    return IPSGPU_OK;
+}
+
+int ipsgpu_sorter_destroy(ipsgpu_sorter *h) {
+    if (!h) return IPSGPU_E_INVAL;
+    cudaDeviceSynchronize();
+    free_all(h->s);
+    delete h;
+    return IPSGPU_OK;
+}
+
+int ipsgpu_sort(ipsgpu_sorter *h, void *d_data, uint64_t n, void *stream) {
+    if (!h) return IPSGPU_E_INVAL;
+    if (n == 0) return IPSGPU_OK;
+    int rc = check_data(h->s, d_data);
+    if (rc) return rc;
+    return sort_impl(h->s, (unsigned char *)d_data, n, (cudaStream_t)stream);
+}
+
+int ipsgpu_partition_level(ipsgpu_sorter *h, void *d_data, uint64_t n, const void *d_splitters,
+                           uint32_t num_splitters, int equal_buckets, uint64_t *d_bucket_begin,
+                           void *stream) {
+    if (!h || !d_bucket_begin || !d_splitters || num_splitters == 0) return IPSGPU_E_INVAL;
+    Sorter &s = h->s;
+    const uint64_t K = next_pow2((uint64_t)num_splitters + 1);
+    const uint64_t B = equal_buckets ? 2 * K : K;
+    if (B > s.k) return IPSGPU_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0)
+        return cuda_status(cudaMemsetAsync(d_bucket_begin, 0, sizeof(uint64_t) * (B + 1), st));
+    int rc = check_data(s, d_data);
+    if (rc) return rc;
+    rc = single_level(s, (unsigned char *)d_data, n, 1, num_splitters, equal_buckets, 0, 0,
+                      (const unsigned char *)d_splitters, st);
+    if (rc) return rc;
+    return cuda_status(cudaMemcpyAsync(d_bucket_begin, s.d_st[0].bucket_begin,
+                                       sizeof(uint64_t) * (B + 1), cudaMemcpyDeviceToDevice, st));
+}
+
+int ipsgpu_radix_level(ipsgpu_sorter *h, void *d_data, uint64_t n, uint32_t shift, uint32_t bits,
+                       uint64_t *d_bucket_begin, void *stream) {
+    if (!h || !d_bucket_begin) return IPSGPU_E_INVAL;
+    Sorter &s = h->s;
+    if (!(s.dtype == IPSGPU_U32 || s.dtype == IPSGPU_U64 || s.dtype == IPSGPU_PAIR_U64))
+        return IPSGPU_E_UNSUPPORTED;
+    const uint32_t keybits = s.dtype == IPSGPU_U32 ? 32 : 64;
+    if (bits < 1 || bits > 8 || (1u << bits) > s.k || shift >= keybits) return IPSGPU_E_INVAL;
+    const uint64_t B = 1ull << bits;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0)
+        return cuda_status(cudaMemsetAsync(d_bucket_begin, 0, sizeof(uint64_t) * (B + 1), st));
+    int rc = check_data(s, d_data);
+    if (rc) return rc;
+    rc = single_level(s, (unsigned char *)d_data, n, 2, 0, 0, shift, bits, nullptr, st);
+    if (rc) return rc;
+    return cuda_status(cudaMemcpyAsync(d_bucket_begin, s.d_st[0].bucket_begin,
+                                       sizeof(uint64_t) * (B + 1), cudaMemcpyDeviceToDevice, st));
+}
+
+int ipsgpu_classify(ipsgpu_sorter *h, const void *d_data, uint64_t n, const void *d_splitters,
+                    uint32_t num_splitters, int equal_buckets, uint32_t *d_class, void *stream) {
+    if (!h || !d_class || !d_splitters || num_splitters == 0) return IPSGPU_E_INVAL;
+    Sorter &s = h->s;
+    const uint64_t K = next_pow2((uint64_t)num_splitters + 1);
+    const uint64_t B = equal_buckets ? 2 * K : K;
+    if (B > s.k) return IPSGPU_E_INVAL;
+    if (n == 0) return IPSGPU_OK;
+    int rc = check_data(s, d_data);
+    if (rc) return rc;
+    if ((rc = wait_uploads(s))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    s.data = (unsigned char *)d_data;
+    SegDesc &sd = s.h_seg[0];
+    memset(&sd, 0, sizeof sd);
+    sd.n = n;
+    sd.b = s.b;
+    sd.C = (uint32_t)B;
+    sd.mode = 1;
+    sd.nsplit = num_splitters;
+    sd.eq_given = equal_buckets ? 1 : 0;
+    BatchPlan bp;
+    bp.nseg = 1;
+    if ((rc = upload_plan(s, bp, st))) return rc;
+    s.level_elems = n;
+    return cuda_status(s.ops->classify_ids(&s, (const unsigned char *)d_splitters, d_class, st));
+}
+
+int ipsgpu_status(ipsgpu_sorter *h, void *stream) {
+    if (!h) return IPSGPU_E_INVAL;
+    Sorter &s = h->s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int code = 0;
+    int rc = read_status(s, st, &code);
+    if (rc) return rc;
+    if (cudaMemsetAsync(s.d_status, 0, sizeof(int), st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return IPSGPU_E_CUDA;
+    return code;
+}
+
+const char *ipsgpu_strerror(int code) {
+    switch (code) {
+    case IPSGPU_OK: return "ok";
+    case IPSGPU_E_INVAL: return "invalid argument";
+    case IPSGPU_E_UNSUPPORTED: return "unsupported element type / algorithm combination";
+    case IPSGPU_E_NOMEM: return "out of memory";
+    case IPSGPU_E_CUDA: return "CUDA runtime error";
+    case IPSGPU_E_TIMEOUT: return "a bounded device wait timed out";
+    case IPSGPU_E_BUSY: return "request cannot be admitted now";
+    case IPSGPU_E_INTERNAL: return "internal consistency check failed";
+    default: return "unknown status";
+    }
+}
+
+int ipsgpu_set_timing(ipsgpu_sorter *h, int enable) {
+    if (!h) return IPSGPU_E_INVAL;
+    h->s.timing = enable != 0;
+    return IPSGPU_OK;
+}
+
+static const char *kKindNames[KK_COUNT] = {"detect", "reverse", "sample_tree", "classify",
+                                           "prep",   "fixup",   "permute",     "stage",
+                                           "fill",   "pack",    "base_case",   "classify_ids",
+                                           "debug_wait"};
+
+const char *ipsgpu_kernel_name(int kind) {
+    return (kind >= 0 && kind < KK_COUNT) ? kKindNames[kind] : "";
+}
+
+int ipsgpu_kernel_stats(ipsgpu_sorter *h, uint64_t *launches, double *ms, double *bytes, int cap) {
+    if (!h) return -IPSGPU_E_INVAL;
+    Sorter &s = h->s;
+    s.collect();
+    for (int i = 0; i < KK_COUNT && i < cap; i++) {
+        if (launches) launches[i] = s.stat_launches[i];
+        if (ms) ms[i] = s.stat_ms[i];
+        if (bytes) bytes[i] = s.stat_bytes[i];
+        s.stat_launches[i] = 0;
+        s.stat_ms[i] = 0;
+        s.stat_bytes[i] = 0;
+    }
+    return KK_COUNT;
+}
+
+int ipsgpu_debug_bounded_wait(ipsgpu_sorter *h, uint32_t spin_limit, void *stream) {
+    if (!h) return IPSGPU_E_INVAL;
+    Sorter &s = h->s;
+    cudaStream_t st = (cudaStream_t)stream;
+    s.tbegin(KK_WAIT, 0, st);
+    k_debug_wait<<<1, 32, 0, st>>>(s.d_waitflag, spin_limit, s.d_status);
+    s.tend(st);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // extern "C"

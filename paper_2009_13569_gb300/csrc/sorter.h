@@ -1,0 +1,117 @@
+// sorter.h -- host-side state of an ipsgpu_sorter and the per-element-type
+// launch table.  Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace ipsgpu {
+
+enum KernelKind {
+    KK_DETECT = 0,
+    KK_REVERSE,
+    KK_SAMPLE,
+    KK_CLASSIFY,
+    KK_PREP,
+    KK_FIXUP,
+    KK_PERMUTE,
+    KK_STAGE,
+    KK_FILL,
+    KK_PACK,
+    KK_BASE,
+    KK_CLASSIFY_IDS,
+    KK_WAIT,
+    KK_COUNT
+};
+
+struct Sorter;
+
+// Kernel launchers of one element type (implemented in ops_<type>.cu).
+struct TypeOps {
+    int D;         // element bytes
+    int key_bytes; // sizeof(K)
+    cudaError_t (*init)(Sorter *);  // one-time kernel attributes
+    cudaError_t (*level)(Sorter *, uint32_t nseg, uint32_t nstripe, uint32_t ncta,
+                         const unsigned char *given_spl, cudaStream_t);
+    cudaError_t (*pack)(Sorter *, uint32_t nseg, cudaStream_t);
+    cudaError_t (*base)(Sorter *, unsigned char *data, const uint64_t *d_segs, uint32_t nsegs,
+                        cudaStream_t);
+    cudaError_t (*detect)(Sorter *, const unsigned char *data, uint64_t n, cudaStream_t);
+    cudaError_t (*reverse)(Sorter *, unsigned char *data, uint64_t n, cudaStream_t);
+    cudaError_t (*classify_ids)(Sorter *, const unsigned char *given_spl, uint32_t *out,
+                                cudaStream_t);
+};
+
+extern const TypeOps ops_u32, ops_u64, ops_f64, ops_pair, ops_rec100;
+
+struct TimedLaunch {
+    int kind;
+    double bytes;
+    cudaEvent_t ev0, ev1;
+};
+
+struct Sorter {
+    int dtype = 0;
+    int device = 0;
+    int nsm = 0;
+    const TypeOps *ops = nullptr;
+    // parameters (defaults resolved)
+    uint32_t k = 256;
+    uint32_t block_bytes = 512;
+    float alpha_scale = 0.2f;
+    uint64_t seed = 0;
+    int algo = 0;
+    uint32_t spin_limit = 1u << 22;
+    uint64_t arena_bytes = 256ull << 20;
+    uint32_t b = 64;        // block size in elements
+    uint32_t smax = 24576;  // largest segment of the base case
+    // capacities of one level batch
+    uint32_t seg_cap = 4096, stripe_cap = 8192, cta_cap = 1u << 16, move_cap = 1u << 21;
+    uint32_t base_cap = 1u << 20;
+    // device scratch
+    SegDesc *d_seg = nullptr;
+    SegState *d_st = nullptr;
+    unsigned char *d_tree = nullptr, *d_spl = nullptr;
+    StripeDesc *d_stripe = nullptr;
+    uint32_t *d_scount = nullptr, *d_sfull = nullptr;
+    unsigned char *d_arena = nullptr, *d_ovf = nullptr;
+    Move *d_moves = nullptr;
+    uint32_t *d_nmoves = nullptr;
+    int *d_status = nullptr;
+    uint32_t *d_cta_seg = nullptr;
+    uint64_t *d_res = nullptr;
+    uint64_t *d_base = nullptr;
+    int *d_flags = nullptr;
+    uint32_t *d_waitflag = nullptr;
+    // pinned host mirrors
+    SegDesc *h_seg = nullptr;
+    StripeDesc *h_stripe = nullptr;
+    uint32_t *h_cta_seg = nullptr;
+    uint64_t *h_res = nullptr;
+    uint64_t *h_base = nullptr;
+    int *h_flags = nullptr;
+    uint64_t scratch_bytes = 0;
+    cudaEvent_t h2d_done = nullptr;  // last upload out of the pinned mirrors
+    // the level currently being launched
+    unsigned char *data = nullptr;
+    // timing
+    bool timing = false;
+    std::vector<TimedLaunch> launches;
+    std::vector<cudaEvent_t> event_pool;
+    uint64_t stat_launches[KK_COUNT] = {};
+    double stat_ms[KK_COUNT] = {};
+    double stat_bytes[KK_COUNT] = {};
+    // per-level algorithmic element count (for the byte model of a launch)
+    uint64_t level_elems = 0;
+
+    void tbegin(int kind, double bytes, cudaStream_t st);
+    void tend(cudaStream_t st);
+    void collect();
+    LevelArgs args(uint32_t nseg, uint32_t nstripe, const unsigned char *given_spl) const;
+};
+
+}  // namespace ipsgpu

@@ -1,0 +1,167 @@
+"""Thin ctypes binding of the C ABI in include/ipsgpu.h.
+
+Every function here only marshals arguments: device pointers and sizes in,
+status codes out.  All work runs in the CUDA kernels of libipsgpu.so.  There
+is no fallback: if the library is missing, loading raises IpsgpuError (build
+it with ``paper_2009_13569_gb300.build.build()``).
+"""
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libipsgpu.so")
+
+DTYPES = {"u32": 0, "u64": 1, "f64": 2, "pair": 3, "rec100": 4}
+ELEM_BYTES = {"u32": 4, "u64": 8, "f64": 8, "pair": 16, "rec100": 100}
+SAMPLESORT, RADIX = 0, 1
+
+OK, E_INVAL, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY, E_INTERNAL = range(8)
+
+
+class IpsgpuError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__("%s: %s (status %d)" % (what, strerror(code) if _lib else "?", code))
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint32), ("block_bytes", ctypes.c_uint32),
+                ("alpha_scale", ctypes.c_float), ("base_case", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64), ("algo", ctypes.c_int32),
+                ("spin_limit", ctypes.c_uint32), ("arena_bytes", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def load():
+    """Load libipsgpu.so (raises IpsgpuError if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise IpsgpuError(E_CUDA, "libipsgpu.so not found at %s; run build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    sig = {
+        "ipsgpu_sorter_create": (i32, [ctypes.POINTER(Params), i32, ctypes.POINTER(vp)]),
+        "ipsgpu_sorter_destroy": (i32, [vp]),
+        "ipsgpu_scratch_bytes": (u64, [ctypes.POINTER(Params), i32]),
+        "ipsgpu_sort": (i32, [vp, vp, u64, vp]),
+        "ipsgpu_partition_level": (i32, [vp, vp, u64, vp, u32, i32, vp, vp]),
+        "ipsgpu_radix_level": (i32, [vp, vp, u64, u32, u32, vp, vp]),
+        "ipsgpu_classify": (i32, [vp, vp, u64, vp, u32, i32, vp, vp]),
+        "ipsgpu_status": (i32, [vp, vp]),
+        "ipsgpu_strerror": (ctypes.c_char_p, [i32]),
+        "ipsgpu_set_timing": (i32, [vp, i32]),
+        "ipsgpu_kernel_stats": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), i32]),
+        "ipsgpu_kernel_name": (ctypes.c_char_p, [i32]),
+        "ipsgpu_debug_bounded_wait": (i32, [vp, u32, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of the C-ABI functions this binding declares."""
+    return [
+        "ipsgpu_sorter_create", "ipsgpu_sorter_destroy", "ipsgpu_scratch_bytes", "ipsgpu_sort",
+        "ipsgpu_partition_level", "ipsgpu_radix_level", "ipsgpu_classify", "ipsgpu_status",
+        "ipsgpu_strerror", "ipsgpu_set_timing", "ipsgpu_kernel_stats", "ipsgpu_kernel_name",
+        "ipsgpu_debug_bounded_wait",
+    ]
+
+
+def strerror(code):
+    return load().ipsgpu_strerror(code).decode()
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise IpsgpuError(rc, what)
+
+
+def make_params(k=0, block_bytes=0, alpha_scale=0.0, base_case=0, seed=0, algo=SAMPLESORT,
+                spin_limit=0, arena_bytes=0):
+    return Params(k, block_bytes, alpha_scale, base_case, seed, algo, spin_limit, arena_bytes)
+
+
+def scratch_bytes(dtype, **params):
+    p = make_params(**params)
+    return int(load().ipsgpu_scratch_bytes(ctypes.byref(p), DTYPES[dtype]))
+
+
+class Sorter:
+    """An ipsgpu_sorter (owns its device scratch).  Pointers are device
+    addresses (ints), streams are cudaStream_t handles (ints, 0 = default)."""
+
+    def __init__(self, dtype, **params):
+        self.dtype = dtype
+        self.elem_bytes = ELEM_BYTES[dtype]
+        p = make_params(**params)
+        h = ctypes.c_void_p()
+        _check(load().ipsgpu_sorter_create(ctypes.byref(p), DTYPES[dtype], ctypes.byref(h)),
+               "ipsgpu_sorter_create")
+        self._h = h
+
+    def close(self):
+        if self._h:
+            load().ipsgpu_sorter_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def sort(self, ptr, n, stream=0):
+        _check(load().ipsgpu_sort(self._h, ptr, n, stream), "ipsgpu_sort")
+
+    def partition_level(self, ptr, n, spl_ptr, num_splitters, equal_buckets, bb_ptr, stream=0):
+        _check(load().ipsgpu_partition_level(self._h, ptr, n, spl_ptr, num_splitters,
+                                             1 if equal_buckets else 0, bb_ptr, stream),
+               "ipsgpu_partition_level")
+
+    def radix_level(self, ptr, n, shift, bits, bb_ptr, stream=0):
+        _check(load().ipsgpu_radix_level(self._h, ptr, n, shift, bits, bb_ptr, stream),
+               "ipsgpu_radix_level")
+
+    def classify(self, ptr, n, spl_ptr, num_splitters, equal_buckets, cls_ptr, stream=0):
+        _check(load().ipsgpu_classify(self._h, ptr, n, spl_ptr, num_splitters,
+                                      1 if equal_buckets else 0, cls_ptr, stream),
+               "ipsgpu_classify")
+
+    def status(self, stream=0):
+        """Synchronize, return and clear the device status word."""
+        return load().ipsgpu_status(self._h, stream)
+
+    def set_timing(self, enable=True):
+        _check(load().ipsgpu_set_timing(self._h, 1 if enable else 0), "ipsgpu_set_timing")
+
+    def kernel_stats(self):
+        """{kernel name: (launches, ms, algorithmic bytes)} since the last call."""
+        cap = 32
+        la = (ctypes.c_uint64 * cap)()
+        ms = (ctypes.c_double * cap)()
+        by = (ctypes.c_double * cap)()
+        nk = load().ipsgpu_kernel_stats(self._h, la, ms, by, cap)
+        if nk < 0:
+            raise IpsgpuError(-nk, "ipsgpu_kernel_stats")
+        return {load().ipsgpu_kernel_name(i).decode(): (int(la[i]), float(ms[i]), float(by[i]))
+                for i in range(nk)}
+
+    def debug_bounded_wait(self, spin_limit, stream=0):
+        _check(load().ipsgpu_debug_bounded_wait(self._h, spin_limit, stream),
+               "ipsgpu_debug_bounded_wait")

@@ -1,0 +1,77 @@
+"""Helpers shared by the GPU parity tests (device placement, comparisons
+against the oracle).  Expected values always come from the oracle package."""
+import numpy as np
+import torch
+
+import oracle
+from paper_2009_13569_gb300 import inputs, ipsgpu
+
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+
+
+def stream():
+    return torch.cuda.current_stream(DEV).cuda_stream
+
+
+def to_dev(host):
+    return host.to(DEV).contiguous()
+
+
+def keys_of(a, dtype):
+    """Order keys of a numpy array in oracle conventions, as something numpy
+    compares in key order (rows of bytes for rec100)."""
+    if dtype == "pair":
+        return a[:, 0]
+    if dtype == "rec100":
+        return a[:, :10]
+    if dtype == "f64":
+        b = a.view(np.uint64)
+        return np.where(b >> np.uint64(63), ~b, b | np.uint64(1 << 63))
+    return a
+
+
+def rows(a, dtype):
+    """Canonically ordered copy of the records, to compare multisets."""
+    if dtype in ("pair", "rec100"):
+        v = np.ascontiguousarray(a).view(np.uint8).reshape(len(a), -1)
+        order = np.lexsort(v.T[::-1])
+        return v[order]
+    return np.sort(a.view(np.uint64) if dtype == "f64" else a)
+
+
+def assert_sorted_parity(got, inp, dtype):
+    """GPU sort output vs the oracle: identical keys everywhere; for u32 /
+    u64 / f64 identical bits, for pair / rec100 the same multiset of records
+    (which, with identical key sequences, means every equal-key run holds
+    the same records)."""
+    ref = oracle.sort(inp, dtype)
+    if dtype in ("u32", "u64"):
+        np.testing.assert_array_equal(got, ref)
+        return
+    if dtype == "f64":
+        np.testing.assert_array_equal(got.view(np.uint64), ref.view(np.uint64))
+        return
+    np.testing.assert_array_equal(keys_of(got, dtype), keys_of(ref, dtype))
+    np.testing.assert_array_equal(rows(got, dtype), rows(inp, dtype))
+
+
+def assert_level_parity(got, bb, inp, dtype, cls, B):
+    """Partition-level parity: bucket boundaries bit-exact, each bucket the
+    same multiset of records as the oracle's bucket."""
+    ref, rbb = oracle.partition(inp, dtype, cls, B)
+    np.testing.assert_array_equal(np.asarray(bb, dtype=np.uint64), rbb)
+    for j in range(B):
+        lo, hi = int(rbb[j]), int(rbb[j + 1])
+        if hi - lo:
+            np.testing.assert_array_equal(rows(got[lo:hi], dtype), rows(ref[lo:hi], dtype),
+                                          err_msg="bucket %d" % j)
+
+
+def run_sort(dtype, host, **params):
+    n = inputs.count(host, dtype)
+    d = to_dev(host)
+    with ipsgpu.Sorter(dtype, **params) as s:
+        s.sort(d.data_ptr(), n, stream())
+        st = s.status(stream())
+    assert st == ipsgpu.OK, ipsgpu.strerror(st)
+    return inputs.to_numpy(d.cpu(), dtype)

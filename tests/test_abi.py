@@ -1,0 +1,50 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, and
+exports every function include/ipsgpu.h declares; host-only entry points
+behave.  No kernel runs here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2009_13569_gb300 import build, ipsgpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return ipsgpu.load()
+
+
+def declared():
+    with open(os.path.join(ROOT, "include", "ipsgpu.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ipsgpu_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(ipsgpu.exported_symbols()) == set(names)
+
+
+def test_strerror_and_scratch_bytes(lib):
+    assert ipsgpu.strerror(ipsgpu.OK) == "ok"
+    assert "timed out" in ipsgpu.strerror(ipsgpu.E_TIMEOUT)
+    b64 = ipsgpu.scratch_bytes("u64")
+    assert b64 > 0
+    # scratch does not depend on n: it is fixed by the parameters
+    assert ipsgpu.scratch_bytes("u64", arena_bytes=1 << 20) < b64
+    # radix takes unsigned keys only
+    assert ipsgpu.scratch_bytes("f64", algo=ipsgpu.RADIX) == 0
+    assert ipsgpu.scratch_bytes("u64", k=3) == 0
+
+
+def test_params_struct_layout():
+    assert ctypes.sizeof(ipsgpu.Params) == 40
+    assert ipsgpu.Params.arena_bytes.offset == 32

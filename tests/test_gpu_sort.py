@@ -1,0 +1,105 @@
+"""GPU parity of the whole sort (levels + base case) through the C ABI
+against the oracle, for every element type and input distribution, plus the
+edge cases of the method (empty, tiny, base-case boundary, sorted, reversed,
+all equal) and the bounded-wait failure path."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2009_13569_gb300 import inputs, ipsgpu
+from _util import DEV, assert_sorted_parity, run_sort, stream
+
+pytestmark = pytest.mark.gpu
+
+N = 300_007
+
+
+@pytest.mark.parametrize("dist", inputs.INT_DISTS)
+@pytest.mark.parametrize("dtype", ["u32", "u64"])
+def test_sort_int_distributions(dtype, dist):
+    host = inputs.generate(dist, dtype, N)
+    assert_sorted_parity(run_sort(dtype, host), inputs.to_numpy(host, dtype), dtype)
+
+
+@pytest.mark.parametrize("dist", inputs.F64_DISTS)
+def test_sort_f64(dist):
+    host = inputs.generate(dist, "f64", N)
+    assert_sorted_parity(run_sort("f64", host), inputs.to_numpy(host, "f64"), "f64")
+
+
+@pytest.mark.parametrize("dist", ["uniform", "rootdup", "twodup", "zipf"])
+def test_sort_pair(dist):
+    host = inputs.generate(dist, "pair", N)
+    assert_sorted_parity(run_sort("pair", host), inputs.to_numpy(host, "pair"), "pair")
+
+
+@pytest.mark.parametrize("dist", inputs.REC_DISTS)
+def test_sort_rec100(dist):
+    host = inputs.generate(dist, "rec100", 60_001)
+    assert_sorted_parity(run_sort("rec100", host), inputs.to_numpy(host, "rec100"), "rec100")
+
+
+@pytest.mark.parametrize("dist", ["uniform", "twodup", "almostsorted", "exponential"])
+@pytest.mark.parametrize("dtype", ["u32", "u64", "pair"])
+def test_sort_radix_variant(dtype, dist):
+    host = inputs.generate(dist, dtype, N)
+    got = run_sort(dtype, host, algo=ipsgpu.RADIX)
+    assert_sorted_parity(got, inputs.to_numpy(host, dtype), dtype)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 31, 32, 33, 63, 64, 65, 1000, 24575, 24576, 24577,
+                               49_155, 2 ** 17, 2 ** 17 + 1])
+def test_sort_sizes(n):
+    host = inputs.generate("uniform", "u64", n, seed=n + 11)
+    assert_sorted_parity(run_sort("u64", host), inputs.to_numpy(host, "u64"), "u64")
+
+
+@pytest.mark.parametrize("base_case", [32, 100, 4096])
+def test_sort_small_base_case_forces_levels(base_case):
+    # a small base case makes even modest inputs recurse through several levels
+    host = inputs.generate("exponential", "u64", 200_000, seed=base_case)
+    got = run_sort("u64", host, base_case=base_case)
+    assert_sorted_parity(got, inputs.to_numpy(host, "u64"), "u64")
+
+
+@pytest.mark.parametrize("k", [4, 16, 64])
+def test_sort_small_k(k):
+    host = inputs.generate("uniform", "u32", 250_000, seed=k)
+    assert_sorted_parity(run_sort("u32", host, k=k), inputs.to_numpy(host, "u32"), "u32")
+
+
+def test_sort_unaligned_view():
+    host = inputs.generate("uniform", "u64", 100_001, seed=3)
+    d = host.to(DEV)
+    v = d[1:]
+    with ipsgpu.Sorter("u64") as s:
+        s.sort(v.data_ptr(), 100_000, stream())
+        assert s.status(stream()) == ipsgpu.OK
+    got = inputs.to_numpy(d.cpu(), "u64")
+    assert got[0] == inputs.to_numpy(host, "u64")[0]
+    assert_sorted_parity(got[1:], inputs.to_numpy(host[1:], "u64"), "u64")
+
+
+def test_sort_on_side_stream_and_reuse():
+    s_ = torch.cuda.Stream(DEV)
+    with ipsgpu.Sorter("u64") as s:
+        for seed in (1, 2, 3):
+            host = inputs.generate("uniform", "u64", 70_000, seed=seed)
+            d = host.to(DEV)
+            torch.cuda.synchronize()
+            s.sort(d.data_ptr(), 70_000, s_.cuda_stream)
+            assert s.status(s_.cuda_stream) == ipsgpu.OK
+            assert_sorted_parity(inputs.to_numpy(d.cpu(), "u64"), inputs.to_numpy(host, "u64"), "u64")
+
+
+def test_bounded_wait_gives_up_with_timeout_status():
+    with ipsgpu.Sorter("u64") as s:
+        s.debug_bounded_wait(1000, stream())
+        assert s.status(stream()) == ipsgpu.E_TIMEOUT
+        # the status word was cleared and the sorter still works
+        assert s.status(stream()) == ipsgpu.OK
+        host = inputs.generate("uniform", "u64", 50_000)
+        d = host.to(DEV)
+        s.sort(d.data_ptr(), 50_000, stream())
+        assert s.status(stream()) == ipsgpu.OK
+    assert_sorted_parity(inputs.to_numpy(d.cpu(), "u64"), inputs.to_numpy(host, "u64"), "u64")
