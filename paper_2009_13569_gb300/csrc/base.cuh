@@ -89,11 +89,12 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(unsigned char *data,
     typedef typename T::K K;
     constexpr int ND = 1 << kBaseDigitBits;
     extern __shared__ __align__(16) unsigned char smem[];
+    // layout: buf | stk (8-byte entries, kept 8-byte aligned) | off | cur | wtmp
     E *buf = reinterpret_cast<E *>(smem);
-    uint32_t *off = reinterpret_cast<uint32_t *>(smem + kBaseSmemBytes);  // ND + 1
+    uint2 *stk = reinterpret_cast<uint2 *>(smem + kBaseSmemBytes);        // kBaseStack
+    uint32_t *off = reinterpret_cast<uint32_t *>(stk + kBaseStack);       // ND + 1
     uint32_t *cur = off + ND + 1;                                         // ND
-    uint2 *stk = reinterpret_cast<uint2 *>(cur + ND);                     // kBaseStack
-    uint32_t *wtmp = reinterpret_cast<uint32_t *>(stk + kBaseStack);      // 34
+    uint32_t *wtmp = cur + ND;                                            // 34
     __shared__ unsigned long long red[2][32];
     __shared__ uint32_t sp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;

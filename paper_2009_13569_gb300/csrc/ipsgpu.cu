@@ -78,7 +78,7 @@ int resolve(const ipsgpu_params *p, int dtype, Resolved *r) {
     if (r->k < 4 || r->k > (uint32_t)kMaxClasses || (r->k & (r->k - 1))) return IPSGPU_E_INVAL;
     if (r->base_case < 32 || r->base_case > cap) return IPSGPU_E_INVAL;
     uint32_t b = block_elems(r->block_bytes, ops->D);
-    if (b == 0 || (uint64_t)b * ops->D * r->k > 160u * 1024 || (b * ops->D) % 4) return IPSGPU_E_INVAL;
+    if (b == 0 || (uint64_t)b * ops->D * r->k > 160u * 1024 || (b * ops->D) % 16) return IPSGPU_E_INVAL;
     if (r->algo != IPSGPU_SAMPLESORT && r->algo != IPSGPU_RADIX) return IPSGPU_E_INVAL;
     if (r->algo == IPSGPU_RADIX &&
         !(dtype == IPSGPU_U32 || dtype == IPSGPU_U64 || dtype == IPSGPU_PAIR_U64))

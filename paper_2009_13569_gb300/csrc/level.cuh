@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(kAuxThreads) k_fixup(LevelArgs a) {
         const SegDesc &sd = a.seg[mv.seg];
         const uint32_t BB = sd.b * T::D;
         unsigned char *base = a.data + sd.begin * (uint64_t)T::D;
-        const int u = access_unit(sd.begin * (uint64_t)T::D);
+        const int u = access_unit((uint64_t)(uintptr_t)base);
         uint4 r;
         warp_load_block(r, base + (uint64_t)(mv.src + k) * BB, BB, lane, u);
         warp_store_block(r, base + (uint64_t)(mv.dst + k) * BB, BB, lane, u);
@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a,
     const uint32_t nfs = st->nfull_slots;
     const uint32_t BB = sd.b * T::D;
     unsigned char *base = a.data + sd.begin * (uint64_t)T::D;
-    const int u = access_unit(sd.begin * (uint64_t)T::D);
+    const int u = access_unit((uint64_t)(uintptr_t)base);
     const uint32_t W = sd.ncta * (kPermuteThreads / 32);
     const uint32_t wid = (blockIdx.x - sd.cta0) * (kPermuteThreads / 32) + warp;
     uint32_t p = (uint32_t)(((uint64_t)wid * B) / W);
@@ -745,7 +745,9 @@ __global__ void __launch_bounds__(kAuxThreads) k_fill(LevelArgs a) {
     const uint64_t nfill = nhead + ntail;
     const uint64_t lo_o = max(hi, ds), hi_o = min(ws, cap);
     const uint32_t nstage = hi_o > lo_o ? (uint32_t)min(hi_o - lo_o, (uint64_t)b) : 0;
-    const uint32_t novf = (ws > cap) ? b : 0;
+    // the overflow block holds this bucket's last full block iff the partial
+    // slot (index nfull_slots) lies inside [d_j, d_j + full_j)
+    const uint32_t novf = (ds <= cap && ws > cap) ? b : 0;
     const E *stage = reinterpret_cast<const E *>(a.arena + sd.stage_off) + (size_t)j * b;
     const E *ovf = reinterpret_cast<const E *>(a.ovf + (size_t)s * a.ovf_stride);
     const uint32_t ns = sd.nstripes;
