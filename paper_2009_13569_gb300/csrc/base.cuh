@@ -9,6 +9,7 @@
 //              insertion-sort base case of Sec. 5)
 #pragma once
 
+#include "classify.cuh"
 #include "common.cuh"
 
 namespace ipsgpu {
@@ -16,9 +17,9 @@ namespace ipsgpu {
 constexpr int kDetectThreads = 256;
 constexpr int kDetectChunk = 8192;
 constexpr int kBaseThreads = 512;
-constexpr int kBaseDigitBits = 11;       // at most 2048 sub-buckets per pass
-constexpr int kBaseInsertion = 24;       // sub-buckets up to this size: insertion sort
-constexpr int kBaseStack = 2048;         // pending ranges: >= 196608 B / 4 B / 25
+constexpr int kBaseDigitBits = 13;       // at most 8192 sub-buckets per pass
+constexpr int kBaseInsertion = 24;       // sub-buckets up to this size: ranked directly
+constexpr int kBaseStack = 2048;         // pending ranges: >= 188416 B / 4 B / 25
 
 
 // second-level radix key: non-zero only for keys wider than 64 bits
@@ -75,12 +76,14 @@ __device__ __forceinline__ Key80 shfl_key<TRec100>(Key80 k, int src) {
 }
 
 // Sorts each listed segment (segs[2i] = begin, segs[2i+1] = n, n <= smax)
-// in place.  Per segment: the elements are read from global memory, spread
-// by an MSD radix digit of (key - min) into shared memory, and each
-// sub-bucket is finished by insertion sort or, if larger, by another pass.
-// A pass reads its range from global memory (the range's final position,
-// which the previous pass left there) and scatters it into the same range
-// of the shared buffer.
+// in place.  The segment is first staged into shared memory with cp.async
+// (one round trip).  A pass over a range [a0, a0+len) then takes min/max and
+// a histogram of an MSD radix digit of (key - min) from shared memory, and
+// scatters the range by digit from its global copy (which equals the
+// shared one) into shared memory.  Sub-buckets of at most kBaseInsertion
+// elements are finished by insertion sort; larger ones get another pass.
+// Every pass writes its range back to global memory, so the global copy of
+// a pending range always matches the shared one.
 template <class T>
 __global__ void __launch_bounds__(kBaseThreads, 1) k_base(unsigned char *data,
                                                           const uint64_t *segs, uint32_t nsegs,
@@ -88,13 +91,18 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(unsigned char *data,
     typedef typename T::E E;
     typedef typename T::K K;
     constexpr int ND = 1 << kBaseDigitBits;
+    constexpr int NB = 8;  // elements loaded per thread before use
+    constexpr int U = (T::D == 4 || T::D == 8 || T::D == 16) ? T::D : 4;
+    constexpr int DPT = ND / kBaseThreads;  // digits per thread in the scan
     extern __shared__ __align__(16) unsigned char smem[];
-    // layout: buf | stk (8-byte entries, kept 8-byte aligned) | off | cur | wtmp
+    // layout: buf | stk | off16 (ND+2 u16) | cur (ND/2 words, two u16
+    // counters each) | wtmp.  Ranges are < 2^16 elements, so 16-bit
+    // counters and offsets suffice; packing two per word keeps 8192 digits.
     E *buf = reinterpret_cast<E *>(smem);
-    uint2 *stk = reinterpret_cast<uint2 *>(smem + kBaseSmemBytes);        // kBaseStack
-    uint32_t *off = reinterpret_cast<uint32_t *>(stk + kBaseStack);       // ND + 1
-    uint32_t *cur = off + ND + 1;                                         // ND
-    uint32_t *wtmp = cur + ND;                                            // 34
+    uint32_t *stk = reinterpret_cast<uint32_t *>(smem + kBaseSmemBytes);   // (a0 << 16) | len
+    uint16_t *off = reinterpret_cast<uint16_t *>(stk + kBaseStack);        // ND + 2
+    uint32_t *cur = reinterpret_cast<uint32_t *>(off + ND + 2);            // ND / 2
+    uint32_t *wtmp = cur + ND / 2;                                         // 34
     __shared__ unsigned long long red[2][32];
     __shared__ uint32_t sp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -124,24 +132,35 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(unsigned char *data,
             __syncthreads();
             continue;
         }
+        {
+            // stage the segment into shared memory
+            const uint32_t units = (uint32_t)(n * T::D / U);
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(g);
+            unsigned char *dst = reinterpret_cast<unsigned char *>(buf);
+            for (uint32_t u = tid; u < units; u += kBaseThreads)
+                cp_async<U>(dst + (size_t)u * U, src + (size_t)u * U);
+            cp_async_commit();
+            cp_async_wait_all();
+        }
         if (tid == 0) {
             sp = 1;
-            stk[0] = make_uint2(0, (uint32_t)n);
+            stk[0] = (uint32_t)n;
         }
         __syncthreads();
         while (sp > 0) {
-            const uint2 top = stk[sp - 1];
+            const uint32_t top = stk[sp - 1];
             __syncthreads();
             if (tid == 0) sp--;
-            const uint32_t a0 = top.x, len = top.y;
+            // a range is packed as (a0 << 16) | len; both are < 2^16 because
+            // a segment holds at most kBaseSmemBytes / 4 < 2^16 elements
+            const uint32_t a0 = top >> 16, len = top & 0xFFFFu;
             // min / max of the radix key over the range (two key words)
             int mode = 0;  // 0: high word, 1: low word (keys wider than 64 bits)
             uint64_t mn = 0, rng = 0;
             for (int pass = 0; pass < 2; pass++) {
                 unsigned long long lmin = ~0ull, lmax = 0;
                 for (uint32_t i = tid; i < len; i += kBaseThreads) {
-                    const E x = g[a0 + i];
-                    uint64_t v = pass == 0 ? T::rkey(x) : rk_lo<T>(x);
+                    const uint64_t v = pass == 0 ? T::rkey(buf[a0 + i]) : rk_lo<T>(buf[a0 + i]);
                     lmin = min(lmin, (unsigned long long)v);
                     lmax = max(lmax, (unsigned long long)v);
                 }
@@ -168,66 +187,125 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(unsigned char *data,
             if (rng == 0) continue;  // all keys equal: the range is final
             const uint32_t nbits = 64 - __clzll((long long)rng);
             uint32_t want = 1;
-            while (want < kBaseDigitBits && ((uint64_t)6 << want) < len) want++;
+            while (want < kBaseDigitBits && ((uint64_t)2 << want) < len) want++;
             const uint32_t dbits = min(nbits, want);
             const uint32_t shift = nbits - dbits;
             const uint32_t nd = 1u << dbits;
-            for (uint32_t d = tid; d < nd; d += kBaseThreads) cur[d] = 0;
+            for (uint32_t w = tid; w < ND / 2; w += kBaseThreads) cur[w] = 0;
             __syncthreads();
             for (uint32_t i = tid; i < len; i += kBaseThreads) {
-                const E x = g[a0 + i];
-                uint64_t v = mode == 0 ? T::rkey(x) : rk_lo<T>(x);
-                atomicAdd(&cur[(uint32_t)((v - mn) >> shift)], 1u);
+                const uint64_t v = mode == 0 ? T::rkey(buf[a0 + i]) : rk_lo<T>(buf[a0 + i]);
+                const uint32_t d = (uint32_t)((v - mn) >> shift);
+                atomicAdd(&cur[d >> 1], 1u << (16 * (d & 1)));
             }
             __syncthreads();
-            cta_exclusive_scan<uint32_t>(cur, off, (int)nd, wtmp);
-            if (tid == 0) off[nd] = len;
-            for (uint32_t d = tid; d < nd; d += kBaseThreads) cur[d] = off[d];
-            __syncthreads();
-            for (uint32_t i = tid; i < len; i += kBaseThreads) {
-                const E x = g[a0 + i];
-                uint64_t v = mode == 0 ? T::rkey(x) : rk_lo<T>(x);
-                uint32_t p = atomicAdd(&cur[(uint32_t)((v - mn) >> shift)], 1u);
-                buf[a0 + p] = x;
-            }
-            __syncthreads();
-            for (uint32_t d = tid; d < nd; d += kBaseThreads) {
-                const uint32_t o = a0 + off[d], c = off[d + 1] - off[d];
-                if (c <= 1) continue;
-                if (c <= kBaseInsertion) {
-                    for (uint32_t i = 1; i < c; i++) {
-                        E x = buf[o + i];
-                        K kx = T::key(x);
-                        uint32_t j = i;
-                        while (j > 0 && kx < T::key(buf[o + j - 1])) {
-                            buf[o + j] = buf[o + j - 1];
-                            j--;
-                        }
-                        buf[o + j] = x;
+            {
+                // exclusive scan of the 16-bit counts; each thread owns DPT
+                // consecutive digits and rewrites them as cursors
+                uint32_t cnt[DPT];
+                uint32_t sum = 0;
+#pragma unroll
+                for (int q = 0; q < DPT / 2; q++) {
+                    const uint32_t w = cur[tid * (DPT / 2) + q];
+                    cnt[2 * q] = w & 0xFFFFu;
+                    cnt[2 * q + 1] = w >> 16;
+                    sum += cnt[2 * q] + cnt[2 * q + 1];
+                }
+                uint32_t x = sum;
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (lane == 31) wtmp[warp] = x;
+                __syncthreads();
+                if (warp == 0) {
+                    uint32_t w = lane < NW ? wtmp[lane] : 0u, v = w;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+                        if (lane >= o) v += y;
                     }
-                } else {
+                    if (lane < NW) wtmp[lane] = v - w;
+                }
+                __syncthreads();
+                uint32_t run = wtmp[warp] + x - sum;
+#pragma unroll
+                for (int q = 0; q < DPT / 2; q++) {
+                    const uint32_t o0 = run, o1 = run + cnt[2 * q];
+                    run = o1 + cnt[2 * q + 1];
+                    off[tid * DPT + 2 * q] = (uint16_t)o0;
+                    off[tid * DPT + 2 * q + 1] = (uint16_t)o1;
+                    cur[tid * (DPT / 2) + q] = o0 | (o1 << 16);
+                }
+                if (tid == kBaseThreads - 1) off[ND] = (uint16_t)len;
+            }
+            __syncthreads();
+            // digits >= nd are empty: their offsets equal len
+            // scatter by digit, reading the range's global copy in batches
+            for (uint32_t i0 = 0; i0 < len; i0 += NB * kBaseThreads) {
+                E x[NB];
+#pragma unroll
+                for (int q = 0; q < NB; q++) {
+                    const uint32_t i = i0 + q * kBaseThreads + tid;
+                    if (i < len) x[q] = g[a0 + i];
+                }
+#pragma unroll
+                for (int q = 0; q < NB; q++) {
+                    const uint32_t i = i0 + q * kBaseThreads + tid;
+                    if (i < len) {
+                        const uint64_t v = mode == 0 ? T::rkey(x[q]) : rk_lo<T>(x[q]);
+                        const uint32_t d = (uint32_t)((v - mn) >> shift);
+                        const uint32_t h = 16 * (d & 1);
+                        const uint32_t p = (atomicAdd(&cur[d >> 1], 1u << h) >> h) & 0xFFFFu;
+                        buf[a0 + p] = x[q];
+                    }
+                }
+            }
+            __syncthreads();
+            // sub-buckets larger than kBaseInsertion get another pass
+            for (uint32_t d = tid; d < nd; d += kBaseThreads) {
+                const uint32_t c = (uint32_t)off[d + 1] - off[d];
+                if (c > kBaseInsertion) {
                     uint32_t q = atomicAdd(&sp, 1u);
                     if (q < kBaseStack)
-                        stk[q] = make_uint2(o, c);
+                        stk[q] = ((a0 + off[d]) << 16) | c;
                     else
                         set_status(status, IPSGPU_E_INTERNAL);
                 }
+            }
+            // every position: inside a small sub-bucket the element's final
+            // place is its rank among the sub-bucket (ties by position); in a
+            // large one it keeps its grouped place for the next pass
+            for (uint32_t p = tid; p < len; p += kBaseThreads) {
+                const E x = buf[a0 + p];
+                const uint64_t v = mode == 0 ? T::rkey(x) : rk_lo<T>(x);
+                const uint32_t d = (uint32_t)((v - mn) >> shift);
+                const uint32_t lo = off[d], c = (uint32_t)off[d + 1] - lo;
+                uint32_t dst = p;
+                if (c <= kBaseInsertion) {
+                    const K kx = T::key(x);
+                    uint32_t rank = 0;
+                    for (uint32_t q = 0; q < c; q++) {
+                        const K kq = T::key(buf[a0 + lo + q]);
+                        rank += (kq < kx || (!(kx < kq) && lo + q < p)) ? 1u : 0u;
+                    }
+                    dst = lo + rank;
+                }
+                g[a0 + dst] = x;
             }
             __syncthreads();
             if (sp > kBaseStack) {
                 if (tid == 0) sp = kBaseStack;
                 __syncthreads();
             }
-            for (uint32_t i = tid; i < len; i += kBaseThreads) g[a0 + i] = buf[a0 + i];
-            __syncthreads();
         }
         __syncthreads();
     }
 }
 
 inline size_t base_smem_bytes() {
-    return kBaseSmemBytes + sizeof(uint32_t) * ((1 << kBaseDigitBits) * 2 + 1) +
-           sizeof(uint2) * kBaseStack + sizeof(uint32_t) * 34 + 16;
+    return kBaseSmemBytes + sizeof(uint32_t) * kBaseStack +
+           sizeof(uint16_t) * ((1 << kBaseDigitBits) + 2) +
+           sizeof(uint32_t) * ((1 << kBaseDigitBits) / 2 + 34) + 16;
 }
 
 }  // namespace ipsgpu

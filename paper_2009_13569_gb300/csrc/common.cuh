@@ -5,7 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/ipsgpu.h"
+#include "ipsgpu.h"
 
 namespace ipsgpu {
 
@@ -13,7 +13,7 @@ namespace ipsgpu {
 constexpr int kMaxClasses = 256;      // buckets per level incl. equality ones
 constexpr int kMaxSortSample = 4096;  // sample elements sorted in one CTA
 constexpr uint32_t kRBias = 1u << 30; // bias of the read pointer field
-constexpr int kBaseSmemBytes = 192 * 1024;  // element buffer of the base case
+constexpr int kBaseSmemBytes = 184 * 1024;  // element buffer of the base case
 
 // ------------------------------------------------------------ key types
 // Rec100 keys: bytes 0..7 big-endian in hi, bytes 8..9 big-endian in lo.
@@ -270,6 +270,47 @@ __device__ inline bool bounded_wait_eq(const volatile uint32_t *p, uint32_t want
         __nanosleep(64);
     }
     return *p == want;
+}
+
+// ---------------------------------------------------- TMA bulk copies
+// One-dimensional bulk copy global -> shared completed on an mbarrier
+// (cp.async.bulk with complete_tx).  Both addresses and the size must be
+// multiples of 16 bytes.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for phase `parity` of an mbarrier; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; it++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+            "r"(smem_addr(dst_smem)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
 }
 
 }  // namespace ipsgpu

@@ -21,9 +21,8 @@
 
 namespace ipsgpu {
 
-constexpr int kClassifyThreads = 512;
-constexpr int kClassifyTileBytes = 32 * 1024;
 constexpr int kSampleThreads = 512;
+constexpr uint32_t kMinSamplesPerBucket = 16;
 constexpr int kPermuteThreads = 256;
 constexpr int kAuxThreads = 256;
 
@@ -117,12 +116,15 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tree(LevelArgs a) {
         }
         __syncthreads();
     } else {
-        // sample size: alpha * C, alpha = max(1, alpha_scale * log2 n), at
-        // least C - 1, at most what one CTA sorts
+        // sample size: alpha * C, alpha = max(1, alpha_scale * log2 n)
+        // (Sec. 5), raised to at least kMinSamplesPerBucket per bucket so
+        // that children stay within the base-case capacity, at most what
+        // one CTA sorts
         const uint32_t C = sd.C;
         float alpha = a.alpha_scale * log2f((float)sd.n);
         if (alpha < 1.f) alpha = 1.f;
         uint32_t m = (uint32_t)(alpha * (float)C);
+        if (m < kMinSamplesPerBucket * C) m = kMinSamplesPerBucket * C;
         if (m < C - 1) m = C - 1;
         if (m > kMaxSortSample) m = kMaxSortSample;
         uint32_t P = 1;
@@ -207,139 +209,6 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tree(LevelArgs a) {
         st->logK = logK;
         st->eq = eq;
         st->B = eq ? 2 * K_ : K_;
-    }
-}
-
-// ------------------------------------------------------------------- K2
-// One CTA per stripe.  Tiles of kClassifyTileBytes are read into registers,
-// classified, grouped by class in shared memory, and appended to the k
-// buffer blocks (shared memory, b elements each).  Whenever a buffer block
-// fills, the full block is written to the next free block slot at the front
-// of the stripe; everything written lies in the part of the stripe that has
-// already been read (Sec. 3.1.2).  Output: per-class counts, the number of
-// full blocks, and the partially filled buffers (leftovers).
-template <class T>
-__global__ void __launch_bounds__(kClassifyThreads, 1) k_classify(LevelArgs a) {
-    typedef typename T::K K;
-    typedef typename T::E E;
-    constexpr int NT = kClassifyThreads;
-    constexpr int TILE = kClassifyTileBytes / T::D >= NT ? kClassifyTileBytes / T::D : NT;
-    constexpr int EPT = TILE / NT;
-    constexpr int NW = NT / 32;
-    extern __shared__ __align__(16) unsigned char smem[];
-    K *s_tree = reinterpret_cast<K *>(smem);
-    K *s_spl = s_tree + kMaxClasses;
-    E *tile = reinterpret_cast<E *>(s_spl + kMaxClasses);
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(tile + TILE);
-    uint32_t *off = cnt + kMaxClasses;
-    uint32_t *fill = off + kMaxClasses;
-    uint32_t *nful = fill + kMaxClasses;
-    uint32_t *nfo = nful + kMaxClasses;
-    uint32_t *tot = nfo + kMaxClasses;
-    uint32_t *wtmp = tot + kMaxClasses;            // 34 entries
-    uint8_t *cls8 = reinterpret_cast<uint8_t *>(wtmp + 34);
-    E *buf = reinterpret_cast<E *>(smem + (((size_t)(reinterpret_cast<unsigned char *>(cls8 + TILE) - smem) + 15) & ~(size_t)15));
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const StripeDesc sp = a.stripe[blockIdx.x];
-    const SegDesc sd = a.seg[sp.seg];
-    const SegState &st = a.st[sp.seg];
-    const uint32_t B = st.B;
-    const uint32_t b = sd.b;
-    const uint32_t lb = ilog2_floor(b);
-    LevelClassifier<T> cl;
-    load_classifier<T>(cl, a, sp.seg, sd, st, s_tree, s_spl);
-    for (uint32_t j = tid; j < kMaxClasses; j += NT) {
-        cnt[j] = 0;
-        fill[j] = 0;
-        tot[j] = 0;
-    }
-    E *segbase = reinterpret_cast<E *>(a.data) + sd.begin;
-    const uint64_t e0 = (uint64_t)sp.blk0 * b;
-    uint64_t e1 = (uint64_t)(sp.blk0 + sp.nblk) * b;
-    if (e1 > sd.n) e1 = sd.n;
-    E *out = segbase + e0;
-    uint32_t wblk = 0;
-    __syncthreads();
-
-    for (uint64_t t0 = e0; t0 < e1; t0 += TILE) {
-        const uint32_t tcount = (uint32_t)min((uint64_t)TILE, e1 - t0);
-        E v[EPT];
-        uint32_t c[EPT];
-        uint32_t r[EPT];
-#pragma unroll
-        for (int i = 0; i < EPT; i++) {
-            uint32_t li = i * NT + tid;
-            if (li < tcount) v[i] = segbase[t0 + li];
-        }
-#pragma unroll
-        for (int i = 0; i < EPT; i++) {
-            uint32_t li = i * NT + tid;
-            c[i] = li < tcount ? cl(v[i]) : 0xFFFFFFFFu;
-        }
-        // rank within the tile: warp-aggregated shared-memory counters
-#pragma unroll
-        for (int i = 0; i < EPT; i++) {
-            uint32_t peers = __match_any_sync(0xffffffffu, c[i]);
-            uint32_t leader = __ffs(peers) - 1;
-            uint32_t rank = 0;
-            if (c[i] != 0xFFFFFFFFu && lane == (int)leader)
-                rank = atomicAdd(&cnt[c[i]], (uint32_t)__popc(peers));
-            rank = __shfl_sync(0xffffffffu, rank, leader);
-            r[i] = rank + __popc(peers & ((1u << lane) - 1));
-        }
-        __syncthreads();
-        cta_exclusive_scan<uint32_t>(cnt, off, (int)B, wtmp);
-        for (uint32_t j = tid; j < B; j += NT) nful[j] = (fill[j] + cnt[j]) >> lb;
-        __syncthreads();
-        const uint32_t tfull = cta_exclusive_scan<uint32_t>(nful, nfo, (int)B, wtmp);
-        // group the tile by class in shared memory
-#pragma unroll
-        for (int i = 0; i < EPT; i++) {
-            if (c[i] != 0xFFFFFFFFu) {
-                uint32_t p = off[c[i]] + r[i];
-                tile[p] = v[i];
-                cls8[p] = (uint8_t)c[i];
-            }
-        }
-        // flush the old contents of buffers that fill up in this tile
-        for (uint32_t j = warp; j < B; j += NW) {
-            uint32_t f = fill[j];
-            if (nful[j] && f) {
-                E *dst = out + ((uint64_t)(wblk + nfo[j]) << lb);
-                const E *src = buf + ((size_t)j << lb);
-                for (uint32_t o = lane; o < f; o += 32) dst[o] = src[o];
-            }
-        }
-        __syncthreads();
-        // write grouped elements: complete blocks go to the stripe front,
-        // the remainder of each class goes to its buffer block
-        for (uint32_t p = tid; p < tcount; p += NT) {
-            uint32_t j = cls8[p];
-            uint32_t g = fill[j] + p - off[j];
-            uint32_t vb = g >> lb;
-            if (vb < nful[j])
-                out[((uint64_t)(wblk + nfo[j] + vb) << lb) + (g & (b - 1))] = tile[p];
-            else
-                buf[((size_t)j << lb) + (g - (nful[j] << lb))] = tile[p];
-        }
-        __syncthreads();
-        for (uint32_t j = tid; j < B; j += NT) {
-            fill[j] = fill[j] + cnt[j] - (nful[j] << lb);
-            tot[j] += cnt[j];
-            cnt[j] = 0;
-        }
-        wblk += tfull;
-        __syncthreads();
-    }
-    uint32_t *sc = a.scount + (size_t)blockIdx.x * kMaxClasses;
-    for (uint32_t j = tid; j < B; j += NT) sc[j] = tot[j];
-    if (tid == 0) a.sfull[blockIdx.x] = wblk;
-    E *left = reinterpret_cast<E *>(a.arena + sp.left_off);
-    for (uint32_t j = warp; j < B; j += NW) {
-        uint32_t f = fill[j];
-        for (uint32_t o = lane; o < f; o += 32)
-            left[((size_t)j << lb) + o] = buf[((size_t)j << lb) + o];
     }
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "base.cuh"
+#include "classify.cuh"
 #include "level.cuh"
 #include "sorter.h"
 
@@ -11,15 +12,7 @@ namespace ipsgpu {
 template <class T>
 struct OpsImpl {
     typedef typename T::K K;
-    static constexpr int kTile =
-        kClassifyTileBytes / T::D >= kClassifyThreads ? kClassifyTileBytes / T::D : kClassifyThreads;
-
-    static size_t classify_smem(const Sorter *s) {
-        size_t x = 2 * kMaxClasses * sizeof(K) + (size_t)kTile * T::D +
-                   sizeof(uint32_t) * (6 * kMaxClasses + 34) + kTile;
-        x = (x + 15) & ~(size_t)15;
-        return x + (size_t)kMaxClasses * s->b * T::D;
-    }
+    static size_t classify_smem(const Sorter *s) { return ClsSmem<T>::bytes(s->b); }
     static size_t sample_smem() {
         return (kMaxSortSample + kMaxClasses) * sizeof(K) + sizeof(uint32_t) * (2 * kMaxClasses + 34);
     }
@@ -47,7 +40,7 @@ struct OpsImpl {
         k_sample_tree<T><<<nseg, kSampleThreads, sample_smem(), st>>>(a);
         s->tend(st);
         s->tbegin(KK_CLASSIFY, 2 * lvl, st);
-        k_classify<T><<<nstripe, kClassifyThreads, classify_smem(s), st>>>(a);
+        k_classify<T><<<nstripe, ClsCfg<T>::NT, classify_smem(s), st>>>(a);
         s->tend(st);
         s->tbegin(KK_PREP, 0, st);
         k_prep<<<nseg, kAuxThreads, 0, st>>>(a);

@@ -142,3 +142,35 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(ipsgpu.IpsgpuError) as e:
         ipsgpu.Sorter("f64", algo=ipsgpu.RADIX)
     assert e.value.code == ipsgpu.E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("dtype,spl_vals", [
+    ("u64", [0, 1, 1 << 63, (1 << 64) - 2, (1 << 64) - 1]),
+    ("u64", [5]),
+    ("u64", [(1 << 64) - 1] * 3),
+    ("u32", [0, 7, (1 << 31), (1 << 32) - 2, (1 << 32) - 1]),
+    ("u32", [(1 << 32) - 3, (1 << 32) - 2]),
+])
+@pytest.mark.parametrize("eq", [False, True])
+def test_partition_level_extreme_splitters(dtype, spl_vals, eq):
+    # splitters at the ends of the key range and keys outside the splitter
+    # range exercise every clamp of the classifier's start-node table
+    n = 120_001
+    host = inputs.generate("uniform", dtype, n, seed=len(spl_vals) + eq)
+    a = inputs.to_numpy(host, dtype)
+    a[::97] = spl_vals[0]
+    a[1::89] = spl_vals[-1]
+    a[2::83] = 0
+    a[3::79] = np.iinfo(a.dtype).max
+    host = inputs.from_numpy(a, dtype)
+    spl = np.array(sorted(spl_vals), dtype=a.dtype)
+    _run_level(dtype, host, spl, eq)
+
+
+@pytest.mark.parametrize("dist", ["exponential", "zipf", "almostsorted", "eightdup"])
+def test_partition_level_clustered_splitters(dist):
+    host = _input("u64", 200_003, dist, seed=17)
+    spl = _splitters(host, "u64", 255, seed=4)
+    _run_level("u64", host, spl, False)
+    spl = _splitters(host, "u64", 127, seed=5)
+    _run_level("u64", host, spl, True)

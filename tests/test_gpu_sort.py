@@ -47,7 +47,7 @@ def test_sort_radix_variant(dtype, dist):
     assert_sorted_parity(got, inputs.to_numpy(host, dtype), dtype)
 
 
-@pytest.mark.parametrize("n", [0, 1, 2, 3, 31, 32, 33, 63, 64, 65, 1000, 24575, 24576, 24577,
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 31, 32, 33, 63, 64, 65, 1000, 23551, 23552, 23553, 24577,
                                49_155, 2 ** 17, 2 ** 17 + 1])
 def test_sort_sizes(n):
     host = inputs.generate("uniform", "u64", n, seed=n + 11)
