@@ -174,6 +174,30 @@ const char *ipsgpu_kernel_name(int kind);
  * IPSGPU_E_TIMEOUT in the status word (read it with ipsgpu_status). */
 int ipsgpu_debug_bounded_wait(ipsgpu_sorter *s, uint32_t spin_limit, void *stream);
 
+/* One partitioning level with given splitters, like ipsgpu_partition_level,
+ * for callers that cannot allocate memory: code running while a CUDA graph is
+ * being captured, code inside an allocator or memory-pool callback, or a
+ * service that reserves all device memory up front.  The paper has no
+ * counterpart; this is a property of the library, not of the method.
+ *   - No sorter is needed and nothing is allocated: all scratch lives in a
+ *     fixed device array inside the library (about 8.3 MiB, held by every GPU
+ *     that loads the library until the process exits).  The caller passes the
+ *     data, the splitters and d_bucket_begin exactly as for
+ *     ipsgpu_partition_level; dtype is an ipsgpu_dtype.
+ *   - Limits: n <= 2^32 - 1 elements and B <= 256 classes; larger requests
+ *     return IPSGPU_E_INVAL.
+ *   - The first call on a device looks up the array's device address and sets
+ *     kernel attributes; make that first call before any stream capture.
+ *   - Every call uses the same array and leaves its contents behind, so calls
+ *     whose work overlaps on the GPU (other streams, other host threads) race:
+ *     serialize them.
+ *   - A kernel-side error (a bounded wait that ran out, an inconsistent count)
+ *     is reported by writing ~0 into d_bucket_begin[B], which otherwise
+ *     equals n. */
+int ipsgpu_partition_level_noalloc(int dtype, void *d_data, uint64_t n, const void *d_splitters,
+                                   uint32_t num_splitters, int equal_buckets,
+                                   uint64_t *d_bucket_begin, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

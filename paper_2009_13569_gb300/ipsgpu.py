@@ -58,6 +58,7 @@ def load():
                                       ctypes.POINTER(ctypes.c_double), i32]),
         "ipsgpu_kernel_name": (ctypes.c_char_p, [i32]),
         "ipsgpu_debug_bounded_wait": (i32, [vp, u32, vp]),
+        "ipsgpu_partition_level_noalloc": (i32, [i32, vp, u64, vp, u32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -73,7 +74,7 @@ def exported_symbols():
         "ipsgpu_sorter_create", "ipsgpu_sorter_destroy", "ipsgpu_scratch_bytes", "ipsgpu_sort",
         "ipsgpu_partition_level", "ipsgpu_radix_level", "ipsgpu_classify", "ipsgpu_status",
         "ipsgpu_strerror", "ipsgpu_set_timing", "ipsgpu_kernel_stats", "ipsgpu_kernel_name",
-        "ipsgpu_debug_bounded_wait",
+        "ipsgpu_debug_bounded_wait", "ipsgpu_partition_level_noalloc",
     ]
 
 
@@ -84,6 +85,15 @@ def strerror(code):
 def _check(rc, what):
     if rc != OK:
         raise IpsgpuError(rc, what)
+
+
+def partition_level_noalloc(dtype, ptr, n, spl_ptr, num_splitters, equal_buckets, bb_ptr,
+                            stream=0):
+    """ipsgpu_partition_level_noalloc: one level without a sorter and without
+    allocating (scratch is a fixed device array inside the library)."""
+    _check(load().ipsgpu_partition_level_noalloc(DTYPES[dtype], ptr, n, spl_ptr, num_splitters,
+                                                 1 if equal_buckets else 0, bb_ptr, stream),
+           "ipsgpu_partition_level_noalloc")
 
 
 def make_params(k=0, block_bytes=0, alpha_scale=0.0, base_case=0, seed=0, algo=SAMPLESORT,
