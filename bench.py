@@ -36,7 +36,7 @@ CPU_SAMPLE_LOG2 = 22
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--log2n", type=int, default=LOG2N)
@@ -101,7 +101,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, ValueError):
             self.proc = None
@@ -134,6 +134,29 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+# DRAM traffic of the dominant kernel per element of a launch, from the ncu
+# capture summarised in profiles/ (dram__bytes_read.sum + dram__bytes_write.sum
+# of one launch divided by the elements it processed).  It is only valid for
+# the kernel source it was measured on, identified by its sha256; otherwise
+# the bench reports traffic as null.
+NCU_TRAFFIC = {
+    "classify": {"bytes_per_elem": 15.1198,
+                 "source": "paper_2009_13569_gb300/csrc/classify.cuh",
+                 "sha256": "afc09346e15ad1910a79def3a02ff9f1c1171deb2be3c34107e535f22ece0623"},
+}
+
+
+def _traffic(kernel, elems_per_launch):
+    import hashlib
+    t = NCU_TRAFFIC.get(kernel)
+    if not t:
+        return None
+    with open(os.path.join(ROOT, t["source"]), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
+            return None
+    return t["bytes_per_elem"] * elems_per_launch
 
 
 def _peak_hbm():
@@ -241,7 +264,8 @@ def run_ours(args):
         l, kms, by = kinds[dom]
         ach = (by / l) / (kms / l * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": None, "peak_source": peak_kind,
+                "frac": ach / peak, "traffic": _traffic(dom, by / l / 16.0),
+                "peak_source": peak_kind,
                 "bytes_per_launch": by / l, "ms_per_launch": kms / l}
     per_kernel = {k: {"launches": v[0] // args.steps, "ms": v[1] / args.steps,
                       "GBps": (v[2] / v[1] / 1e6) if v[1] and v[2] else None}
