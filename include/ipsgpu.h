@@ -143,6 +143,45 @@ int ipsgpu_partition_level(ipsgpu_sorter *s, void *d_data, uint64_t n,
 int ipsgpu_radix_level(ipsgpu_sorter *s, void *d_data, uint64_t n, uint32_t shift,
                        uint32_t bits, uint64_t *d_bucket_begin, void *stream);
 
+/* Sort many independent arrays in one call (segmented sort): segment i is
+ * d_data[d_offsets[i] .. d_offsets[i+1]) for i < num_segments, sorted in
+ * place exactly as ipsgpu_sort would sort it alone (Sec. 3.2 recursion run
+ * breadth-first over all segments of the batch at once).
+ *   - d_offsets: num_segments + 1 u64 element offsets in device memory,
+ *     non-decreasing, the last one <= n; n is the length of d_data.  A
+ *     segment that violates this is left untouched and E_INVAL is recorded
+ *     in the status word.  Elements outside every segment are not touched.
+ *   - Every level is planned on the device, so the call never synchronizes:
+ *     it enqueues a launch sequence that depends only on (n, num_segments)
+ *     and the sorter's parameters, and it can be captured into a CUDA graph
+ *     (or use ipsgpu_segmented_graph_create).  Unlike ipsgpu_sort it does not
+ *     look for already sorted or reversed inputs.
+ *   - Limits of one level: the sorter's segment, stripe, class and arena
+ *     capacities (ipsgpu_params.arena_bytes).  A level that exceeds one
+ *     records E_NOMEM in the status word and stops the recursion; the data
+ *     then still holds a permutation of every segment.
+ *   - Kernel-side errors go to the status word (ipsgpu_status).
+ * Errors: E_INVAL (NULL or misaligned pointers, n > 2^40), E_CUDA. */
+int ipsgpu_sort_segmented(ipsgpu_sorter *s, void *d_data, uint64_t n,
+                          const uint64_t *d_offsets, uint64_t num_segments, void *stream);
+
+/* A segmented sort captured once into an instantiated CUDA graph: the same
+ * launch sequence as ipsgpu_sort_segmented over fixed buffers (d_data,
+ * d_offsets), replayed by ipsgpu_graph_launch with one host call per batch.
+ * The graph reads the offsets and data at launch time, so the caller may
+ * refill both buffers between launches.  The graph uses the sorter's
+ * scratch: launches of graphs of one sorter, and its other calls, must not
+ * overlap on the GPU.  Errors: as ipsgpu_sort_segmented, plus E_CUDA if the
+ * capture or instantiation fails. */
+typedef struct ipsgpu_graph ipsgpu_graph;
+int ipsgpu_segmented_graph_create(ipsgpu_sorter *s, void *d_data, uint64_t n,
+                                  const uint64_t *d_offsets, uint64_t num_segments,
+                                  ipsgpu_graph **out);
+int ipsgpu_graph_launch(ipsgpu_graph *g, void *stream);
+/* Number of nodes (kernel launches and memsets) in the captured graph. */
+int ipsgpu_graph_nodes(ipsgpu_graph *g, uint64_t *nodes);
+int ipsgpu_graph_destroy(ipsgpu_graph *g);
+
 /* The classification rule alone (Sec. 2 branchless tree, Algorithm 1):
  * writes class(d_data[i]) to d_class[i] (u32, device) without moving data.
  * Same splitter semantics and errors as ipsgpu_partition_level. */

@@ -76,7 +76,7 @@ __device__ __forceinline__ Key80 shfl_key<TRec100>(Key80 k, int src) {
 }
 
 // Sorts each listed segment (segs[2i] = begin, segs[2i+1] = n, n <= smax)
-// in place.  The segment is first staged into shared memory with cp.async
+// in place; the number of segments is *nsegs_dev if given, else nsegs_host.  The segment is first staged into shared memory with cp.async
 // (one round trip).  A pass over a range [a0, a0+len) then takes min/max and
 // a histogram of an MSD radix digit of (key - min) from shared memory, and
 // scatters the range by digit from its global copy (which equals the
@@ -86,8 +86,8 @@ __device__ __forceinline__ Key80 shfl_key<TRec100>(Key80 k, int src) {
 // a pending range always matches the shared one.
 template <class T>
 __global__ void __launch_bounds__(kBaseThreads, 1) k_base(unsigned char *data,
-                                                          const uint64_t *segs, uint32_t nsegs,
-                                                          int *status) {
+                                                          const uint64_t *segs, uint32_t nsegs_host,
+                                                          const uint32_t *nsegs_dev, int *status) {
     typedef typename T::E E;
     typedef typename T::K K;
     constexpr int ND = 1 << kBaseDigitBits;
@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(unsigned char *data,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = kBaseThreads / 32;
 
+    const uint32_t nsegs = nsegs_dev ? *nsegs_dev : nsegs_host;
     for (uint32_t si = blockIdx.x; si < nsegs; si += gridDim.x) {
         const uint64_t begin = segs[2 * si], n = segs[2 * si + 1];
         E *g = reinterpret_cast<E *>(data) + begin;

@@ -302,14 +302,22 @@ __global__ void __launch_bounds__(ClsCfg<T>::NT, 1) k_classify(LevelArgs a) {
     __shared__ __align__(8) uint64_t sh_bar;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const StripeDesc sp = a.stripe[blockIdx.x];
+    if (tid == 0) {
+        mbar_init(&sh_bar, 1);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    uint32_t parity = 0;
+    const uint32_t nstripe = lv_nstripe(a);
+    for (uint32_t sidx = blockIdx.x; sidx < nstripe; sidx += gridDim.x) {
+    __syncthreads();
+    const StripeDesc sp = a.stripe[sidx];
     const SegDesc sd = a.seg[sp.seg];
     const SegState &st = a.st[sp.seg];
     const uint32_t B = st.B;
     const uint32_t b = sd.b;
     const uint32_t lb = ilog2_floor(b);
     LevelClassifier<T> cl;
-    load_classifier<T>(cl, a, sp.seg, sd, st, s_tree, s_spl);
+    load_classifier<T>(cl, a, sd, st, s_tree, s_spl);
     for (uint32_t j = tid; j < kMaxClasses; j += NT) {
         cnt[j] = 0;
         fill[j] = 0;
@@ -326,10 +334,6 @@ __global__ void __launch_bounds__(ClsCfg<T>::NT, 1) k_classify(LevelArgs a) {
     // aligned interior lands on a 16-byte boundary for the bulk copy
     const unsigned char *gsrc = reinterpret_cast<const unsigned char *>(segbase + e0);
     E *stage = reinterpret_cast<E *>(stage_raw + ((uintptr_t)gsrc & 15));
-    if (tid == 0) {
-        mbar_init(&sh_bar, 1);
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    }
     __syncthreads();
     if (e0 < e1)
         tile_load(reinterpret_cast<unsigned char *>(stage), gsrc,
@@ -340,7 +344,6 @@ __global__ void __launch_bounds__(ClsCfg<T>::NT, 1) k_classify(LevelArgs a) {
         if (tid == 0) sh_cm = cm;
     }
 
-    uint32_t parity = 0;
     for (uint64_t t0 = e0; t0 < e1; t0 += TILE, parity ^= 1) {
         const uint32_t tcount = (uint32_t)min((uint64_t)TILE, e1 - t0);
         // [A] the tile is in shared memory (bounded wait on the bulk copy)
@@ -439,15 +442,16 @@ __global__ void __launch_bounds__(ClsCfg<T>::NT, 1) k_classify(LevelArgs a) {
     }
     cp_async_wait_all();
     __syncthreads();
-    uint32_t *sc = a.scount + (size_t)blockIdx.x * kMaxClasses;
+    uint32_t *sc = a.scount + sp.cnt_off;
     for (uint32_t j = tid; j < B; j += NT) sc[j] = tot[j];
-    if (tid == 0) a.sfull[blockIdx.x] = sh_wblk;
+    if (tid == 0) a.sfull[sidx] = sh_wblk;
     E *left = reinterpret_cast<E *>(a.arena + sp.left_off);
     for (uint32_t j = warp; j < B; j += NW) {
         const uint32_t f = fill[j];
         for (uint32_t o = lane; o < f; o += 32)
             left[((size_t)j << lb) + o] = buf[((size_t)j << lb) + o];
     }
+    }  // stripes
 }
 
 }  // namespace ipsgpu

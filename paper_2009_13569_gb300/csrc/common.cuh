@@ -117,76 +117,115 @@ struct TRec100 {
 };
 
 // ------------------------------------------------------------ level layouts
-// Host-planned description of one segment partitioned in a level launch.
+// Planned description of one segment partitioned in a level launch (written
+// by the host planner, or on the device for the segmented batch).
 struct SegDesc {
     uint64_t begin;      // element offset of the segment in the data array
     uint64_t n;          // elements
     uint32_t b;          // block size in elements
-    uint32_t C;          // class budget (power of two <= 256)
+    uint32_t C;          // class budget (power of two <= 256): bounds B
     uint32_t stripe0;    // first stripe of the segment
     uint32_t nstripes;
     uint32_t cta0;       // first block-permutation CTA of the segment
     uint32_t ncta;
-    uint64_t stage_off;  // arena byte offset of the cleanup staging area
+    uint64_t stage_off;  // arena bytes: cleanup staging (C blocks), then the overflow block
+    uint64_t arr_off;    // state-arena bytes: per-class arrays (SegArrays)
+    uint64_t key_off;    // key-arena bytes: tree[C] then splitters[C]
+    uint32_t cls0;       // first (segment, class) work item: prefix sum of C
     uint32_t mode;       // 0: sample splitters, 1: given splitters, 2: radix
     uint32_t radix_shift;
     uint32_t radix_bits;
     uint32_t nsplit;     // given splitters (mode 1)
     uint32_t eq_given;
-    uint32_t pad;
+    uint32_t cnt0;       // first per-class count entry of the segment's stripes
 };
 
-// Per-stripe plan (host) and output (device).
+// Per-stripe plan and outputs.
 struct StripeDesc {
     uint32_t seg;
     uint32_t blk0;       // first block of the stripe within its segment
     uint32_t nblk;       // blocks (the last one may be partial)
-    uint32_t pad;
-    uint64_t left_off;   // arena byte offset of this stripe's leftover buffers
+    uint32_t cnt_off;    // first entry of the stripe's per-class counts
+    uint64_t left_off;   // arena bytes: leftover buffer blocks (C blocks)
 };
 
-// Device-computed state of a segment during a level.
+// Device-computed header of a segment during a level.
 struct SegState {
     uint32_t K, B, logK, eq;
     uint32_t nslots;       // ceil(n / b)
     uint32_t nfull_slots;  // floor(n / b)
     uint32_t ovf_used;     // 1 if a block was written to the overflow block
     uint32_t pad;
-    uint64_t bucket_begin[kMaxClasses + 1];
-    unsigned long long ptr[kMaxClasses];  // (w << 32) | (r_excl + kRBias)
-    uint32_t readers[kMaxClasses];
-    uint32_t full[kMaxClasses];       // full blocks of each class
-    uint32_t dlm[kMaxClasses + 1];    // delimiters (blocks)
 };
+
+// Per-class arrays of a segment, C entries each, in the state arena:
+//   u64 bucket_begin[C+1] | u64 ptr[C] | u32 readers[C] | u32 full[C] |
+//   u32 dlm[C+1]
+// ptr[i] packs the write pointer w_i (high half) and the exclusive read
+// pointer r_i + 1 + kRBias (low half); dlm[i] is the delimiter (in blocks).
+struct SegArrays {
+    uint64_t *bb;
+    unsigned long long *ptr;
+    uint32_t *readers;
+    uint32_t *full;
+    uint32_t *dlm;
+};
+__host__ __device__ inline uint64_t seg_arrays_bytes(uint32_t C) {
+    return ((uint64_t)28 * C + 12 + 15) & ~(uint64_t)15;
+}
+__device__ inline SegArrays seg_arrays(unsigned char *sarr, const SegDesc &sd) {
+    unsigned char *p = sarr + sd.arr_off;
+    SegArrays r;
+    r.bb = reinterpret_cast<uint64_t *>(p);
+    r.ptr = reinterpret_cast<unsigned long long *>(p + 8 * (sd.C + 1));
+    r.readers = reinterpret_cast<uint32_t *>(p + 8 * (sd.C + 1) + 8 * sd.C);
+    r.full = r.readers + sd.C;
+    r.dlm = r.full + sd.C;
+    return r;
+}
 
 struct Move {
     uint32_t seg;
     uint32_t src, dst, len;  // block indices within the segment
 };
 
+// Work counts of a level when they live in device memory (segmented batch);
+// with cnt == nullptr the host-provided values in LevelArgs are used.
+struct LevelCounts {
+    uint32_t nseg, nstripe, ncta, ncls;
+};
+
 struct LevelArgs {
     unsigned char *data;
     const SegDesc *seg;
     SegState *st;
-    unsigned char *tree;      // [nseg][kMaxClasses] keys (BFS tree, index 1..K-1)
-    unsigned char *spl;       // [nseg][kMaxClasses] keys (padded splitters)
+    unsigned char *sarr;      // state arena (SegArrays)
+    unsigned char *keys;      // key arena (tree, splitters)
     const unsigned char *given_spl;  // mode 1: user splitters (elements)
     const StripeDesc *stripe;
-    uint32_t *scount;         // [nstripe][kMaxClasses]
+    uint32_t *scount;         // count arena: per stripe, C entries
     uint32_t *sfull;          // [nstripe] full blocks written by the stripe
-    unsigned char *arena;
-    unsigned char *ovf;       // [nseg][block bytes]
+    unsigned char *arena;     // leftovers, staging, overflow blocks
     Move *moves;
     uint32_t *nmoves;
     uint32_t move_cap;
     int *status;
-    uint32_t nseg, nstripe;
+    uint32_t nseg, nstripe, ncta, ncls;
+    const LevelCounts *cnt;
+    const uint32_t *cta_seg;
     uint32_t spin_limit;
     uint32_t pad;
     uint64_t seed;
     float alpha_scale;
-    uint32_t ovf_stride;      // bytes per overflow block slot
+    uint32_t pad2;
 };
+
+__device__ inline uint32_t lv_nseg(const LevelArgs &a) { return a.cnt ? a.cnt->nseg : a.nseg; }
+__device__ inline uint32_t lv_nstripe(const LevelArgs &a) {
+    return a.cnt ? a.cnt->nstripe : a.nstripe;
+}
+__device__ inline uint32_t lv_ncta(const LevelArgs &a) { return a.cnt ? a.cnt->ncta : a.ncta; }
+__device__ inline uint32_t lv_ncls(const LevelArgs &a) { return a.cnt ? a.cnt->ncls : a.ncls; }
 
 // ------------------------------------------------------------ helpers
 __device__ inline void set_status(int *status, int code) {

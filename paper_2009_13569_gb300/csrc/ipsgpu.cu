@@ -11,6 +11,7 @@
 #include <utility>
 #include <vector>
 
+#include "graph.cuh"
 #include "sorter.h"
 
 using namespace ipsgpu;
@@ -87,27 +88,31 @@ int resolve(const ipsgpu_params *p, int dtype, Resolved *r) {
 }
 
 struct Layout {
-    uint64_t seg, st, tree, stripe, scount, sfull, arena, ovf, moves, cta, res, base, misc;
+    uint64_t seg, st, sarr, keys, stripe, scount, sfull, arena, moves, cta, res, base, glist, misc;
     uint64_t total() const {
-        return seg + st + 2 * tree + stripe + scount + sfull + arena + ovf + moves + cta + res +
-               base + misc;
+        return seg + st + sarr + keys + stripe + scount + sfull + arena + moves + cta + res + base +
+               glist + misc;
     }
 };
 
+// Per-segment sizes: SegArrays of C classes fit 28 C + 32 bytes, the tree
+// and splitters 2 C keys + 16 bytes; both summed over at most cls_cap
+// classes and seg_cap segments.
 Layout layout(const Sorter &s, int key_bytes) {
     Layout L;
     L.seg = (uint64_t)s.seg_cap * sizeof(SegDesc);
     L.st = (uint64_t)s.seg_cap * sizeof(SegState);
-    L.tree = (uint64_t)s.seg_cap * kMaxClasses * key_bytes;
+    L.sarr = (uint64_t)28 * s.cls_cap + 32ull * s.seg_cap;
+    L.keys = (uint64_t)2 * s.cls_cap * key_bytes + 16ull * s.seg_cap;
     L.stripe = (uint64_t)s.stripe_cap * sizeof(StripeDesc);
-    L.scount = (uint64_t)s.stripe_cap * kMaxClasses * sizeof(uint32_t);
+    L.scount = (uint64_t)s.cnt_cap * sizeof(uint32_t);
     L.sfull = (uint64_t)s.stripe_cap * sizeof(uint32_t);
     L.arena = s.arena_bytes;
-    L.ovf = (uint64_t)s.seg_cap * align_up((uint64_t)s.b * s.ops->D, 16);
     L.moves = (uint64_t)s.move_cap * sizeof(Move);
     L.cta = (uint64_t)s.cta_cap * sizeof(uint32_t);
-    L.res = (uint64_t)s.seg_cap * kResStride * sizeof(uint64_t);
+    L.res = (uint64_t)s.host_seg_cap * kResStride * sizeof(uint64_t);
     L.base = (uint64_t)s.base_cap * 2 * sizeof(uint64_t);
+    L.glist = 2ull * s.seg_cap * sizeof(GList);
     L.misc = 256;
     return L;
 }
@@ -124,14 +129,18 @@ void apply(Sorter &s, const Resolved &r, int dtype) {
     s.arena_bytes = r.arena_bytes;
     s.b = block_elems(r.block_bytes, s.ops->D);
     s.smax = r.base_case;
+    Layout L = layout(s, s.ops->key_bytes);
+    s.sarr_bytes = L.sarr;
+    s.keys_bytes = L.keys;
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? IPSGPU_OK : IPSGPU_E_CUDA; }
 
 void free_all(Sorter &s) {
-    void *dev[] = {s.d_seg, s.d_st, s.d_tree, s.d_spl, s.d_stripe, s.d_scount, s.d_sfull,
-                   s.d_arena, s.d_ovf, s.d_moves, s.d_nmoves, s.d_status, s.d_cta_seg,
-                   s.d_res, s.d_base, s.d_flags, s.d_waitflag};
+    void *dev[] = {s.d_seg,    s.d_st,     s.d_sarr,   s.d_keys,    s.d_stripe,
+                   s.d_scount, s.d_sfull,  s.d_arena,  s.d_moves,   s.d_nmoves,
+                   s.d_status, s.d_cta_seg, s.d_res,   s.d_base,    s.d_flags,
+                   s.d_waitflag, s.d_glist, s.d_gcount};
     for (void *p : dev)
         if (p) cudaFree(p);
     void *host[] = {s.h_seg, s.h_stripe, s.h_cta_seg, s.h_res, s.h_base, s.h_flags};
@@ -161,8 +170,8 @@ uint32_t class_budget(const Sorter &s, uint64_t n) {
 }
 
 struct BatchPlan {
-    uint32_t nseg = 0, nstripe = 0, ncta = 0, nmoves = 0;
-    uint64_t arena = 0, elems = 0;
+    uint32_t nseg = 0, nstripe = 0, ncta = 0, nmoves = 0, ncls = 0, ncnt = 0;
+    uint64_t arena = 0, elems = 0, sarr = 0, keys = 0;
 };
 
 // Plans segments [i, j) of `list` into the pinned descriptors, up to the
@@ -189,12 +198,19 @@ size_t plan_batch(Sorter &s, const std::vector<Pending> &list, size_t i, uint32_
         if (p > nb) p = nb;
         uint64_t nc = (nb + blocks_per_cta - 1) / blocks_per_cta;
         if (nc < 1) nc = 1;
+        // arena: cleanup staging (C blocks) directly followed by the overflow
+        // block, then C leftover buffer blocks per stripe
+        const uint64_t stageb = align_up((uint64_t)C * s.b * D + (uint64_t)s.b * D, 256);
         const uint64_t bufb = align_up((uint64_t)C * s.b * D, 256);
-        const uint64_t arena_need = (p + 1) * bufb;
+        const uint64_t arena_need = stageb + p * bufb;
         const uint64_t move_need = 2 * (p + C) + 4;
-        if (bp.nseg + 1 > s.seg_cap || bp.nstripe + p > s.stripe_cap ||
+        const uint64_t sarr_need = seg_arrays_bytes(C);
+        const uint64_t keys_need = align_up(2ull * C * s.ops->key_bytes, 16);
+        if (bp.nseg + 1 > std::min(s.seg_cap, s.host_seg_cap) || bp.nstripe + p > s.stripe_cap ||
             bp.ncta + nc > s.cta_cap || bp.arena + arena_need > s.arena_bytes ||
-            bp.nmoves + move_need > s.move_cap) {
+            bp.nmoves + move_need > s.move_cap || bp.ncls + C > s.cls_cap ||
+            bp.ncnt + (uint64_t)C * p > s.cnt_cap || bp.sarr + sarr_need > s.sarr_bytes ||
+            bp.keys + keys_need > s.keys_bytes) {
             if (bp.nseg == 0) return (size_t)-1;  // one segment does not fit at all
             break;
         }
@@ -209,19 +225,23 @@ size_t plan_batch(Sorter &s, const std::vector<Pending> &list, size_t i, uint32_
         sd.cta0 = bp.ncta;
         sd.ncta = (uint32_t)nc;
         sd.stage_off = bp.arena;
+        sd.arr_off = bp.sarr;
+        sd.key_off = bp.keys;
+        sd.cls0 = bp.ncls;
+        sd.cnt0 = bp.ncnt;
         sd.mode = mode;
         sd.radix_shift = pd.shift;
         sd.radix_bits = radix_bits;
         sd.nsplit = nsplit;
         sd.eq_given = eq_given ? 1 : 0;
-        uint64_t off = bp.arena + bufb;
+        uint64_t off = bp.arena + stageb;
         for (uint64_t q = 0; q < p; q++) {
             StripeDesc &sp = s.h_stripe[bp.nstripe + q];
             sp.seg = bp.nseg;
             const uint64_t b0 = q * nb / p, b1 = (q + 1) * nb / p;
             sp.blk0 = (uint32_t)b0;
             sp.nblk = (uint32_t)(b1 - b0);
-            sp.pad = 0;
+            sp.cnt_off = (uint32_t)(bp.ncnt + q * C);
             sp.left_off = off;
             off += bufb;
         }
@@ -230,6 +250,10 @@ size_t plan_batch(Sorter &s, const std::vector<Pending> &list, size_t i, uint32_
         bp.nstripe += (uint32_t)p;
         bp.ncta += (uint32_t)nc;
         bp.nmoves += (uint32_t)move_need;
+        bp.ncls += C;
+        bp.ncnt += (uint32_t)(C * p);
+        bp.sarr += sarr_need;
+        bp.keys += keys_need;
         bp.elems += pd.n;
         bp.nseg++;
     }
@@ -293,7 +317,7 @@ int flush_base(Sorter &s, std::vector<Pending> &base, cudaStream_t st) {
         if (e == cudaSuccess) e = cudaEventRecord(s.h2d_done, st);
         if (e != cudaSuccess) return IPSGPU_E_CUDA;
         s.level_elems = elems;
-        e = s.ops->base(&s, s.data, s.d_base, (uint32_t)m, st);
+        e = s.ops->base(&s, s.data, s.d_base, (uint32_t)m, nullptr, (uint32_t)m, st);
         if (e != cudaSuccess) return IPSGPU_E_CUDA;
         i += m;
     }
@@ -350,9 +374,10 @@ int sort_impl(Sorter &s, unsigned char *data, uint64_t n, cudaStream_t st) {
             if (j == (size_t)-1 || j == i) return IPSGPU_E_INTERNAL;
             if ((rc = upload_plan(s, bp, st))) return rc;
             s.level_elems = bp.elems;
-            if ((e = s.ops->level(&s, bp.nseg, bp.nstripe, bp.ncta, nullptr, st)) != cudaSuccess)
-                return IPSGPU_E_CUDA;
-            if ((e = s.ops->pack(&s, bp.nseg, st)) != cudaSuccess) return IPSGPU_E_CUDA;
+            const LevelArgs a = s.args(bp.nseg, bp.nstripe, bp.ncta, bp.ncls, nullptr);
+            const LevelGrids g{bp.nseg, bp.nstripe, bp.ncta, bp.ncls};
+            if ((e = s.ops->level(&s, a, g, st)) != cudaSuccess) return IPSGPU_E_CUDA;
+            if ((e = s.ops->pack(&s, a, bp.nseg, st)) != cudaSuccess) return IPSGPU_E_CUDA;
             e = cudaMemcpyAsync(s.h_res, s.d_res, sizeof(uint64_t) * kResStride * bp.nseg,
                                 cudaMemcpyDeviceToHost, st);
             if (e != cudaSuccess) return IPSGPU_E_CUDA;
@@ -402,7 +427,9 @@ int single_level(Sorter &s, unsigned char *data, uint64_t n, uint32_t mode, uint
     if (j != 1) return IPSGPU_E_INVAL;
     if ((rc = upload_plan(s, bp, st))) return rc;
     s.level_elems = n;
-    return cuda_status(s.ops->level(&s, bp.nseg, bp.nstripe, bp.ncta, given, st));
+    const LevelArgs a = s.args(bp.nseg, bp.nstripe, bp.ncta, bp.ncls, given);
+    const LevelGrids g{bp.nseg, bp.nstripe, bp.ncta, bp.ncls};
+    return cuda_status(s.ops->level(&s, a, g, st));
 }
 
 }  // namespace
@@ -410,30 +437,33 @@ int single_level(Sorter &s, unsigned char *data, uint64_t n, uint32_t mode, uint
 // ------------------------------------------------------------- Sorter methods
 namespace ipsgpu {
 
-LevelArgs Sorter::args(uint32_t nseg, uint32_t nstripe, const unsigned char *given_spl) const {
+LevelArgs Sorter::args(uint32_t nseg, uint32_t nstripe, uint32_t ncta, uint32_t ncls,
+                       const unsigned char *given_spl) const {
     LevelArgs a;
     memset(&a, 0, sizeof a);
     a.data = data;
     a.seg = d_seg;
     a.st = d_st;
-    a.tree = d_tree;
-    a.spl = d_spl;
+    a.sarr = d_sarr;
+    a.keys = d_keys;
     a.given_spl = given_spl;
     a.stripe = d_stripe;
     a.scount = d_scount;
     a.sfull = d_sfull;
     a.arena = d_arena;
-    a.ovf = d_ovf;
     a.moves = d_moves;
     a.nmoves = d_nmoves;
     a.move_cap = move_cap;
     a.status = d_status;
     a.nseg = nseg;
     a.nstripe = nstripe;
+    a.ncta = ncta;
+    a.ncls = ncls;
+    a.cnt = nullptr;
+    a.cta_seg = d_cta_seg;
     a.spin_limit = spin_limit;
     a.seed = seed;
     a.alpha_scale = alpha_scale;
-    a.ovf_stride = (uint32_t)align_up((uint64_t)b * ops->D, 16);
     return a;
 }
 
@@ -514,13 +544,12 @@ int ipsgpu_sorter_create(const ipsgpu_params *params, int dtype, ipsgpu_sorter *
     };
     dm((void **)&s.d_seg, L.seg);
     dm((void **)&s.d_st, L.st);
-    dm((void **)&s.d_tree, L.tree);
-    dm((void **)&s.d_spl, L.tree);
+    dm((void **)&s.d_sarr, L.sarr);
+    dm((void **)&s.d_keys, L.keys);
     dm((void **)&s.d_stripe, L.stripe);
     dm((void **)&s.d_scount, L.scount);
     dm((void **)&s.d_sfull, L.sfull);
     dm((void **)&s.d_arena, L.arena);
-    dm((void **)&s.d_ovf, L.ovf);
     dm((void **)&s.d_moves, L.moves);
     dm((void **)&s.d_nmoves, 64);
     dm((void **)&s.d_status, 64);
@@ -529,6 +558,8 @@ int ipsgpu_sorter_create(const ipsgpu_params *params, int dtype, ipsgpu_sorter *
     dm((void **)&s.d_base, L.base);
     dm((void **)&s.d_flags, 64);
     dm((void **)&s.d_waitflag, 64);
+    dm((void **)&s.d_glist, L.glist);
+    dm((void **)&s.d_gcount, 64);
     hm((void **)&s.h_seg, L.seg);
     hm((void **)&s.h_stripe, L.stripe);
     hm((void **)&s.h_cta_seg, L.cta);
@@ -591,8 +622,9 @@ int ipsgpu_partition_level(ipsgpu_sorter *h, void *d_data, uint64_t n, const voi
     rc = single_level(s, (unsigned char *)d_data, n, 1, num_splitters, equal_buckets, 0, 0,
                       (const unsigned char *)d_splitters, st);
     if (rc) return rc;
-    return cuda_status(cudaMemcpyAsync(d_bucket_begin, s.d_st[0].bucket_begin,
-                                       sizeof(uint64_t) * (B + 1), cudaMemcpyDeviceToDevice, st));
+    // the single segment's SegArrays start the state arena: bucket_begin first
+    return cuda_status(cudaMemcpyAsync(d_bucket_begin, s.d_sarr, sizeof(uint64_t) * (B + 1),
+                                       cudaMemcpyDeviceToDevice, st));
 }
 
 int ipsgpu_radix_level(ipsgpu_sorter *h, void *d_data, uint64_t n, uint32_t shift, uint32_t bits,
@@ -611,8 +643,152 @@ int ipsgpu_radix_level(ipsgpu_sorter *h, void *d_data, uint64_t n, uint32_t shif
     if (rc) return rc;
     rc = single_level(s, (unsigned char *)d_data, n, 2, 0, 0, shift, bits, nullptr, st);
     if (rc) return rc;
-    return cuda_status(cudaMemcpyAsync(d_bucket_begin, s.d_st[0].bucket_begin,
-                                       sizeof(uint64_t) * (B + 1), cudaMemcpyDeviceToDevice, st));
+    // the single segment's SegArrays start the state arena: bucket_begin first
+    return cuda_status(cudaMemcpyAsync(d_bucket_begin, s.d_sarr, sizeof(uint64_t) * (B + 1),
+                                       cudaMemcpyDeviceToDevice, st));
+}
+
+// Level count of a device-planned batch over at most n elements: radix
+// consumes kbits key bits per level; samplesort shrinks a segment of m
+// elements by its class budget per level (expected), plus slack levels for
+// children that an unlucky sample left above the base-case size.
+static int graph_levels(const Sorter &s, uint64_t n) {
+    const uint32_t kbits = (uint32_t)__builtin_ctz(s.k);
+    if (s.algo == IPSGPU_RADIX) {
+        const uint32_t keybits = s.ops->D == 4 ? 32 : 64;
+        return (int)((keybits + kbits - 1) / kbits);
+    }
+    int L = 0;
+    for (uint64_t m = n; m > s.smax; L++) {
+        const uint32_t C = class_budget(s, m);
+        m = (m + C - 1) / C;
+    }
+    return L + 3;
+}
+
+static int segmented_impl(Sorter &s, unsigned char *data, uint64_t n, const uint64_t *d_offsets,
+                          uint64_t nseg, cudaStream_t st) {
+    s.data = data;
+    s.level_elems = n;
+    GraphArgs ga;
+    memset(&ga, 0, sizeof ga);
+    ga.lv = s.args(0, 0, 0, 0, nullptr);
+    ga.counts = reinterpret_cast<LevelCounts *>(s.d_gcount);
+    ga.list_count[0] = s.d_gcount + 4;
+    ga.list_count[1] = s.d_gcount + 5;
+    ga.base_count = s.d_gcount + 6;
+    ga.invalid = s.d_gcount + 7;
+    ga.list[0] = reinterpret_cast<GList *>(s.d_glist);
+    ga.list[1] = ga.list[0] + s.seg_cap;
+    ga.base_list = s.d_base;
+    ga.offsets = d_offsets;
+    ga.nseg_in = nseg;
+    ga.n_total = n;
+    ga.list_cap = s.seg_cap;
+    ga.base_cap = s.base_cap;
+    ga.seg_cap = s.seg_cap;
+    ga.stripe_cap = s.stripe_cap;
+    ga.cta_cap = s.cta_cap;
+    ga.cls_cap = s.cls_cap;
+    ga.cnt_cap = s.cnt_cap;
+    ga.smax = s.smax;
+    ga.k = s.k;
+    ga.b = s.b;
+    ga.nsm = (uint32_t)s.nsm;
+    ga.kbits = (uint32_t)__builtin_ctz(s.k);
+    ga.keybits = s.ops->D == 4 ? 32 : 64;
+    ga.arena_bytes = s.arena_bytes;
+    ga.sarr_bytes = s.sarr_bytes;
+    ga.keys_bytes = s.keys_bytes;
+    ga.algo = s.algo == IPSGPU_RADIX ? 1 : 0;
+    ga.levels = graph_levels(s, n);
+    return cuda_status(s.ops->segmented(&s, ga, st));
+}
+
+static int check_segmented(ipsgpu_sorter *h, void *d_data, uint64_t n, const uint64_t *d_offsets,
+                           uint64_t nseg) {
+    if (!h) return IPSGPU_E_INVAL;
+    if (n > (1ull << 40) || nseg > 0xFFFFFFFFull) return IPSGPU_E_INVAL;
+    if (nseg > 0 && (!d_offsets || ((uintptr_t)d_offsets % 8))) return IPSGPU_E_INVAL;
+    if (n > 0 && nseg > 0) return check_data(h->s, d_data);
+    return IPSGPU_OK;
+}
+
+int ipsgpu_sort_segmented(ipsgpu_sorter *h, void *d_data, uint64_t n, const uint64_t *d_offsets,
+                          uint64_t num_segments, void *stream) {
+    int rc = check_segmented(h, d_data, n, d_offsets, num_segments);
+    if (rc) return rc;
+    if (n < 2 || num_segments == 0) return IPSGPU_OK;
+    return segmented_impl(h->s, (unsigned char *)d_data, n, d_offsets, num_segments,
+                          (cudaStream_t)stream);
+}
+
+struct ipsgpu_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+int ipsgpu_segmented_graph_create(ipsgpu_sorter *h, void *d_data, uint64_t n,
+                                  const uint64_t *d_offsets, uint64_t num_segments,
+                                  ipsgpu_graph **out) {
+    if (!out) return IPSGPU_E_INVAL;
+    *out = nullptr;
+    int rc = check_segmented(h, d_data, n, d_offsets, num_segments);
+    if (rc) return rc;
+    Sorter &s = h->s;
+    ipsgpu_graph *g = new (std::nothrow) ipsgpu_graph;
+    if (!g) return IPSGPU_E_NOMEM;
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        delete g;
+        return IPSGPU_E_CUDA;
+    }
+    const bool timing = s.timing;
+    s.timing = false;  // no event records inside the graph
+    rc = IPSGPU_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        rc = IPSGPU_E_CUDA;
+    } else {
+        if (n >= 2 && num_segments > 0)
+            rc = segmented_impl(s, (unsigned char *)d_data, n, d_offsets, num_segments, cs);
+        else
+            rc = cuda_status(cudaMemsetAsync(s.d_gcount, 0, sizeof(uint32_t), cs));  // an empty graph node
+        cudaError_t e = cudaStreamEndCapture(cs, &g->graph);
+        if (rc == IPSGPU_OK && e != cudaSuccess) rc = IPSGPU_E_CUDA;
+    }
+    s.timing = timing;
+    if (rc == IPSGPU_OK && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) rc = IPSGPU_E_CUDA;
+    cudaStreamDestroy(cs);
+    if (rc) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        cudaGetLastError();
+        return rc;
+    }
+    *out = g;
+    return IPSGPU_OK;
+}
+
+int ipsgpu_graph_launch(ipsgpu_graph *g, void *stream) {
+    if (!g || !g->exec) return IPSGPU_E_INVAL;
+    return cuda_status(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+}
+
+int ipsgpu_graph_nodes(ipsgpu_graph *g, uint64_t *nodes) {
+    if (!g || !g->graph || !nodes) return IPSGPU_E_INVAL;
+    size_t cnt = 0;
+    if (cudaGraphGetNodes(g->graph, nullptr, &cnt) != cudaSuccess) return IPSGPU_E_CUDA;
+    *nodes = cnt;
+    return IPSGPU_OK;
+}
+
+int ipsgpu_graph_destroy(ipsgpu_graph *g) {
+    if (!g) return IPSGPU_E_INVAL;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return IPSGPU_OK;
 }
 
 int ipsgpu_classify(ipsgpu_sorter *h, const void *d_data, uint64_t n, const void *d_splitters,
@@ -640,7 +816,8 @@ int ipsgpu_classify(ipsgpu_sorter *h, const void *d_data, uint64_t n, const void
     bp.nseg = 1;
     if ((rc = upload_plan(s, bp, st))) return rc;
     s.level_elems = n;
-    return cuda_status(s.ops->classify_ids(&s, (const unsigned char *)d_splitters, d_class, st));
+    const LevelArgs a = s.args(1, 0, 0, (uint32_t)B, (const unsigned char *)d_splitters);
+    return cuda_status(s.ops->classify_ids(&s, a, d_class, st));
 }
 
 int ipsgpu_status(ipsgpu_sorter *h, void *stream) {
@@ -679,7 +856,7 @@ int ipsgpu_set_timing(ipsgpu_sorter *h, int enable) {
 static const char *kKindNames[KK_COUNT] = {"detect", "reverse", "sample_tree", "classify",
                                            "prep",   "fixup",   "permute",     "stage",
                                            "fill",   "pack",    "base_case",   "classify_ids",
-                                           "debug_wait"};
+                                           "debug_wait", "plan"};
 
 const char *ipsgpu_kernel_name(int kind) {
     return (kind >= 0 && kind < KK_COUNT) ? kKindNames[kind] : "";

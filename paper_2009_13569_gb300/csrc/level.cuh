@@ -3,7 +3,8 @@
 //   k_sample_tree  sampling, splitter selection, dedupe, branchless tree
 //                  (Sec. 3.1.1, Sec. 2)
 //   k_classify     classification into per-bucket buffer blocks, full blocks
-//                  flushed to the front of the stripe (Sec. 3.1.2)
+//                  flushed to the front of the stripe (Sec. 3.1.2;
+//                  classify.cuh)
 //   k_prep         bucket sizes -> prefix sum -> delimiters, per-bucket
 //                  (write, read) pointers, stripe-boundary fix-up plan
 //                  (Sec. 3.1.3, first part)
@@ -15,6 +16,9 @@
 //   k_stage/k_fill cleanup of bucket heads and tails from the overflowing
 //                  last block, the leftover buffer blocks and the overflow
 //                  block (Sec. 3.1.4)
+// Every kernel loops over its work items (segments, stripes, CTAs or
+// (segment, class) pairs), so the same kernels serve a host-planned batch
+// and a device-planned one whose counts live in device memory.
 #pragma once
 
 #include "common.cuh"
@@ -44,10 +48,19 @@ struct LevelClassifier {
 };
 
 template <class T>
+__device__ __forceinline__ const typename T::K *seg_tree(const LevelArgs &a, const SegDesc &sd) {
+    return reinterpret_cast<const typename T::K *>(a.keys + sd.key_off);
+}
+template <class T>
+__device__ __forceinline__ const typename T::K *seg_spl(const LevelArgs &a, const SegDesc &sd) {
+    return reinterpret_cast<const typename T::K *>(a.keys + sd.key_off) + sd.C;
+}
+
+// Copies the segment's tree and splitters into shared memory; callers sync.
+template <class T>
 __device__ __forceinline__ void load_classifier(LevelClassifier<T> &c, const LevelArgs &a,
-                                                uint32_t s, const SegDesc &sd,
-                                                const SegState &st, typename T::K *s_tree,
-                                                typename T::K *s_spl) {
+                                                const SegDesc &sd, const SegState &st,
+                                                typename T::K *s_tree, typename T::K *s_spl) {
     typedef typename T::K K;
     c.radix = sd.mode == 2;
     c.shift = sd.radix_shift;
@@ -57,8 +70,8 @@ __device__ __forceinline__ void load_classifier(LevelClassifier<T> &c, const Lev
     c.tree = s_tree;
     c.spl = s_spl;
     if (!c.radix) {
-        const K *gt = reinterpret_cast<const K *>(a.tree) + (size_t)s * kMaxClasses;
-        const K *gs = reinterpret_cast<const K *>(a.spl) + (size_t)s * kMaxClasses;
+        const K *gt = seg_tree<T>(a, sd);
+        const K *gs = seg_spl<T>(a, sd);
         for (uint32_t i = threadIdx.x; i < st.K; i += blockDim.x) {
             s_tree[i] = gt[i];
             s_spl[i] = gs[i];
@@ -81,134 +94,137 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tree(LevelArgs a) {
     K *cand = smp + kMaxSortSample;                             // kMaxClasses
     uint32_t *flag = reinterpret_cast<uint32_t *>(cand + kMaxClasses);  // kMaxClasses
     uint32_t *pos = flag + kMaxClasses;                         // kMaxClasses
-    uint32_t *wtmp = pos + kMaxClasses;                         // 33
-    __shared__ uint32_t sh_m, sh_eq, sh_d;
-
-    const uint32_t s = blockIdx.x;
-    const SegDesc sd = a.seg[s];
-    SegState *st = a.st + s;
+    uint32_t *wtmp = pos + kMaxClasses;                         // 34
+    __shared__ uint32_t sh_eq, sh_d;
     const int tid = threadIdx.x;
-    const uint32_t b = sd.b;
-    if (tid == 0) {
-        st->nslots = (uint32_t)((sd.n + b - 1) / b);
-        st->nfull_slots = (uint32_t)(sd.n / b);
-        st->ovf_used = 0;
-    }
-    if (sd.mode == 2) {
-        if (tid == 0) {
-            st->K = 1u << sd.radix_bits;
-            st->B = 1u << sd.radix_bits;
-            st->logK = sd.radix_bits;
-            st->eq = 0;
-        }
-        return;
-    }
-    K *gtree = reinterpret_cast<K *>(a.tree) + (size_t)s * kMaxClasses;
-    K *gspl = reinterpret_cast<K *>(a.spl) + (size_t)s * kMaxClasses;
-    const E *base = reinterpret_cast<const E *>(a.data) + sd.begin;
+    const uint32_t nseg = lv_nseg(a);
 
-    if (sd.mode == 1) {
-        const E *g = reinterpret_cast<const E *>(a.given_spl);
-        for (uint32_t j = tid; j < sd.nsplit; j += blockDim.x) cand[j] = T::key(g[j]);
+    for (uint32_t s = blockIdx.x; s < nseg; s += gridDim.x) {
+        const SegDesc sd = a.seg[s];
+        SegState *st = a.st + s;
+        const uint32_t b = sd.b;
         if (tid == 0) {
-            sh_d = sd.nsplit;
-            sh_eq = sd.eq_given;
+            st->nslots = (uint32_t)((sd.n + b - 1) / b);
+            st->nfull_slots = (uint32_t)(sd.n / b);
+            st->ovf_used = 0;
         }
-        __syncthreads();
-    } else {
-        // sample size: alpha * C, alpha = max(1, alpha_scale * log2 n)
-        // (Sec. 5), raised to at least kMinSamplesPerBucket per bucket so
-        // that children stay within the base-case capacity, at most what
-        // one CTA sorts
-        const uint32_t C = sd.C;
-        float alpha = a.alpha_scale * log2f((float)sd.n);
-        if (alpha < 1.f) alpha = 1.f;
-        uint32_t m = (uint32_t)(alpha * (float)C);
-        if (m < kMinSamplesPerBucket * C) m = kMinSamplesPerBucket * C;
-        if (m < C - 1) m = C - 1;
-        if (m > kMaxSortSample) m = kMaxSortSample;
-        uint32_t P = 1;
-        while (P < m) P <<= 1;
-        const uint64_t sseed = a.seed ^ (sd.begin * 0xD1B54A32D192ED03ull) ^ (sd.n << 17);
-        for (uint32_t t = tid; t < P; t += blockDim.x) {
-            if (t < m) {
-                uint64_t idx = splitmix64(sseed + t * 0x9E3779B97F4A7C15ull) % sd.n;
-                smp[t] = T::key(base[idx]);
-            } else {
-                smp[t] = T::max_key();
+        if (sd.mode == 2) {
+            if (tid == 0) {
+                st->K = 1u << sd.radix_bits;
+                st->B = 1u << sd.radix_bits;
+                st->logK = sd.radix_bits;
+                st->eq = 0;
             }
+            continue;
         }
-        __syncthreads();
-        // bitonic sort of smp[0..P)
-        for (uint32_t k = 2; k <= P; k <<= 1) {
-            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                for (uint32_t i = tid; i < P / 2; i += blockDim.x) {
-                    uint32_t lo = 2 * j * (i / j) + (i % j);
-                    uint32_t hi = lo + j;
-                    bool up = (lo & k) == 0;
-                    K x = smp[lo], y = smp[hi];
-                    if ((y < x) == up) {
-                        smp[lo] = y;
-                        smp[hi] = x;
+        K *gtree = reinterpret_cast<K *>(a.keys + sd.key_off);
+        K *gspl = gtree + sd.C;
+        const E *base = reinterpret_cast<const E *>(a.data) + sd.begin;
+
+        if (sd.mode == 1) {
+            const E *g = reinterpret_cast<const E *>(a.given_spl);
+            for (uint32_t j = tid; j < sd.nsplit; j += blockDim.x) cand[j] = T::key(g[j]);
+            if (tid == 0) {
+                sh_d = sd.nsplit;
+                sh_eq = sd.eq_given;
+            }
+            __syncthreads();
+        } else {
+            // sample size: alpha * C, alpha = max(1, alpha_scale * log2 n)
+            // (Sec. 5), raised to at least kMinSamplesPerBucket per bucket
+            // so that children stay within the base-case capacity, at most
+            // what one CTA sorts
+            const uint32_t C = sd.C;
+            float alpha = a.alpha_scale * log2f((float)sd.n);
+            if (alpha < 1.f) alpha = 1.f;
+            uint32_t m = (uint32_t)(alpha * (float)C);
+            if (m < kMinSamplesPerBucket * C) m = kMinSamplesPerBucket * C;
+            if (m < C - 1) m = C - 1;
+            if (m > kMaxSortSample) m = kMaxSortSample;
+            uint32_t P = 1;
+            while (P < m) P <<= 1;
+            const uint64_t sseed = a.seed ^ (sd.begin * 0xD1B54A32D192ED03ull) ^ (sd.n << 17);
+            for (uint32_t t = tid; t < P; t += blockDim.x) {
+                if (t < m) {
+                    uint64_t idx = splitmix64(sseed + t * 0x9E3779B97F4A7C15ull) % sd.n;
+                    smp[t] = T::key(base[idx]);
+                } else {
+                    smp[t] = T::max_key();
+                }
+            }
+            __syncthreads();
+            // bitonic sort of smp[0..P)
+            for (uint32_t k = 2; k <= P; k <<= 1) {
+                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                    for (uint32_t i = tid; i < P / 2; i += blockDim.x) {
+                        uint32_t lo = 2 * j * (i / j) + (i % j);
+                        uint32_t hi = lo + j;
+                        bool up = (lo & k) == 0;
+                        K x = smp[lo], y = smp[hi];
+                        if ((y < x) == up) {
+                            smp[lo] = y;
+                            smp[hi] = x;
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            // equidistant splitters, dedupe.  If any duplicate was found the
+            // level uses equality buckets: the splitters are picked again for
+            // C/2 leaves so that the 2K classes still fit the budget C.
+            uint32_t Cc = C;
+            for (int attempt = 0; attempt < 2; attempt++) {
+                const uint32_t ns = Cc - 1;
+                for (uint32_t j = tid; j < ns; j += blockDim.x)
+                    cand[j] = smp[((uint64_t)(j + 1) * m) / Cc - 1];
+                __syncthreads();
+                for (uint32_t j = tid; j < ns; j += blockDim.x)
+                    flag[j] = (j == 0 || cand[j - 1] < cand[j]) ? 1u : 0u;
+                __syncthreads();
+                uint32_t d = cta_exclusive_scan<uint32_t>(flag, pos, (int)ns, wtmp);
+                K keep = T::max_key();
+                bool mine = false;
+                uint32_t mypos = 0;
+                // ns <= 255 < blockDim.x: each thread holds at most one entry
+                for (uint32_t j = tid; j < ns; j += blockDim.x) {
+                    if (flag[j]) {
+                        keep = cand[j];
+                        mine = true;
+                        mypos = pos[j];
                     }
                 }
                 __syncthreads();
-            }
-        }
-        // equidistant splitters, dedupe.  If any duplicate was found the
-        // level uses equality buckets: the splitters are picked again for
-        // C/2 leaves so that the 2K classes still fit the budget C.
-        uint32_t Cc = C;
-        for (int attempt = 0; attempt < 2; attempt++) {
-            const uint32_t ns = Cc - 1;
-            for (uint32_t j = tid; j < ns; j += blockDim.x)
-                cand[j] = smp[((uint64_t)(j + 1) * m) / Cc - 1];
-            __syncthreads();
-            for (uint32_t j = tid; j < ns; j += blockDim.x)
-                flag[j] = (j == 0 || cand[j - 1] < cand[j]) ? 1u : 0u;
-            __syncthreads();
-            uint32_t d = cta_exclusive_scan<uint32_t>(flag, pos, (int)ns, wtmp);
-            K keep = T::max_key();
-            bool mine = false;
-            uint32_t mypos = 0;
-            // ns <= 255 < blockDim.x: each thread holds at most one entry
-            for (uint32_t j = tid; j < ns; j += blockDim.x) {
-                if (flag[j]) {
-                    keep = cand[j];
-                    mine = true;
-                    mypos = pos[j];
+                if (mine) cand[mypos] = keep;
+                if (tid == 0) {
+                    sh_d = d;
+                    if (attempt == 0) sh_eq = (d < ns) ? 1u : 0u;
                 }
+                __syncthreads();
+                if (sh_eq == 0 || attempt == 1 || Cc < 4) break;
+                Cc >>= 1;
+                __syncthreads();
             }
-            __syncthreads();
-            if (mine) cand[mypos] = keep;
-            if (tid == 0) {
-                sh_d = d;
-                if (attempt == 0) sh_eq = (d < ns) ? 1u : 0u;
-            }
-            __syncthreads();
-            if (sh_eq == 0 || attempt == 1 || Cc < 4) break;
-            Cc >>= 1;
-            __syncthreads();
         }
-    }
-    const uint32_t d = sh_d;
-    const uint32_t eq = sh_eq;
-    uint32_t K_ = 1;
-    while (K_ < d + 1) K_ <<= 1;
-    const uint32_t logK = ilog2_floor(K_);
-    for (uint32_t j = tid; j < K_; j += blockDim.x) gspl[j] = cand[j < d ? j : d - 1];
-    for (uint32_t i = tid; i < K_; i += blockDim.x) {
-        if (i == 0) continue;
-        uint32_t l = ilog2_floor(i);
-        uint32_t q = i - (1u << l);
-        uint32_t idx = (2 * q + 1) * (K_ >> (l + 1)) - 1;
-        gtree[i] = cand[idx < d ? idx : d - 1];
-    }
-    if (tid == 0) {
-        st->K = K_;
-        st->logK = logK;
-        st->eq = eq;
-        st->B = eq ? 2 * K_ : K_;
+        const uint32_t d = sh_d;
+        const uint32_t eq = sh_eq;
+        uint32_t K_ = 1;
+        while (K_ < d + 1) K_ <<= 1;
+        const uint32_t logK = ilog2_floor(K_);
+        for (uint32_t j = tid; j < K_; j += blockDim.x) gspl[j] = cand[j < d ? j : d - 1];
+        for (uint32_t i = tid; i < K_; i += blockDim.x) {
+            if (i == 0) continue;
+            uint32_t l = ilog2_floor(i);
+            uint32_t q = i - (1u << l);
+            uint32_t idx = (2 * q + 1) * (K_ >> (l + 1)) - 1;
+            gtree[i] = cand[idx < d ? idx : d - 1];
+        }
+        if (tid == 0) {
+            st->K = K_;
+            st->logK = logK;
+            st->eq = eq;
+            st->B = eq ? 2 * K_ : K_;
+        }
+        __syncthreads();
     }
 }
 
@@ -267,69 +283,74 @@ static __global__ void __launch_bounds__(kAuxThreads) k_prep(LevelArgs a) {
     __shared__ unsigned long long sz[kMaxClasses];
     __shared__ unsigned long long pre[kMaxClasses];
     __shared__ unsigned long long wtmp[34];
-    const uint32_t s = blockIdx.x;
-    const SegDesc sd = a.seg[s];
-    SegState *st = a.st + s;
-    const uint32_t B = st->B;
-    const uint32_t b = sd.b;
-    const uint32_t lb = ilog2_floor(b);
     const int tid = threadIdx.x;
-    for (uint32_t j = tid; j < B; j += blockDim.x) {
-        unsigned long long sum = 0;
-        uint32_t full = 0;
-        for (uint32_t q = 0; q < sd.nstripes; q++) {
-            uint32_t c = a.scount[(size_t)(sd.stripe0 + q) * kMaxClasses + j];
-            sum += c;
-            full += c >> lb;
+    const uint32_t nseg = lv_nseg(a);
+    for (uint32_t s = blockIdx.x; s < nseg; s += gridDim.x) {
+        const SegDesc sd = a.seg[s];
+        SegState *st = a.st + s;
+        const SegArrays ar = seg_arrays(a.sarr, sd);
+        const uint32_t B = st->B;
+        const uint32_t b = sd.b;
+        const uint32_t lb = ilog2_floor(b);
+        const uint32_t nslots = st->nslots;
+        for (uint32_t j = tid; j < B; j += blockDim.x) {
+            unsigned long long sum = 0;
+            uint32_t full = 0;
+            for (uint32_t q = 0; q < sd.nstripes; q++) {
+                uint32_t c = a.scount[a.stripe[sd.stripe0 + q].cnt_off + j];
+                sum += c;
+                full += c >> lb;
+            }
+            sz[j] = sum;
+            ar.full[j] = full;
         }
-        sz[j] = sum;
-        st->full[j] = full;
-    }
-    __syncthreads();
-    cta_exclusive_scan<unsigned long long>(sz, pre, (int)B, wtmp);
-    for (uint32_t j = tid; j <= B; j += blockDim.x) {
-        uint64_t bb = j < B ? pre[j] : sd.n;
-        st->bucket_begin[j] = bb;
-        st->dlm[j] = j < B ? (uint32_t)((bb + b - 1) >> lb) : st->nslots;
-    }
-    __syncthreads();
-    const StripeDesc *sp = a.stripe;
-    for (uint32_t j = tid; j < B; j += blockDim.x) {
-        const uint32_t lo = st->dlm[j], hi = st->dlm[j + 1];
-        uint32_t f = 0;
-        if (lo < hi) {
-            RunIter it{sp, a.sfull, first_stripe_ending_after(sp, sd.stripe0, sd.nstripes, lo),
-                       sd.stripe0 + sd.nstripes, lo, hi, true};
-            uint32_t rs, re;
-            while (it.next(rs, re)) f += re - rs;
+        __syncthreads();
+        cta_exclusive_scan<unsigned long long>(sz, pre, (int)B, wtmp);
+        for (uint32_t j = tid; j <= B; j += blockDim.x) {
+            uint64_t bb = j < B ? pre[j] : sd.n;
+            ar.bb[j] = bb;
+            ar.dlm[j] = j < B ? (uint32_t)((bb + b - 1) >> lb) : nslots;
         }
-        st->ptr[j] = ((unsigned long long)lo << 32) | (unsigned long long)(lo + f + kRBias);
-        st->readers[j] = 0;
-        // fix-up: empty slots in [lo, lo+f) <- full slots in [lo+f, hi)
-        const uint32_t P = lo + f;
-        if (f > 0 && P < hi) {
-            RunIter ei{sp, a.sfull, first_stripe_ending_after(sp, sd.stripe0, sd.nstripes, lo),
-                       sd.stripe0 + sd.nstripes, lo, P, false};
-            RunIter fi{sp, a.sfull, first_stripe_ending_after(sp, sd.stripe0, sd.nstripes, P),
-                       sd.stripe0 + sd.nstripes, P, hi, true};
-            uint32_t es = 0, ee = 0, fs = 0, fe = 0;
-            while (true) {
-                if (es == ee && !ei.next(es, ee)) break;
-                if (fs == fe && !fi.next(fs, fe)) {
-                    set_status(a.status, IPSGPU_E_INTERNAL);
-                    break;
+        __syncthreads();
+        const StripeDesc *sp = a.stripe;
+        for (uint32_t j = tid; j < B; j += blockDim.x) {
+            const uint32_t lo = ar.dlm[j], hi = ar.dlm[j + 1];
+            uint32_t f = 0;
+            if (lo < hi) {
+                RunIter it{sp, a.sfull, first_stripe_ending_after(sp, sd.stripe0, sd.nstripes, lo),
+                           sd.stripe0 + sd.nstripes, lo, hi, true};
+                uint32_t rs, re;
+                while (it.next(rs, re)) f += re - rs;
+            }
+            ar.ptr[j] = ((unsigned long long)lo << 32) | (unsigned long long)(lo + f + kRBias);
+            ar.readers[j] = 0;
+            // fix-up: empty slots in [lo, lo+f) <- full slots in [lo+f, hi)
+            const uint32_t P = lo + f;
+            if (f > 0 && P < hi) {
+                RunIter ei{sp, a.sfull, first_stripe_ending_after(sp, sd.stripe0, sd.nstripes, lo),
+                           sd.stripe0 + sd.nstripes, lo, P, false};
+                RunIter fi{sp, a.sfull, first_stripe_ending_after(sp, sd.stripe0, sd.nstripes, P),
+                           sd.stripe0 + sd.nstripes, P, hi, true};
+                uint32_t es = 0, ee = 0, fs = 0, fe = 0;
+                while (true) {
+                    if (es == ee && !ei.next(es, ee)) break;
+                    if (fs == fe && !fi.next(fs, fe)) {
+                        set_status(a.status, IPSGPU_E_INTERNAL);
+                        break;
+                    }
+                    uint32_t len = min(ee - es, fe - fs);
+                    uint32_t mi = atomicAdd(a.nmoves, 1u);
+                    if (mi < a.move_cap) {
+                        a.moves[mi] = Move{s, fs, es, len};
+                    } else {
+                        set_status(a.status, IPSGPU_E_INTERNAL);
+                    }
+                    es += len;
+                    fs += len;
                 }
-                uint32_t len = min(ee - es, fe - fs);
-                uint32_t mi = atomicAdd(a.nmoves, 1u);
-                if (mi < a.move_cap) {
-                    a.moves[mi] = Move{s, fs, es, len};
-                } else {
-                    set_status(a.status, IPSGPU_E_INTERNAL);
-                }
-                es += len;
-                fs += len;
             }
         }
+        __syncthreads();
     }
 }
 
@@ -373,6 +394,11 @@ __device__ __forceinline__ void warp_store_block(const uint4 &r, unsigned char *
 
 __device__ __forceinline__ int access_unit(uint64_t byte_off) {
     return (byte_off & 15) == 0 ? 16 : ((byte_off & 7) == 0 ? 8 : 4);
+}
+
+// the segment's overflow block sits after its C staging blocks
+__device__ __forceinline__ unsigned char *seg_ovf(const LevelArgs &a, const SegDesc &sd, int D) {
+    return a.arena + sd.stage_off + (uint64_t)sd.C * sd.b * D;
 }
 
 // ------------------------------------------------------------------ fixup
@@ -419,137 +445,147 @@ __global__ void __launch_bounds__(kAuxThreads) k_fixup(LevelArgs a) {
 
 // ---------------------------------------------------------------- permute
 // Block permutation (Sec. 3.1.3).  Each warp is one worker with two swap
-// buffers (one 512-byte block per buffer, 16 bytes per lane, in
-// registers).  Per bucket i, ptr[i] packs the write pointer w_i (high half)
-// and the exclusive read pointer r_i + 1 (low half, biased), so that one
-// 64-bit atomic reads and modifies both consistently.  Blocks in [d_i, w_i)
-// are correct, blocks in [w_i, r_i] unprocessed, the rest empty.
+// buffers (one block per buffer, 16 bytes per lane, in registers).  Per
+// bucket i, ptr[i] packs the write pointer w_i (high half) and the exclusive
+// read pointer r_i + 1 (low half, biased), so that one 64-bit atomic reads
+// and modifies both consistently.  Blocks in [d_i, w_i) are correct, blocks
+// in [w_i, r_i] unprocessed, the rest empty.  A CTA runs the virtual CTAs
+// blockIdx.x, blockIdx.x + gridDim.x, ... of the level; workers of a segment
+// never wait for one another except for the bounded reader wait, so they need
+// not run at the same time.
 template <class T>
-__global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a,
-                                                             const uint32_t *cta_seg) {
+__global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a) {
     typedef typename T::K K;
-    typedef typename T::E E;
     __shared__ K s_tree[kMaxClasses];
     __shared__ K s_spl[kMaxClasses];
-    const uint32_t s = cta_seg[blockIdx.x];
-    const SegDesc sd = a.seg[s];
-    SegState *st = a.st + s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    LevelClassifier<T> cl;
-    load_classifier<T>(cl, a, s, sd, *st, s_tree, s_spl);
-    __syncthreads();
-    const uint32_t B = st->B;
-    const uint32_t nfs = st->nfull_slots;
-    const uint32_t BB = sd.b * T::D;
-    unsigned char *base = a.data + sd.begin * (uint64_t)T::D;
-    const int u = access_unit((uint64_t)(uintptr_t)base);
-    const uint32_t W = sd.ncta * (kPermuteThreads / 32);
-    const uint32_t wid = (blockIdx.x - sd.cta0) * (kPermuteThreads / 32) + warp;
-    uint32_t p = (uint32_t)(((uint64_t)wid * B) / W);
-    uint32_t scanned = 0;
-    uint4 A = make_uint4(0, 0, 0, 0), Bk = make_uint4(0, 0, 0, 0);
-    uint32_t t = 0;
-    bool hold = false;
+    const uint32_t ncta = lv_ncta(a);
     const uint32_t limit = a.spin_limit;
+    for (uint32_t v = blockIdx.x; v < ncta; v += gridDim.x) {
+        const uint32_t s = a.cta_seg[v];
+        const SegDesc sd = a.seg[s];
+        SegState *st = a.st + s;
+        const SegArrays ar = seg_arrays(a.sarr, sd);
+        LevelClassifier<T> cl;
+        __syncthreads();
+        load_classifier<T>(cl, a, sd, *st, s_tree, s_spl);
+        __syncthreads();
+        const uint32_t B = st->B;
+        const uint32_t nfs = st->nfull_slots;
+        const uint32_t BB = sd.b * T::D;
+        unsigned char *base = a.data + sd.begin * (uint64_t)T::D;
+        const int u = access_unit((uint64_t)(uintptr_t)base);
+        const uint32_t W = sd.ncta * (kPermuteThreads / 32);
+        const uint32_t wid = (v - sd.cta0) * (kPermuteThreads / 32) + warp;
+        uint32_t p = (uint32_t)(((uint64_t)wid * B) / W);
+        uint32_t scanned = 0;
+        uint4 A = make_uint4(0, 0, 0, 0), Bk = make_uint4(0, 0, 0, 0);
+        uint32_t t = 0;
+        bool hold = false;
+        bool failed = false;
 
-    while (true) {
-        if (!hold) {
-            bool got = false;
-            while (scanned < B) {
-                int res = 0;
-                uint32_t blk = 0;
-                if (lane == 0) {
-                    unsigned long long v = *(volatile unsigned long long *)&st->ptr[p];
-                    int64_t w = (int64_t)(v >> 32);
-                    int64_t re = (int64_t)(uint32_t)v - (int64_t)kRBias;
-                    if (re > w) {
-                        atomicAdd(&st->readers[p], 1u);
-                        __threadfence();
-                        unsigned long long old = atomicAdd(&st->ptr[p], ~0ull);  // r - 1
-                        w = (int64_t)(old >> 32);
-                        re = (int64_t)(uint32_t)old - (int64_t)kRBias;
+        while (true) {
+            if (!hold) {
+                bool got = false;
+                while (scanned < B) {
+                    int res = 0;
+                    uint32_t blk = 0;
+                    if (lane == 0) {
+                        unsigned long long vv = *(volatile unsigned long long *)&ar.ptr[p];
+                        int64_t w = (int64_t)(vv >> 32);
+                        int64_t re = (int64_t)(uint32_t)vv - (int64_t)kRBias;
                         if (re > w) {
-                            blk = (uint32_t)(re - 1);
-                            res = 1;
-                        } else {
+                            atomicAdd(&ar.readers[p], 1u);
                             __threadfence();
-                            atomicSub(&st->readers[p], 1u);
+                            unsigned long long old = atomicAdd(&ar.ptr[p], ~0ull);  // r - 1
+                            w = (int64_t)(old >> 32);
+                            re = (int64_t)(uint32_t)old - (int64_t)kRBias;
+                            if (re > w) {
+                                blk = (uint32_t)(re - 1);
+                                res = 1;
+                            } else {
+                                __threadfence();
+                                atomicSub(&ar.readers[p], 1u);
+                            }
                         }
                     }
-                }
-                res = __shfl_sync(0xffffffffu, res, 0);
-                if (res) {
-                    blk = __shfl_sync(0xffffffffu, blk, 0);
-                    if (blk >= nfs) {  // unprocessed blocks are always full slots
-                        if (lane == 0) set_status(a.status, IPSGPU_E_INTERNAL);
-                        return;
+                    res = __shfl_sync(0xffffffffu, res, 0);
+                    if (res) {
+                        blk = __shfl_sync(0xffffffffu, blk, 0);
+                        if (blk >= nfs) {  // unprocessed blocks are always full slots
+                            if (lane == 0) set_status(a.status, IPSGPU_E_INTERNAL);
+                            failed = true;
+                            break;
+                        }
+                        warp_load_block(A, base + (uint64_t)blk * BB, BB, lane, u);
+                        __threadfence();
+                        __syncwarp();
+                        if (lane == 0) atomicSub(&ar.readers[p], 1u);
+                        got = true;
+                        break;
                     }
-                    warp_load_block(A, base + (uint64_t)blk * BB, BB, lane, u);
+                    p = (p + 1 == B) ? 0 : p + 1;
+                    scanned++;
+                }
+                if (!got) break;
+                scanned = 0;
+                uint32_t tt = 0;
+                if (lane == 0) tt = cl(T::head(A));
+                t = __shfl_sync(0xffffffffu, tt, 0);
+                hold = true;
+            }
+            // place the held block into bucket t
+            uint32_t slot = 0;
+            int unproc = 0;
+            if (lane == 0) {
+                unsigned long long old = atomicAdd(&ar.ptr[t], 1ull << 32);  // w + 1
+                int64_t w = (int64_t)(old >> 32);
+                int64_t re = (int64_t)(uint32_t)old - (int64_t)kRBias;
+                slot = (uint32_t)w;
+                unproc = w < re ? 1 : 0;
+            }
+            slot = __shfl_sync(0xffffffffu, slot, 0);
+            unproc = __shfl_sync(0xffffffffu, unproc, 0);
+            if (slot >= ar.dlm[t + 1] || (unproc && slot >= nfs)) {
+                // a write pointer never leaves its bucket region
+                if (lane == 0) set_status(a.status, IPSGPU_E_INTERNAL);
+                failed = true;
+                break;
+            }
+            if (unproc) {
+                warp_load_block(Bk, base + (uint64_t)slot * BB, BB, lane, u);
+                uint32_t t2 = 0;
+                if (lane == 0) t2 = cl(T::head(Bk));
+                t2 = __shfl_sync(0xffffffffu, t2, 0);
+                if (t2 == t) continue;  // already in place: w moved past it
+                warp_store_block(A, base + (uint64_t)slot * BB, BB, lane, u);
+                A = Bk;
+                t = t2;
+            } else {
+                // empty slot: no reader of bucket t may still be copying it out
+                int ok = 1;
+                if (lane == 0) {
                     __threadfence();
-                    __syncwarp();
-                    if (lane == 0) atomicSub(&st->readers[p], 1u);
-                    got = true;
+                    ok = bounded_wait_eq(&ar.readers[t], 0u, limit) ? 1 : 0;
+                    __threadfence();
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    if (lane == 0) set_status(a.status, IPSGPU_E_TIMEOUT);
+                    failed = true;
                     break;
                 }
-                p = (p + 1 == B) ? 0 : p + 1;
-                scanned++;
+                if (slot >= nfs) {
+                    // the last, partial block of the segment: use the overflow block
+                    warp_store_block(A, seg_ovf(a, sd, T::D), BB, lane, 16);
+                    if (lane == 0) st->ovf_used = 1;
+                } else {
+                    warp_store_block(A, base + (uint64_t)slot * BB, BB, lane, u);
+                }
+                hold = false;
             }
-            if (!got) break;
-            scanned = 0;
-            uint32_t tt = 0;
-            if (lane == 0) tt = cl(T::head(A));
-            t = __shfl_sync(0xffffffffu, tt, 0);
-            hold = true;
         }
-        // place the held block into bucket t
-        uint32_t slot = 0;
-        int unproc = 0;
-        if (lane == 0) {
-            unsigned long long old = atomicAdd(&st->ptr[t], 1ull << 32);  // w + 1
-            int64_t w = (int64_t)(old >> 32);
-            int64_t re = (int64_t)(uint32_t)old - (int64_t)kRBias;
-            slot = (uint32_t)w;
-            unproc = w < re ? 1 : 0;
-        }
-        slot = __shfl_sync(0xffffffffu, slot, 0);
-        unproc = __shfl_sync(0xffffffffu, unproc, 0);
-        if (slot >= st->dlm[t + 1] || (unproc && slot >= nfs)) {
-            // a write pointer never leaves its bucket region
-            if (lane == 0) set_status(a.status, IPSGPU_E_INTERNAL);
-            return;
-        }
-        if (unproc) {
-            warp_load_block(Bk, base + (uint64_t)slot * BB, BB, lane, u);
-            uint32_t t2 = 0;
-            if (lane == 0) t2 = cl(T::head(Bk));
-            t2 = __shfl_sync(0xffffffffu, t2, 0);
-            if (t2 == t) continue;  // already in place: w moved past it
-            warp_store_block(A, base + (uint64_t)slot * BB, BB, lane, u);
-            A = Bk;
-            t = t2;
-        } else {
-            // empty slot: no reader of bucket t may still be copying it out
-            int ok = 1;
-            if (lane == 0) {
-                __threadfence();
-                ok = bounded_wait_eq(&st->readers[t], 0u, limit) ? 1 : 0;
-                __threadfence();
-            }
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) {
-                if (lane == 0) set_status(a.status, IPSGPU_E_TIMEOUT);
-                return;
-            }
-            if (slot >= nfs) {
-                // the last, partial block of the segment: use the overflow block
-                unsigned char *ob = a.ovf + (size_t)s * a.ovf_stride;
-                warp_store_block(A, ob, BB, lane, 16);
-                if (lane == 0) st->ovf_used = 1;
-            } else {
-                warp_store_block(A, base + (uint64_t)slot * BB, BB, lane, u);
-            }
-            hold = false;
-        }
+        (void)failed;
     }
 }
 
@@ -562,116 +598,136 @@ __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a,
 template <class T>
 __global__ void __launch_bounds__(kAuxThreads) k_stage(LevelArgs a) {
     typedef typename T::E E;
-    const uint32_t s = blockIdx.x;
-    const SegDesc sd = a.seg[s];
-    const SegState &st = a.st[s];
-    const uint32_t B = st.B, b = sd.b;
-    const E *base = reinterpret_cast<const E *>(a.data) + sd.begin;
-    E *stage = reinterpret_cast<E *>(a.arena + sd.stage_off);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t cap = (uint64_t)st.nfull_slots * b;
-    for (uint32_t j = warp; j < B; j += blockDim.x / 32) {
-        const uint64_t hi = st.bucket_begin[j + 1];
-        const uint64_t ds = (uint64_t)st.dlm[j] * b;
-        const uint64_t ws = (uint64_t)(st.dlm[j] + st.full[j]) * b;
-        const uint64_t lo_o = max(hi, ds), hi_o = min(ws, cap);
-        if (hi_o > lo_o && hi_o - lo_o >= b) {  // a spill is shorter than a block
-            if (lane == 0) set_status(a.status, IPSGPU_E_INTERNAL);
-            continue;
+    const uint32_t nseg = lv_nseg(a);
+    for (uint32_t s = blockIdx.x; s < nseg; s += gridDim.x) {
+        const SegDesc sd = a.seg[s];
+        const SegState &st = a.st[s];
+        const SegArrays ar = seg_arrays(a.sarr, sd);
+        const uint32_t B = st.B, b = sd.b;
+        const E *base = reinterpret_cast<const E *>(a.data) + sd.begin;
+        E *stage = reinterpret_cast<E *>(a.arena + sd.stage_off);
+        const uint64_t cap = (uint64_t)st.nfull_slots * b;
+        for (uint32_t j = warp; j < B; j += blockDim.x / 32) {
+            const uint64_t hi = ar.bb[j + 1];
+            const uint64_t ds = (uint64_t)ar.dlm[j] * b;
+            const uint64_t ws = (uint64_t)(ar.dlm[j] + ar.full[j]) * b;
+            const uint64_t lo_o = max(hi, ds), hi_o = min(ws, cap);
+            if (hi_o > lo_o && hi_o - lo_o >= b) {  // a spill is shorter than a block
+                if (lane == 0) set_status(a.status, IPSGPU_E_INTERNAL);
+                continue;
+            }
+            for (uint64_t x = lo_o + lane; x < hi_o; x += 32)
+                stage[(size_t)j * b + (x - lo_o)] = base[x];
         }
-        for (uint64_t x = lo_o + lane; x < hi_o; x += 32)
-            stage[(size_t)j * b + (x - lo_o)] = base[x];
     }
 }
 
-// One CTA per (segment, bucket): gather the bucket's missing elements from
-// the staged spill, the overflow block and the leftover buffer blocks of all
-// stripes, and write them to the bucket's head and tail positions
-// (Sec. 3.1.4, sources 1, 2 and 4; the workers of k_permute end with empty
-// swap buffers, so source 3 is empty here).
+// One CTA per (segment, class) work item: gather the bucket's missing
+// elements from the staged spill, the overflow block and the leftover buffer
+// blocks of all stripes, and write them to the bucket's head and tail
+// positions (Sec. 3.1.4, sources 1, 2 and 4; the workers of k_permute end
+// with empty swap buffers, so source 3 is empty here).  Work item q belongs
+// to the segment s with cls0[s] <= q < cls0[s] + C_s.
 template <class T>
 __global__ void __launch_bounds__(kAuxThreads) k_fill(LevelArgs a) {
     typedef typename T::E E;
     constexpr int kMaxStripePre = 2048;
     __shared__ uint32_t pre[kMaxStripePre + 1];
     __shared__ uint32_t wtmp[34];
-    const uint32_t s = blockIdx.y;
-    const uint32_t j = blockIdx.x;
-    const SegDesc sd = a.seg[s];
-    const SegState &st = a.st[s];
-    const uint32_t B = st.B, b = sd.b;
-    if (j >= B) return;
     const int tid = threadIdx.x;
-    E *base = reinterpret_cast<E *>(a.data) + sd.begin;
-    const uint64_t lo = st.bucket_begin[j], hi = st.bucket_begin[j + 1];
-    const uint64_t ds = (uint64_t)st.dlm[j] * b;
-    const uint64_t ws = (uint64_t)(st.dlm[j] + st.full[j]) * b;
-    const uint64_t cap = (uint64_t)st.nfull_slots * b;
-    const uint64_t head_end = min(ds, hi);
-    const uint64_t nhead = head_end - lo;
-    const uint64_t rend = max(ds, min(min(ws, hi), cap));
-    const uint64_t ntail = hi > rend ? hi - rend : 0;
-    const uint64_t nfill = nhead + ntail;
-    const uint64_t lo_o = max(hi, ds), hi_o = min(ws, cap);
-    const uint32_t nstage = hi_o > lo_o ? (uint32_t)min(hi_o - lo_o, (uint64_t)b) : 0;
-    // the overflow block holds this bucket's last full block iff the partial
-    // slot (index nfull_slots) lies inside [d_j, d_j + full_j)
-    const uint32_t novf = (ds <= cap && ws > cap) ? b : 0;
-    const E *stage = reinterpret_cast<const E *>(a.arena + sd.stage_off) + (size_t)j * b;
-    const E *ovf = reinterpret_cast<const E *>(a.ovf + (size_t)s * a.ovf_stride);
-    const uint32_t ns = sd.nstripes;
-    // leftover counts per stripe, processed in chunks of kMaxStripePre stripes
-    uint64_t done = nstage + novf;
-    // sources 1 and 4 first
-    for (uint64_t t = tid; t < nstage + novf && t < nfill; t += blockDim.x) {
-        E x = t < nstage ? stage[t] : ovf[t - nstage];
-        uint64_t dst = t < nhead ? lo + t : rend + (t - nhead);
-        base[dst] = x;
-    }
-    for (uint32_t c0 = 0; c0 < ns; c0 += kMaxStripePre) {
-        const uint32_t cn = min((uint32_t)kMaxStripePre, ns - c0);
-        for (uint32_t q = tid; q < cn; q += blockDim.x)
-            pre[q] = a.scount[(size_t)(sd.stripe0 + c0 + q) * kMaxClasses + j] & (b - 1);
-        __syncthreads();
-        const uint32_t tot = cta_exclusive_scan<uint32_t>(pre, pre, (int)cn, wtmp);
-        if (tid == 0) pre[cn] = tot;
-        __syncthreads();
-        for (uint32_t t = tid; t < tot; t += blockDim.x) {
-            // stripe q with pre[q] <= t < pre[q+1]
-            uint32_t l = 0, h = cn;
-            while (h - l > 1) {
-                uint32_t mid = (l + h) >> 1;
-                if (pre[mid] <= t)
-                    l = mid;
-                else
-                    h = mid;
-            }
-            const StripeDesc &sp = a.stripe[sd.stripe0 + c0 + l];
-            const E *left = reinterpret_cast<const E *>(a.arena + sp.left_off) + (size_t)j * b;
-            E x = left[t - pre[l]];
-            uint64_t tt = done + t;
-            if (tt < nfill) {
-                uint64_t dst = tt < nhead ? lo + tt : rend + (tt - nhead);
-                base[dst] = x;
-            }
+    const uint32_t nseg = lv_nseg(a), ncls = lv_ncls(a);
+    for (uint32_t q = blockIdx.x; q < ncls; q += gridDim.x) {
+        uint32_t lo_s = 0, hi_s = nseg;  // last segment with cls0 <= q
+        while (hi_s - lo_s > 1) {
+            const uint32_t mid = (lo_s + hi_s) >> 1;
+            if (a.seg[mid].cls0 <= q)
+                lo_s = mid;
+            else
+                hi_s = mid;
         }
-        done += tot;
+        const uint32_t s = lo_s;
+        const SegDesc sd = a.seg[s];
+        const SegState &st = a.st[s];
+        const uint32_t j = q - sd.cls0;
+        const uint32_t B = st.B, b = sd.b;
+        if (j >= B) continue;
+        const SegArrays ar = seg_arrays(a.sarr, sd);
+        E *base = reinterpret_cast<E *>(a.data) + sd.begin;
+        const uint64_t lo = ar.bb[j], hi = ar.bb[j + 1];
+        const uint64_t ds = (uint64_t)ar.dlm[j] * b;
+        const uint64_t ws = (uint64_t)(ar.dlm[j] + ar.full[j]) * b;
+        const uint64_t cap = (uint64_t)st.nfull_slots * b;
+        const uint64_t head_end = min(ds, hi);
+        const uint64_t nhead = head_end - lo;
+        const uint64_t rend = max(ds, min(min(ws, hi), cap));
+        const uint64_t ntail = hi > rend ? hi - rend : 0;
+        const uint64_t nfill = nhead + ntail;
+        const uint64_t lo_o = max(hi, ds), hi_o = min(ws, cap);
+        const uint32_t nstage = hi_o > lo_o ? (uint32_t)min(hi_o - lo_o, (uint64_t)b) : 0;
+        // the overflow block holds this bucket's last full block iff the
+        // partial slot (index nfull_slots) lies inside [d_j, d_j + full_j)
+        const uint32_t novf = (ds <= cap && ws > cap) ? b : 0;
+        const E *stage = reinterpret_cast<const E *>(a.arena + sd.stage_off) + (size_t)j * b;
+        const E *ovf = reinterpret_cast<const E *>(seg_ovf(a, sd, T::D));
+        const uint32_t ns = sd.nstripes;
+        uint64_t done = nstage + novf;
+        // sources 1 and 4 first
+        for (uint64_t t = tid; t < nstage + novf && t < nfill; t += blockDim.x) {
+            E x = t < nstage ? stage[t] : ovf[t - nstage];
+            uint64_t dst = t < nhead ? lo + t : rend + (t - nhead);
+            base[dst] = x;
+        }
+        // leftover buffer blocks of every stripe, in chunks of kMaxStripePre
+        for (uint32_t c0 = 0; c0 < ns; c0 += kMaxStripePre) {
+            const uint32_t cn = min((uint32_t)kMaxStripePre, ns - c0);
+            for (uint32_t r = tid; r < cn; r += blockDim.x)
+                pre[r] = a.scount[a.stripe[sd.stripe0 + c0 + r].cnt_off + j] & (b - 1);
+            __syncthreads();
+            const uint32_t tot = cta_exclusive_scan<uint32_t>(pre, pre, (int)cn, wtmp);
+            if (tid == 0) pre[cn] = tot;
+            __syncthreads();
+            for (uint32_t t = tid; t < tot; t += blockDim.x) {
+                // stripe r with pre[r] <= t < pre[r+1]
+                uint32_t l = 0, h = cn;
+                while (h - l > 1) {
+                    uint32_t mid = (l + h) >> 1;
+                    if (pre[mid] <= t)
+                        l = mid;
+                    else
+                        h = mid;
+                }
+                const StripeDesc &sp = a.stripe[sd.stripe0 + c0 + l];
+                const E *left = reinterpret_cast<const E *>(a.arena + sp.left_off) + (size_t)j * b;
+                E x = left[t - pre[l]];
+                uint64_t tt = done + t;
+                if (tt < nfill) {
+                    uint64_t dst = tt < nhead ? lo + tt : rend + (tt - nhead);
+                    base[dst] = x;
+                }
+            }
+            done += tot;
+            __syncthreads();
+        }
+        if (tid == 0 && done != nfill) set_status(a.status, IPSGPU_E_INTERNAL);
         __syncthreads();
     }
-    if (tid == 0 && done != nfill) set_status(a.status, IPSGPU_E_INTERNAL);
 }
 
 // Copy (B, eq, bucket_begin[0..B]) of every segment into a dense array
 // res[s][kMaxClasses + 3] for one device-to-host transfer.
 static __global__ void __launch_bounds__(kAuxThreads) k_pack_results(LevelArgs a, uint64_t *res) {
-    const uint32_t s = blockIdx.x;
-    const SegState &st = a.st[s];
-    uint64_t *r = res + (size_t)s * (kMaxClasses + 3);
-    if (threadIdx.x == 0) {
-        r[0] = st.B;
-        r[1] = st.eq;
+    const uint32_t nseg = lv_nseg(a);
+    for (uint32_t s = blockIdx.x; s < nseg; s += gridDim.x) {
+        const SegState &st = a.st[s];
+        const SegArrays ar = seg_arrays(a.sarr, a.seg[s]);
+        uint64_t *r = res + (size_t)s * (kMaxClasses + 3);
+        if (threadIdx.x == 0) {
+            r[0] = st.B;
+            r[1] = st.eq;
+        }
+        for (uint32_t j = threadIdx.x; j <= st.B; j += blockDim.x) r[2 + j] = ar.bb[j];
     }
-    for (uint32_t j = threadIdx.x; j <= st.B; j += blockDim.x) r[2 + j] = st.bucket_begin[j];
 }
 
 // Element-wise classification (the classifier alone, for ipsgpu_classify).
@@ -683,7 +739,7 @@ __global__ void __launch_bounds__(kAuxThreads) k_classify_ids(LevelArgs a, uint3
     __shared__ K s_spl[kMaxClasses];
     const SegDesc sd = a.seg[0];
     LevelClassifier<T> cl;
-    load_classifier<T>(cl, a, 0, sd, a.st[0], s_tree, s_spl);
+    load_classifier<T>(cl, a, sd, a.st[0], s_tree, s_spl);
     __syncthreads();
     const E *base = reinterpret_cast<const E *>(a.data) + sd.begin;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sd.n;

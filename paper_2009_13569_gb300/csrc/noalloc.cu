@@ -41,20 +41,21 @@ constexpr uint64_t kNaMaxN = 0xFFFFFFFFull;                // elements per call
 constexpr int kNaMaxDevices = 64;
 
 constexpr uint64_t al(uint64_t x) { return (x + 255) & ~(uint64_t)255; }
+// cleanup staging of C <= 256 blocks of <= 512 bytes, then the overflow block
+constexpr uint64_t kNaStage = al(kNaSlot + 512);
 constexpr uint64_t kOSeg = 0;
 constexpr uint64_t kOSt = al(kOSeg + sizeof(SegDesc));
-constexpr uint64_t kOTree = al(kOSt + sizeof(SegState));
-constexpr uint64_t kOSpl = al(kOTree + kMaxClasses * 16);
-constexpr uint64_t kOStripe = al(kOSpl + kMaxClasses * 16);
+constexpr uint64_t kOSarr = al(kOSt + sizeof(SegState));   // SegArrays: bucket_begin first
+constexpr uint64_t kOKeys = al(kOSarr + 28 * kMaxClasses + 32);  // tree, splitters
+constexpr uint64_t kOStripe = al(kOKeys + 2 * kMaxClasses * 16);
 constexpr uint64_t kOScount = al(kOStripe + kNaStripes * sizeof(StripeDesc));
 constexpr uint64_t kOSfull = al(kOScount + (uint64_t)kNaStripes * kMaxClasses * 4);
-constexpr uint64_t kOOvf = al(kOSfull + kNaStripes * 4);
-constexpr uint64_t kOMoves = al(kOOvf + 512);
+constexpr uint64_t kOMoves = al(kOSfull + kNaStripes * 4);
 constexpr uint64_t kONmoves = al(kOMoves + kNaMoves * sizeof(Move));
 constexpr uint64_t kOStatus = kONmoves + 4;
 constexpr uint64_t kOCta = al(kOStatus + 4);
 constexpr uint64_t kOArena = al(kOCta + kNaCtas * 4);
-constexpr uint64_t kNaScratchBytes = kOArena + (kNaStripes + 1) * kNaSlot;
+constexpr uint64_t kNaScratchBytes = kOArena + kNaStage + kNaStripes * kNaSlot;
 
 static __device__ __align__(256) unsigned char g_na_scratch[kNaScratchBytes];
 
@@ -88,6 +89,10 @@ __global__ void k_na_plan(unsigned char *scr, uint64_t n, uint32_t b, uint32_t C
         d.cta0 = 0;
         d.ncta = nc;
         d.stage_off = 0;
+        d.arr_off = 0;
+        d.key_off = 0;
+        d.cls0 = 0;
+        d.cnt0 = 0;
         d.mode = 1;
         d.nsplit = nsplit;
         d.eq_given = eq;
@@ -100,8 +105,8 @@ __global__ void k_na_plan(unsigned char *scr, uint64_t n, uint32_t b, uint32_t C
         q.seg = 0;
         q.blk0 = (uint32_t)(t * nb / p);
         q.nblk = (uint32_t)((t + 1) * nb / p - t * nb / p);
-        q.pad = 0;
-        q.left_off = (uint64_t)(t + 1) * slot_bytes;
+        q.cnt_off = t * C;
+        q.left_off = kNaStage + (uint64_t)t * slot_bytes;
         sp[t] = q;
     }
     if (t < nc) cta[t] = 0;
@@ -110,10 +115,10 @@ __global__ void k_na_plan(unsigned char *scr, uint64_t n, uint32_t b, uint32_t C
 // bucket_begin[0..B] to the caller; an error seen by any kernel of this call
 // turns the total bucket_begin[B] into ~0 so the caller can detect it
 __global__ void k_na_finish(const unsigned char *scr, uint64_t *out, uint32_t B) {
-    const SegState *st = reinterpret_cast<const SegState *>(scr + kOSt);
+    const uint64_t *bb = reinterpret_cast<const uint64_t *>(scr + kOSarr);
     const int status = *reinterpret_cast<const int *>(scr + kOStatus);
     for (uint32_t j = threadIdx.x; j <= B; j += blockDim.x)
-        out[j] = (j == B && status != 0) ? ~0ull : st->bucket_begin[j];
+        out[j] = (j == B && status != 0) ? ~0ull : bb[j];
 }
 
 const TypeOps *na_ops(int dtype) {
@@ -178,13 +183,12 @@ extern "C" int ipsgpu_partition_level_noalloc(int dtype, void *d_data, uint64_t 
     s.k = kMaxClasses;
     s.d_seg = reinterpret_cast<SegDesc *>(scr + kOSeg);
     s.d_st = reinterpret_cast<SegState *>(scr + kOSt);
-    s.d_tree = scr + kOTree;
-    s.d_spl = scr + kOSpl;
+    s.d_sarr = scr + kOSarr;
+    s.d_keys = scr + kOKeys;
     s.d_stripe = reinterpret_cast<StripeDesc *>(scr + kOStripe);
     s.d_scount = reinterpret_cast<uint32_t *>(scr + kOScount);
     s.d_sfull = reinterpret_cast<uint32_t *>(scr + kOSfull);
     s.d_arena = scr + kOArena;
-    s.d_ovf = scr + kOOvf;
     s.d_moves = reinterpret_cast<Move *>(scr + kOMoves);
     s.d_nmoves = reinterpret_cast<uint32_t *>(scr + kONmoves);
     s.d_status = reinterpret_cast<int *>(scr + kOStatus);
@@ -212,9 +216,10 @@ extern "C" int ipsgpu_partition_level_noalloc(int dtype, void *d_data, uint64_t 
         scr, n, b, (uint32_t)B, (uint32_t)p, (uint32_t)nc, num_splitters, equal_buckets ? 1u : 0u,
         (uint32_t)kNaSlot);
     if (cudaGetLastError() != cudaSuccess) return IPSGPU_E_CUDA;
-    if (ops->level(&s, 1, (uint32_t)p, (uint32_t)nc, static_cast<const unsigned char *>(d_splitters),
-                   st) != cudaSuccess)
-        return IPSGPU_E_CUDA;
+    const LevelArgs a = s.args(1, (uint32_t)p, (uint32_t)nc, (uint32_t)B,
+                               static_cast<const unsigned char *>(d_splitters));
+    const LevelGrids g{1, (uint32_t)p, (uint32_t)nc, (uint32_t)B};
+    if (ops->level(&s, a, g, st) != cudaSuccess) return IPSGPU_E_CUDA;
     k_na_finish<<<1, 256, 0, st>>>(scr, d_bucket_begin, (uint32_t)B);
     return cudaGetLastError() == cudaSuccess ? IPSGPU_OK : IPSGPU_E_CUDA;
 }

@@ -4,6 +4,7 @@
 
 #include "base.cuh"
 #include "classify.cuh"
+#include "graph.cuh"
 #include "level.cuh"
 #include "sorter.h"
 
@@ -30,38 +31,38 @@ struct OpsImpl {
         return e;
     }
 
-    static cudaError_t level(Sorter *s, uint32_t nseg, uint32_t nstripe, uint32_t ncta,
-                             const unsigned char *given_spl, cudaStream_t st) {
-        LevelArgs a = s->args(nseg, nstripe, given_spl);
+    // One partitioning level.  g holds the grid of each kernel: the exact
+    // work counts for a host-planned batch, or fixed persistent grids when
+    // the counts live in device memory (a.cnt != nullptr).
+    static cudaError_t level(Sorter *s, const LevelArgs &a, const LevelGrids &g, cudaStream_t st) {
         const double lvl = (double)s->level_elems * T::D;
         cudaError_t e;
         if ((e = cudaMemsetAsync(s->d_nmoves, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
         s->tbegin(KK_SAMPLE, 0, st);
-        k_sample_tree<T><<<nseg, kSampleThreads, sample_smem(), st>>>(a);
+        k_sample_tree<T><<<g.seg, kSampleThreads, sample_smem(), st>>>(a);
         s->tend(st);
         s->tbegin(KK_CLASSIFY, 2 * lvl, st);
-        k_classify<T><<<nstripe, ClsCfg<T>::NT, classify_smem(s), st>>>(a);
+        k_classify<T><<<g.stripe, ClsCfg<T>::NT, classify_smem(s), st>>>(a);
         s->tend(st);
         s->tbegin(KK_PREP, 0, st);
-        k_prep<<<nseg, kAuxThreads, 0, st>>>(a);
+        k_prep<<<g.seg, kAuxThreads, 0, st>>>(a);
         s->tend(st);
         s->tbegin(KK_FIXUP, 0, st);
         k_fixup<T><<<s->nsm * 4, kAuxThreads, 0, st>>>(a);
         s->tend(st);
         s->tbegin(KK_PERMUTE, 2 * lvl, st);
-        k_permute<T><<<ncta, kPermuteThreads, 0, st>>>(a, s->d_cta_seg);
+        k_permute<T><<<g.cta, kPermuteThreads, 0, st>>>(a);
         s->tend(st);
         s->tbegin(KK_STAGE, 0, st);
-        k_stage<T><<<nseg, kAuxThreads, 0, st>>>(a);
+        k_stage<T><<<g.seg, kAuxThreads, 0, st>>>(a);
         s->tend(st);
         s->tbegin(KK_FILL, 0, st);
-        k_fill<T><<<dim3(kMaxClasses, nseg), kAuxThreads, 0, st>>>(a);
+        k_fill<T><<<g.cls, kAuxThreads, 0, st>>>(a);
         s->tend(st);
         return cudaGetLastError();
     }
 
-    static cudaError_t pack(Sorter *s, uint32_t nseg, cudaStream_t st) {
-        LevelArgs a = s->args(nseg, 0, nullptr);
+    static cudaError_t pack(Sorter *s, const LevelArgs &a, uint32_t nseg, cudaStream_t st) {
         s->tbegin(KK_PACK, 0, st);
         k_pack_results<<<nseg, kAuxThreads, 0, st>>>(a, s->d_res);
         s->tend(st);
@@ -69,11 +70,11 @@ struct OpsImpl {
     }
 
     static cudaError_t base(Sorter *s, unsigned char *data, const uint64_t *d_segs, uint32_t nsegs,
-                            cudaStream_t st) {
-        if (nsegs == 0) return cudaSuccess;
-        uint32_t grid = nsegs < (uint32_t)s->nsm * 64 ? nsegs : (uint32_t)s->nsm * 64;
+                            const uint32_t *nsegs_dev, uint32_t grid, cudaStream_t st) {
+        if (grid == 0) return cudaSuccess;
         s->tbegin(KK_BASE, 2.0 * (double)s->level_elems * T::D, st);
-        k_base<T><<<grid, kBaseThreads, base_smem_bytes(), st>>>(data, d_segs, nsegs, s->d_status);
+        k_base<T><<<grid, kBaseThreads, base_smem_bytes(), st>>>(data, d_segs, nsegs, nsegs_dev,
+                                                                 s->d_status);
         s->tend(st);
         return cudaGetLastError();
     }
@@ -99,9 +100,7 @@ struct OpsImpl {
         return cudaGetLastError();
     }
 
-    static cudaError_t classify_ids(Sorter *s, const unsigned char *given_spl, uint32_t *out,
-                                    cudaStream_t st) {
-        LevelArgs a = s->args(1, 0, given_spl);
+    static cudaError_t classify_ids(Sorter *s, const LevelArgs &a, uint32_t *out, cudaStream_t st) {
         s->tbegin(KK_SAMPLE, 0, st);
         k_sample_tree<T><<<1, kSampleThreads, sample_smem(), st>>>(a);
         s->tend(st);
@@ -112,6 +111,49 @@ struct OpsImpl {
         s->tbegin(KK_CLASSIFY_IDS, (double)n * (T::D + 4), st);
         k_classify_ids<T><<<grid, kAuxThreads, 0, st>>>(a, out);
         s->tend(st);
+        return cudaGetLastError();
+    }
+
+    // The device-planned segmented batch (graph.cuh): the input segments in
+    // chunks of at most base_cap (split, then base case), then ga.levels
+    // levels of plan -> level kernels -> emit -> base case.  Every launch
+    // has a fixed grid and reads its work counts from device memory, so the
+    // sequence depends only on (nseg_in, levels) and can be captured.
+    static cudaError_t segmented(Sorter *s, const GraphArgs &ga, cudaStream_t st) {
+        cudaError_t e;
+        const uint32_t big = (uint32_t)s->nsm * 8;
+        if ((e = cudaMemsetAsync(ga.list_count[0], 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(ga.invalid, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+        for (uint64_t i0 = 0; i0 < ga.nseg_in; i0 += ga.base_cap) {
+            const uint64_t i1 = i0 + ga.base_cap < ga.nseg_in ? i0 + ga.base_cap : ga.nseg_in;
+            if ((e = cudaMemsetAsync(ga.base_count, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+            s->tbegin(KK_PLAN, 0, st);
+            k_g_init<<<big, kAuxThreads, 0, st>>>(ga, i0, i1);
+            s->tend(st);
+            if ((e = base(s, ga.lv.data, ga.base_list, 0, ga.base_count, s->nsm, st)) != cudaSuccess)
+                return e;
+        }
+        for (int L = 0; L < ga.levels; L++) {
+            s->tbegin(KK_PLAN, 0, st);
+            k_g_plan<T><<<1, kPlanThreads, 0, st>>>(ga, L);
+            k_g_fill_stripes<T><<<big, kAuxThreads, 0, st>>>(ga);
+            s->tend(st);
+            LevelArgs a = ga.lv;
+            a.cnt = ga.counts;
+            LevelGrids g;
+            g.seg = (uint32_t)s->nsm * 4;
+            g.stripe = (uint32_t)s->nsm;
+            g.cta = (uint32_t)s->nsm * 8;
+            g.cls = big;
+            if ((e = level(s, a, g, st)) != cudaSuccess) return e;
+            s->tbegin(KK_PLAN, 0, st);
+            k_g_emit<T><<<big, kAuxThreads, 0, st>>>(ga, L);
+            s->tend(st);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = base(s, ga.lv.data, ga.base_list, 0, ga.base_count, s->nsm, st)) != cudaSuccess)
+                return e;
+        }
+        k_g_finish<<<1, 32, 0, st>>>(ga);
         return cudaGetLastError();
     }
 
@@ -126,6 +168,7 @@ struct OpsImpl {
         o.detect = &detect;
         o.reverse = &reverse;
         o.classify_ids = &classify_ids;
+        o.segmented = &segmented;
         return o;
     }
 };

@@ -25,25 +25,32 @@ enum KernelKind {
     KK_BASE,
     KK_CLASSIFY_IDS,
     KK_WAIT,
+    KK_PLAN,
     KK_COUNT
 };
 
 struct Sorter;
+struct GraphArgs;
+
+// Grid of each level kernel (work items are looped over, so any grid is
+// correct; the host planner passes the exact counts).
+struct LevelGrids {
+    uint32_t seg, stripe, cta, cls;
+};
 
 // Kernel launchers of one element type (implemented in ops_<type>.cu).
 struct TypeOps {
     int D;         // element bytes
     int key_bytes; // sizeof(K)
     cudaError_t (*init)(Sorter *);  // one-time kernel attributes
-    cudaError_t (*level)(Sorter *, uint32_t nseg, uint32_t nstripe, uint32_t ncta,
-                         const unsigned char *given_spl, cudaStream_t);
-    cudaError_t (*pack)(Sorter *, uint32_t nseg, cudaStream_t);
+    cudaError_t (*level)(Sorter *, const LevelArgs &, const LevelGrids &, cudaStream_t);
+    cudaError_t (*pack)(Sorter *, const LevelArgs &, uint32_t nseg, cudaStream_t);
     cudaError_t (*base)(Sorter *, unsigned char *data, const uint64_t *d_segs, uint32_t nsegs,
-                        cudaStream_t);
+                        const uint32_t *nsegs_dev, uint32_t grid, cudaStream_t);
     cudaError_t (*detect)(Sorter *, const unsigned char *data, uint64_t n, cudaStream_t);
     cudaError_t (*reverse)(Sorter *, unsigned char *data, uint64_t n, cudaStream_t);
-    cudaError_t (*classify_ids)(Sorter *, const unsigned char *given_spl, uint32_t *out,
-                                cudaStream_t);
+    cudaError_t (*classify_ids)(Sorter *, const LevelArgs &, uint32_t *out, cudaStream_t);
+    cudaError_t (*segmented)(Sorter *, const GraphArgs &, cudaStream_t);
 };
 
 extern const TypeOps ops_u32, ops_u64, ops_f64, ops_pair, ops_rec100;
@@ -69,16 +76,23 @@ struct Sorter {
     uint64_t arena_bytes = 256ull << 20;
     uint32_t b = 64;        // block size in elements
     uint32_t smax = 24576;  // largest segment of the base case
-    // capacities of one level batch
-    uint32_t seg_cap = 4096, stripe_cap = 8192, cta_cap = 1u << 16, move_cap = 1u << 21;
-    uint32_t base_cap = 1u << 20;
+    // capacities of one level (device-planned) or one host-planned batch
+    uint32_t seg_cap = 1u << 16;     // segments
+    uint32_t host_seg_cap = 4096;    // segments of a host-planned batch (result rows)
+    uint32_t stripe_cap = 1u << 16;  // classification stripes
+    uint32_t cta_cap = 1u << 17;     // block-permutation CTAs
+    uint32_t cls_cap = 1u << 20;     // (segment, class) pairs
+    uint32_t cnt_cap = 1u << 21;     // per-stripe class counters
+    uint32_t move_cap = 1u << 22;    // fix-up moves
+    uint32_t base_cap = 1u << 20;    // base-case segments per launch (>= cls_cap)
+    uint64_t sarr_bytes = 0, keys_bytes = 0;
     // device scratch
     SegDesc *d_seg = nullptr;
     SegState *d_st = nullptr;
-    unsigned char *d_tree = nullptr, *d_spl = nullptr;
+    unsigned char *d_sarr = nullptr, *d_keys = nullptr;
     StripeDesc *d_stripe = nullptr;
     uint32_t *d_scount = nullptr, *d_sfull = nullptr;
-    unsigned char *d_arena = nullptr, *d_ovf = nullptr;
+    unsigned char *d_arena = nullptr;
     Move *d_moves = nullptr;
     uint32_t *d_nmoves = nullptr;
     int *d_status = nullptr;
@@ -87,6 +101,8 @@ struct Sorter {
     uint64_t *d_base = nullptr;
     int *d_flags = nullptr;
     uint32_t *d_waitflag = nullptr;
+    unsigned char *d_glist = nullptr;  // two segment lists of the device planner
+    uint32_t *d_gcount = nullptr;      // LevelCounts, two list counts, base count
     // pinned host mirrors
     SegDesc *h_seg = nullptr;
     StripeDesc *h_stripe = nullptr;
@@ -111,7 +127,8 @@ struct Sorter {
     void tbegin(int kind, double bytes, cudaStream_t st);
     void tend(cudaStream_t st);
     void collect();
-    LevelArgs args(uint32_t nseg, uint32_t nstripe, const unsigned char *given_spl) const;
+    LevelArgs args(uint32_t nseg, uint32_t nstripe, uint32_t ncta, uint32_t ncls,
+                   const unsigned char *given_spl) const;
 };
 
 }  // namespace ipsgpu

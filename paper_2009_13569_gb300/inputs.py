@@ -192,6 +192,82 @@ def generate(dist, dtype, n, seed=DEFAULT_SEED, device="cpu"):
     raise ValueError("unknown dtype %r" % dtype)
 
 
+SEG_DISTS = ("uniform", "twodup", "almostsorted")
+
+
+def segment_lengths(nseg, lo_log2, hi_log2, seed=DEFAULT_SEED):
+    """nseg lengths log-uniform in [2^lo_log2, 2^hi_log2]: length i is
+    floor(2^(lo + u_i (hi - lo))) with u_i uniform in [0, 1) (stream 40).
+    Returns an int64 CPU tensor."""
+    u = _lsr(_draw(nseg, seed, 40, "cpu"), 11).to(torch.float64) * 2.0 ** -53
+    return torch.floor(torch.pow(2.0, lo_log2 + u * (hi_log2 - lo_log2))).to(torch.int64)
+
+
+def _draw_at(idx, seed, stream):
+    return splitmix64(idx, _stream(seed, stream))
+
+
+def segmented_batch(lengths, dists=SEG_DISTS, seed=DEFAULT_SEED, device="cpu",
+                    chunk_elems=1 << 26):
+    """A batch of independent uint64 arrays stored back to back: array i has
+    lengths[i] elements drawn from dists[i % len(dists)], where
+      uniform       uniform in [0, 2^64)   (stream 41, by global position)
+      twodup        (j^2 + m/2) mod m      (j: position in the array, m: its length)
+      almostsorted  0..m-1 with about sqrt(m) disjoint adjacent swaps: pair
+                    (2q, 2q+1) is swapped for every q drawn an odd number of
+                    times among sqrt(m) draws q uniform in [0, (m-1)/2)
+                    (stream 42, by array)
+    Returns (data int64 (sum lengths,), offsets int64 (nseg + 1,)) on `device`;
+    offsets[i] is the first element of array i.  Generated in chunks of whole
+    arrays of about chunk_elems elements."""
+    lengths = torch.as_tensor(lengths, dtype=torch.int64).cpu()
+    nseg = lengths.numel()
+    offsets = torch.zeros(nseg + 1, dtype=torch.int64)
+    offsets[1:] = torch.cumsum(lengths, 0)
+    total = int(offsets[-1])
+    data = torch.empty(total, dtype=torch.int64, device=device)
+    kind = torch.arange(nseg, dtype=torch.int64) % len(dists)
+    codes = {"uniform": 0, "twodup": 1, "almostsorted": 2}
+    kind = torch.tensor([codes[d] for d in dists], dtype=torch.int64)[kind]
+    s0 = 0
+    while s0 < nseg:
+        s1 = s0
+        acc = 0
+        while s1 < nseg and (s1 == s0 or acc + int(lengths[s1]) <= chunk_elems):
+            acc += int(lengths[s1])
+            s1 += 1
+        e0, e1 = int(offsets[s0]), int(offsets[s1])
+        if e1 > e0:
+            lens = lengths[s0:s1].to(device)
+            sid = torch.repeat_interleave(torch.arange(s1 - s0, device=device), lens)
+            start = offsets[s0:s1].to(device)
+            gidx = torch.arange(e0, e1, dtype=torch.int64, device=device)
+            loc = gidx - start[sid]
+            m = lens[sid]
+            k = kind[s0:s1].to(device)[sid]
+            uni = _draw_at(gidx, seed, 41)
+            two = (loc * loc + m // 2) % m
+            v = torch.where(k == 0, uni, torch.where(k == 1, two, loc))
+            data[e0:e1] = v
+            # almost sorted arrays: disjoint adjacent swaps
+            al = [i for i in range(s0, s1) if int(kind[i]) == 2 and int(lengths[i]) >= 4]
+            for i in al:
+                mlen = int(lengths[i])
+                nsw = math.isqrt(mlen)
+                npair = (mlen - 1) // 2
+                q = _umod(_draw_at(torch.arange(nsw, dtype=torch.int64) + (i << 32), seed, 42),
+                          npair)
+                uq, cnt = torch.unique(q, return_counts=True)
+                uq = uq[cnt % 2 == 1]
+                if uq.numel():
+                    a = int(offsets[i]) + 2 * uq.to(device)
+                    x = data[a].clone()
+                    data[a] = data[a + 1]
+                    data[a + 1] = x
+        s0 = s1
+    return data, offsets.to(device)
+
+
 def to_numpy(t, dtype):
     """Storage tensor -> numpy array in the oracle's conventions."""
     a = t.detach().cpu().contiguous().numpy()

@@ -59,6 +59,11 @@ def load():
         "ipsgpu_kernel_name": (ctypes.c_char_p, [i32]),
         "ipsgpu_debug_bounded_wait": (i32, [vp, u32, vp]),
         "ipsgpu_partition_level_noalloc": (i32, [i32, vp, u64, vp, u32, i32, vp, vp]),
+        "ipsgpu_sort_segmented": (i32, [vp, vp, u64, vp, u64, vp]),
+        "ipsgpu_segmented_graph_create": (i32, [vp, vp, u64, vp, u64, ctypes.POINTER(vp)]),
+        "ipsgpu_graph_launch": (i32, [vp, vp]),
+        "ipsgpu_graph_nodes": (i32, [vp, ctypes.POINTER(u64)]),
+        "ipsgpu_graph_destroy": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -74,7 +79,9 @@ def exported_symbols():
         "ipsgpu_sorter_create", "ipsgpu_sorter_destroy", "ipsgpu_scratch_bytes", "ipsgpu_sort",
         "ipsgpu_partition_level", "ipsgpu_radix_level", "ipsgpu_classify", "ipsgpu_status",
         "ipsgpu_strerror", "ipsgpu_set_timing", "ipsgpu_kernel_stats", "ipsgpu_kernel_name",
-        "ipsgpu_debug_bounded_wait", "ipsgpu_partition_level_noalloc",
+        "ipsgpu_debug_bounded_wait", "ipsgpu_partition_level_noalloc", "ipsgpu_sort_segmented",
+        "ipsgpu_segmented_graph_create", "ipsgpu_graph_launch", "ipsgpu_graph_nodes",
+        "ipsgpu_graph_destroy",
     ]
 
 
@@ -139,6 +146,16 @@ class Sorter:
     def sort(self, ptr, n, stream=0):
         _check(load().ipsgpu_sort(self._h, ptr, n, stream), "ipsgpu_sort")
 
+    def sort_segmented(self, ptr, n, offsets_ptr, num_segments, stream=0):
+        """Sort segments [offsets[i], offsets[i+1]) of the n-element array in
+        place; offsets_ptr points to num_segments + 1 u64 in device memory."""
+        _check(load().ipsgpu_sort_segmented(self._h, ptr, n, offsets_ptr, num_segments, stream),
+               "ipsgpu_sort_segmented")
+
+    def segmented_graph(self, ptr, n, offsets_ptr, num_segments):
+        """Capture a segmented sort over these buffers into a CUDA graph."""
+        return SegmentedGraph(self, ptr, n, offsets_ptr, num_segments)
+
     def partition_level(self, ptr, n, spl_ptr, num_splitters, equal_buckets, bb_ptr, stream=0):
         _check(load().ipsgpu_partition_level(self._h, ptr, n, spl_ptr, num_splitters,
                                              1 if equal_buckets else 0, bb_ptr, stream),
@@ -175,3 +192,35 @@ class Sorter:
     def debug_bounded_wait(self, spin_limit, stream=0):
         _check(load().ipsgpu_debug_bounded_wait(self._h, spin_limit, stream),
                "ipsgpu_debug_bounded_wait")
+
+
+class SegmentedGraph:
+    """An ipsgpu_graph: one segmented sort over fixed buffers, replayed by
+    launch().  Keeps its sorter alive."""
+
+    def __init__(self, sorter, ptr, n, offsets_ptr, num_segments):
+        self.sorter = sorter
+        h = ctypes.c_void_p()
+        _check(load().ipsgpu_segmented_graph_create(sorter._h, ptr, n, offsets_ptr, num_segments,
+                                                    ctypes.byref(h)),
+               "ipsgpu_segmented_graph_create")
+        self._h = h
+
+    def launch(self, stream=0):
+        _check(load().ipsgpu_graph_launch(self._h, stream), "ipsgpu_graph_launch")
+
+    def nodes(self):
+        v = ctypes.c_uint64()
+        _check(load().ipsgpu_graph_nodes(self._h, ctypes.byref(v)), "ipsgpu_graph_nodes")
+        return int(v.value)
+
+    def close(self):
+        if self._h:
+            load().ipsgpu_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

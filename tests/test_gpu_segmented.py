@@ -1,0 +1,181 @@
+"""GPU parity of the segmented batch (many independent arrays sorted by one
+device-planned launch sequence, Sec. 3.2 recursion breadth-first over the
+whole batch) through the C ABI against the oracle, segment by segment: mixed
+lengths that span tiny arrays, the base-case boundary and several
+partitioning levels; every element type; the radix variant; the captured
+CUDA graph replayed on refilled buffers; empty, single-element and uncovered
+ranges; and invalid offsets."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2009_13569_gb300 import inputs, ipsgpu
+from _util import DEV, assert_sorted_parity, stream, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SMAX_U64 = 184 * 1024 // 8  # default base-case capacity for 8-byte elements
+
+
+def _offsets_dev(offsets):
+    return torch.as_tensor(offsets, dtype=torch.int64).to(DEV).contiguous()
+
+
+def _check_segments(got, inp, offsets, dtype):
+    for i in range(len(offsets) - 1):
+        lo, hi = int(offsets[i]), int(offsets[i + 1])
+        if hi - lo > 1:
+            assert_sorted_parity(got[lo:hi], inp[lo:hi], dtype)
+        elif hi - lo == 1:
+            np.testing.assert_array_equal(got[lo:hi], inp[lo:hi])
+
+
+def _run(dtype, host, offsets, **params):
+    n = inputs.count(host, dtype)
+    d = to_dev(host)
+    off = _offsets_dev(offsets)
+    with ipsgpu.Sorter(dtype, **params) as s:
+        s.sort_segmented(d.data_ptr(), n, off.data_ptr(), len(offsets) - 1, stream())
+        st = s.status(stream())
+    assert st == ipsgpu.OK, ipsgpu.strerror(st)
+    return inputs.to_numpy(d.cpu(), dtype)
+
+
+def _concat(dtype, lengths, dists, seed):
+    parts = [inputs.generate(dists[i % len(dists)], dtype, int(m), seed=seed + i)
+             for i, m in enumerate(lengths)]
+    offsets = np.zeros(len(lengths) + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(lengths)
+    return torch.cat(parts, 0).contiguous(), offsets
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_segmented_u64_mixed_lengths(seed):
+    # log-uniform lengths 2^0 .. 2^18: tiny arrays, the base case, one and two levels
+    lengths = inputs.segment_lengths(300, 0, 18, seed=seed)
+    data, offsets = inputs.segmented_batch(lengths, seed=seed)
+    got = _run("u64", data, offsets.numpy())
+    _check_segments(got, inputs.to_numpy(data, "u64"), offsets.numpy(), "u64")
+
+
+def test_segmented_u64_base_case_boundary():
+    lengths = [SMAX_U64 - 1, SMAX_U64, SMAX_U64 + 1, 2 * SMAX_U64 + 3, 1, 0, 2, 33, 200_001]
+    data, offsets = inputs.segmented_batch(lengths, seed=9)
+    got = _run("u64", data, offsets.numpy())
+    _check_segments(got, inputs.to_numpy(data, "u64"), offsets.numpy(), "u64")
+
+
+@pytest.mark.parametrize("dtype", ["u32", "f64", "pair", "rec100"])
+def test_segmented_other_types(dtype):
+    if dtype == "rec100":
+        lengths, dists = [5000, 1, 30_000, 700, 9000, 12], inputs.REC_DISTS
+    elif dtype == "f64":
+        lengths, dists = [100_000, 3, 50_000, 20_000, 64, 130_000], inputs.F64_DISTS
+    else:
+        lengths, dists = [120_000, 3, 90_000, 20_000, 64, 130_000, 7], \
+            ("uniform", "twodup", "zipf", "rootdup")
+    host, offsets = _concat(dtype, lengths, dists, seed=77)
+    got = _run(dtype, host, offsets)
+    _check_segments(got, inputs.to_numpy(host, dtype), offsets, dtype)
+
+
+@pytest.mark.parametrize("dtype", ["u32", "u64", "pair"])
+def test_segmented_radix(dtype):
+    host, offsets = _concat(dtype, [150_000, 40_000, 5, 260_000], ("uniform", "exponential"),
+                            seed=5)
+    got = _run(dtype, host, offsets, algo=ipsgpu.RADIX)
+    _check_segments(got, inputs.to_numpy(host, dtype), offsets, dtype)
+
+
+@pytest.mark.parametrize("base_case", [32, 300])
+def test_segmented_small_base_case_many_levels(base_case):
+    lengths = inputs.segment_lengths(40, 4, 17, seed=base_case)
+    data, offsets = inputs.segmented_batch(lengths, seed=base_case)
+    got = _run("u64", data, offsets.numpy(), base_case=base_case)
+    _check_segments(got, inputs.to_numpy(data, "u64"), offsets.numpy(), "u64")
+
+
+def test_segmented_many_tiny():
+    # 20,000 arrays of at most 64 elements: all go straight to the base case
+    lengths = inputs.segment_lengths(20_000, 0, 6, seed=3)
+    data, offsets = inputs.segmented_batch(lengths, seed=3)
+    got = _run("u64", data, offsets.numpy())
+    _check_segments(got, inputs.to_numpy(data, "u64"), offsets.numpy(), "u64")
+
+
+def test_segmented_partial_cover_leaves_rest():
+    # segments cover [100, 60100) and [70000, 190000) only; the gaps stay as they were
+    host = inputs.generate("uniform", "u64", 200_000, seed=4)
+    offsets = np.array([100, 60_100, 60_100, 70_000], dtype=np.int64)
+    d = to_dev(host)
+    off = _offsets_dev([100, 60_100, 70_000, 190_000])
+    with ipsgpu.Sorter("u64") as s:
+        s.sort_segmented(d.data_ptr(), 200_000, off.data_ptr(), 3, stream())
+        assert s.status(stream()) == ipsgpu.OK
+    got = inputs.to_numpy(d.cpu(), "u64")
+    inp = inputs.to_numpy(host, "u64")
+    np.testing.assert_array_equal(got[:100], inp[:100])
+    np.testing.assert_array_equal(got[190_000:], inp[190_000:])
+    _check_segments(got, inp, [100, 60_100, 70_000, 190_000], "u64")
+    del offsets
+
+
+def test_segmented_invalid_offsets_reported():
+    host = inputs.generate("uniform", "u64", 50_000, seed=6)
+    d = to_dev(host)
+    # segment 1 runs backwards, segment 2 past the end: both skipped, E_INVAL recorded
+    off = _offsets_dev([0, 30_000, 20_000, 60_000])
+    with ipsgpu.Sorter("u64") as s:
+        s.sort_segmented(d.data_ptr(), 50_000, off.data_ptr(), 3, stream())
+        assert s.status(stream()) == ipsgpu.E_INVAL
+        assert s.status(stream()) == ipsgpu.OK  # cleared by the read
+    got = inputs.to_numpy(d.cpu(), "u64")
+    inp = inputs.to_numpy(host, "u64")
+    np.testing.assert_array_equal(got[:30_000], oracle.sort(inp[:30_000], "u64"))
+    np.testing.assert_array_equal(got[30_000:], inp[30_000:])
+
+
+def test_segmented_empty_batches():
+    d = torch.zeros(16, dtype=torch.int64, device=DEV)
+    off = _offsets_dev([0])
+    with ipsgpu.Sorter("u64") as s:
+        s.sort_segmented(d.data_ptr(), 16, off.data_ptr(), 0, stream())
+        s.sort_segmented(d.data_ptr(), 0, off.data_ptr(), 0, stream())
+        assert s.status(stream()) == ipsgpu.OK
+        with pytest.raises(ipsgpu.IpsgpuError):
+            s.sort_segmented(d.data_ptr(), 16, 0, 3, stream())
+
+
+def test_segmented_graph_replay_refilled():
+    lengths = inputs.segment_lengths(120, 2, 17, seed=21)
+    data1, offsets = inputs.segmented_batch(lengths, seed=21)
+    data2, _ = inputs.segmented_batch(lengths, seed=22)
+    n = data1.numel()
+    d = to_dev(data1)
+    off = offsets.to(DEV)
+    with ipsgpu.Sorter("u64") as s:
+        g = s.segmented_graph(d.data_ptr(), n, off.data_ptr(), len(lengths))
+        assert g.nodes() > 10
+        for host in (data1, data2, data1):
+            d.copy_(host.to(DEV))
+            g.launch(stream())
+            assert s.status(stream()) == ipsgpu.OK
+            _check_segments(inputs.to_numpy(d.cpu(), "u64"), inputs.to_numpy(host, "u64"),
+                            offsets.numpy(), "u64")
+        g.close()
+
+
+def test_segmented_matches_per_array_sort():
+    # the batch gives, array by array, exactly what one plain sort per array gives
+    lengths = inputs.segment_lengths(25, 8, 17, seed=31)
+    data, offsets = inputs.segmented_batch(lengths, seed=31)
+    o = offsets.numpy()
+    batch = _run("u64", data, o)
+    d = to_dev(data)
+    with ipsgpu.Sorter("u64") as s:
+        for i in range(len(lengths)):
+            lo, hi = int(o[i]), int(o[i + 1])
+            s.sort(d[lo:hi].data_ptr(), hi - lo, stream())
+        assert s.status(stream()) == ipsgpu.OK
+    np.testing.assert_array_equal(batch, inputs.to_numpy(d.cpu(), "u64"))
