@@ -20,9 +20,10 @@
  *     call on them is in flight.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls are asynchronous with respect to the host unless a
- *     function says it synchronizes.  ipsgpu_sort synchronizes `stream`
- *     once per recursion level (it reads bucket boundaries back to plan the
- *     next level) and returns after the last kernel has been enqueued.
+ *     function says it synchronizes.  The sorts (ipsgpu_sort,
+ *     ipsgpu_sort_segmented, ipsgpu_sort_batch) plan every recursion level
+ *     on the device and never synchronize; the single-level calls wait for
+ *     their previous call's descriptor upload.
  *   - Return values are status codes (IPSGPU_OK = 0).  Errors detected by
  *     kernels (a bounded wait that ran out, an inconsistent count) are kept
  *     in a device status word of the sorter and reported by ipsgpu_status.
@@ -115,7 +116,9 @@ uint64_t ipsgpu_scratch_bytes(const ipsgpu_params *params, int dtype);
 
 /* Sort d_data[0..n) in place, ascending in the key order of the sorter's
  * dtype (Sec. 2 problem statement; Sec. 3 and 5).  Detects non-decreasing
- * inputs (returns) and non-increasing ones (reverses them) first (Sec. 5).
+ * inputs (left as they are) and non-increasing ones (reversed) first
+ * (Sec. 5), on the device.  Asynchronous: never synchronizes, and can be
+ * captured into a CUDA graph.
  * For U32/U64/F64 the result is the unique sorted sequence; for PAIR_U64
  * and REC100 records with equal keys may appear in any order.
  * Errors: E_INVAL, E_CUDA; kernel-side errors via ipsgpu_status. */
@@ -164,6 +167,18 @@ int ipsgpu_radix_level(ipsgpu_sorter *s, void *d_data, uint64_t n, uint32_t shif
  * Errors: E_INVAL (NULL or misaligned pointers, n > 2^40), E_CUDA. */
 int ipsgpu_sort_segmented(ipsgpu_sorter *s, void *d_data, uint64_t n,
                           const uint64_t *d_offsets, uint64_t num_segments, void *stream);
+
+/* Sort many separate arrays in one call: array i starts at the device
+ * address d_segs[2i] (aligned as for ipsgpu_sort) and has d_segs[2i+1]
+ * elements; d_segs holds 2 * num_segments u64 in device memory.  Each array
+ * is sorted in place exactly as ipsgpu_sort_segmented would sort it; the
+ * arrays must not overlap.  max_n must be at least the largest length (it
+ * fixes the number of levels that are launched).  Asynchronous, never
+ * synchronizes, capturable; an entry with a NULL or misaligned address (and
+ * n > 0) or n > 2^40 is skipped and recorded as E_INVAL in the status word.
+ * Errors: E_INVAL (max_n > 2^40, misaligned d_segs), E_CUDA. */
+int ipsgpu_sort_batch(ipsgpu_sorter *s, const uint64_t *d_segs, uint64_t num_segments,
+                      uint64_t max_n, void *stream);
 
 /* A segmented sort captured once into an instantiated CUDA graph: the same
  * launch sequence as ipsgpu_sort_segmented over fixed buffers (d_data,

@@ -52,8 +52,11 @@ __global__ void __launch_bounds__(kDetectThreads) k_detect(const unsigned char *
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_reverse(unsigned char *data, uint64_t n) {
+__global__ void __launch_bounds__(256) k_reverse(unsigned char *data, uint64_t n,
+                                                 const int *flags) {
     typedef typename T::E E;
+    // reverse only an input that is non-increasing and not also non-decreasing
+    if (!(flags[1] && !flags[0])) return;
     E *a = reinterpret_cast<E *>(data);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n / 2;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -75,7 +78,8 @@ __device__ __forceinline__ Key80 shfl_key<TRec100>(Key80 k, int src) {
     return r;
 }
 
-// Sorts each listed segment (segs[2i] = begin, segs[2i+1] = n, n <= smax)
+// Sorts each listed segment (segs[2i] = device byte address, segs[2i+1] = n,
+// n <= smax)
 // in place; the number of segments is *nsegs_dev if given, else nsegs_host.  The segment is first staged into shared memory with cp.async
 // (one round trip).  A pass over a range [a0, a0+len) then takes min/max and
 // a histogram of an MSD radix digit of (key - min) from shared memory, and
@@ -85,8 +89,8 @@ __device__ __forceinline__ Key80 shfl_key<TRec100>(Key80 k, int src) {
 // Every pass writes its range back to global memory, so the global copy of
 // a pending range always matches the shared one.
 template <class T>
-__global__ void __launch_bounds__(kBaseThreads, 1) k_base(unsigned char *data,
-                                                          const uint64_t *segs, uint32_t nsegs_host,
+__global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
+                                                          uint32_t nsegs_host,
                                                           const uint32_t *nsegs_dev, int *status) {
     typedef typename T::E E;
     typedef typename T::K K;
@@ -110,8 +114,8 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(unsigned char *data,
 
     const uint32_t nsegs = nsegs_dev ? *nsegs_dev : nsegs_host;
     for (uint32_t si = blockIdx.x; si < nsegs; si += gridDim.x) {
-        const uint64_t begin = segs[2 * si], n = segs[2 * si + 1];
-        E *g = reinterpret_cast<E *>(data) + begin;
+        const uint64_t addr = segs[2 * si], n = segs[2 * si + 1];
+        E *g = reinterpret_cast<E *>(addr);
         if (n <= 1) continue;
         if (n <= 32) {
             // rank sort by one warp

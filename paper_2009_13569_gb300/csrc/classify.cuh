@@ -324,8 +324,8 @@ __global__ void __launch_bounds__(ClsCfg<T>::NT, 1) k_classify(LevelArgs a) {
         tot[j] = 0;
     }
     if (tid == 0) sh_wblk = 0;
-    const E *segbase = reinterpret_cast<const E *>(a.data) + sd.begin;
-    E *segw = reinterpret_cast<E *>(a.data) + sd.begin;
+    const E *segbase = reinterpret_cast<const E *>(sd.addr);
+    E *segw = reinterpret_cast<E *>(sd.addr);
     const uint64_t e0 = (uint64_t)sp.blk0 * b;
     uint64_t e1 = (uint64_t)(sp.blk0 + sp.nblk) * b;
     if (e1 > sd.n) e1 = sd.n;

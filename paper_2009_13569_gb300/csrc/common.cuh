@@ -120,7 +120,7 @@ struct TRec100 {
 // Planned description of one segment partitioned in a level launch (written
 // by the host planner, or on the device for the segmented batch).
 struct SegDesc {
-    uint64_t begin;      // element offset of the segment in the data array
+    uint64_t addr;       // device byte address of the segment's first element
     uint64_t n;          // elements
     uint32_t b;          // block size in elements
     uint32_t C;          // class budget (power of two <= 256): bounds B

@@ -2,8 +2,10 @@
 // of Sec. 3.2 planned level by level by kernels instead of the host, so the
 // whole batch is one fixed sequence of launches (capturable in a CUDA graph).
 //
-//   k_g_init          splits the input arrays: one element or fewer: done;
-//                     at most the base-case size: base list; else level 0
+//   k_g_init          splits the input arrays (offsets into one array, a list
+//                     of (address, length) pairs, or one whole array): one
+//                     element or fewer: done; at most the base-case size:
+//                     base list; else level 0
 //   k_g_plan          one CTA plans a level: class budget, stripes, CTAs and
 //                     arena offsets of every segment (prefix sums)
 //   k_g_fill_stripes  stripe descriptors and the CTA -> segment map
@@ -21,7 +23,7 @@ constexpr int kPlanThreads = 1024;
 constexpr uint32_t kMinStripeElems = 1u << 15;
 
 struct GList {
-    uint64_t begin, n;
+    uint64_t addr, n;          // device byte address of the first element, elements
     uint32_t shift, pad;
 };
 
@@ -30,12 +32,17 @@ struct GraphArgs {
     LevelCounts *counts;       // device: counts of the level being run
     GList *list[2];            // ping-pong lists of segments to partition
     uint32_t *list_count[2];
-    uint64_t *base_list;       // (begin, n) pairs for the base case
+    uint64_t *base_list;       // (address, n) pairs for the base case
     uint32_t *base_count;
     uint32_t *invalid;         // set when an input segment had bad offsets
-    const uint64_t *offsets;   // input: nseg_in + 1 element offsets
+    // input, one of: offsets (nseg_in + 1 element offsets into lv.data),
+    // segs (nseg_in (address, n) pairs), or neither (all of lv.data)
+    const uint64_t *offsets;
+    const uint64_t *segs;
+    const int *skip_flags;     // if set: skip the input when flags[0] or flags[1]
     uint64_t nseg_in;
-    uint64_t n_total;          // elements of the data array
+    uint64_t n_total;          // elements of lv.data (offsets mode, single array)
+    uint32_t elem_bytes, elem_align;
     uint32_t list_cap, base_cap, seg_cap, stripe_cap, cta_cap, cls_cap, cnt_cap;
     uint32_t smax, k, b, nsm, kbits, keybits;
     uint64_t arena_bytes, sarr_bytes, keys_bytes;
@@ -64,10 +71,10 @@ __device__ inline uint64_t g_al256(uint64_t x) { return (x + 255) & ~(uint64_t)2
 // Appends to a bounded list.  An append past the capacity is undone, so once
 // the appending kernel has finished the count never exceeds the capacity and
 // every entry below it is written; the overflow is reported as E_NOMEM.
-__device__ inline void g_push_base(const GraphArgs &g, uint64_t begin, uint64_t n) {
+__device__ inline void g_push_base(const GraphArgs &g, uint64_t addr, uint64_t n) {
     const uint32_t q = atomicAdd(g.base_count, 1u);
     if (q < g.base_cap) {
-        g.base_list[2 * q] = begin;
+        g.base_list[2 * q] = addr;
         g.base_list[2 * q + 1] = n;
     } else {
         atomicSub(g.base_count, 1u);
@@ -95,24 +102,40 @@ __device__ inline uint64_t g_left_bytes(uint32_t C, uint32_t b) {
     return g_al256((uint64_t)C * b * T::D);
 }
 
-// Input segments [i0, i1): offsets must be non-decreasing and within the
-// data array; a segment that is not is skipped, and k_g_finish reports
-// E_INVAL once the valid segments are sorted.
+// Input segments [i0, i1).  Offsets must be non-decreasing and within the
+// data array, listed arrays aligned to the element type; a segment that is
+// not is skipped, and k_g_finish reports E_INVAL once the valid segments are
+// sorted.  Segments of at most the base-case size go to the base list, the
+// others to the first level.
 static __global__ void __launch_bounds__(256) k_g_init(GraphArgs g, uint64_t i0, uint64_t i1) {
+    if (g.skip_flags && (g.skip_flags[0] || g.skip_flags[1])) return;  // sorted (or reversed)
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = i0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < i1; i += stride) {
-        const uint64_t b0 = g.offsets[i], b1 = g.offsets[i + 1];
-        if (b1 < b0 || b1 > g.n_total) {
-            *g.invalid = 1;
-            continue;
-        }
-        if (b1 <= b0 + 1) continue;
-        const uint64_t n = b1 - b0;
-        if (n <= g.smax) {
-            g_push_base(g, b0, n);
+        uint64_t addr, n;
+        if (g.offsets) {
+            const uint64_t b0 = g.offsets[i], b1 = g.offsets[i + 1];
+            if (b1 < b0 || b1 > g.n_total) {
+                *g.invalid = 1;
+                continue;
+            }
+            addr = (uint64_t)(uintptr_t)g.lv.data + b0 * g.elem_bytes;
+            n = b1 - b0;
+        } else if (g.segs) {
+            addr = g.segs[2 * i];
+            n = g.segs[2 * i + 1];
+            if ((n > 0 && (addr == 0 || addr % g.elem_align)) || n > (1ull << 40)) {
+                *g.invalid = 1;
+                continue;
+            }
         } else {
-            g_push_list(g, 0, GList{b0, n, g.keybits > g.kbits ? g.keybits - g.kbits : 0u, 0u});
+            addr = (uint64_t)(uintptr_t)g.lv.data;
+            n = g.n_total;
         }
+        if (n <= 1) continue;
+        if (n <= g.smax)
+            g_push_base(g, addr, n);
+        else
+            g_push_list(g, 0, GList{addr, n, g.keybits > g.kbits ? g.keybits - g.kbits : 0u, 0u});
     }
 }
 
@@ -237,7 +260,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_g_plan(GraphArgs g, int L) {
     for (uint32_t i = r0; i < r1 && nin; i++) {
         const GPlanItem it = g_item<T>(g, in[i].n, stripe_elems, bpc);
         SegDesc d;
-        d.begin = in[i].begin;
+        d.addr = in[i].addr;
         d.n = in[i].n;
         d.b = g.b;
         d.C = it.C;
@@ -345,9 +368,9 @@ __global__ void __launch_bounds__(256) k_g_emit(GraphArgs g, int L) {
             shift = sd.radix_shift >= g.kbits ? sd.radix_shift - g.kbits : 0u;
         }
         if (n <= g.smax) {
-            g_push_base(g, sd.begin + b0, n);
+            g_push_base(g, sd.addr + b0 * T::D, n);
         } else if (L + 1 < g.levels) {
-            g_push_list(g, (L + 1) & 1, GList{sd.begin + b0, n, shift, 0u});
+            g_push_list(g, (L + 1) & 1, GList{sd.addr + b0 * T::D, n, shift, 0u});
         } else {
             set_status(g.lv.status, IPSGPU_E_INTERNAL);  // deeper than planned
         }

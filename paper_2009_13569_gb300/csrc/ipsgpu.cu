@@ -23,7 +23,6 @@ struct ipsgpu_sorter {
 namespace {
 
 constexpr uint64_t kMinStripe = 1u << 15;  // elements
-constexpr int kResStride = kMaxClasses + 3;
 
 __global__ void k_debug_wait(uint32_t *flag, uint32_t limit, int *status) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -49,6 +48,10 @@ uint64_t next_pow2(uint64_t x) {
 }
 
 uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// alignment the kernels need of a data array: the element size (4 bytes for
+// rec100), at most 16
+uint64_t elem_align(int D) { return D == 100 ? 4 : (uint64_t)std::min(D, 16); }
 
 // block size in elements: block_bytes / D rounded down to a power of two
 uint32_t block_elems(uint32_t block_bytes, int D) {
@@ -88,10 +91,10 @@ int resolve(const ipsgpu_params *p, int dtype, Resolved *r) {
 }
 
 struct Layout {
-    uint64_t seg, st, sarr, keys, stripe, scount, sfull, arena, moves, cta, res, base, glist, misc;
+    uint64_t seg, st, sarr, keys, stripe, scount, sfull, arena, moves, cta, base, glist, misc;
     uint64_t total() const {
-        return seg + st + sarr + keys + stripe + scount + sfull + arena + moves + cta + res + base +
-               glist + misc;
+        return seg + st + sarr + keys + stripe + scount + sfull + arena + moves + cta + base + glist +
+               misc;
     }
 };
 
@@ -110,7 +113,6 @@ Layout layout(const Sorter &s, int key_bytes) {
     L.arena = s.arena_bytes;
     L.moves = (uint64_t)s.move_cap * sizeof(Move);
     L.cta = (uint64_t)s.cta_cap * sizeof(uint32_t);
-    L.res = (uint64_t)s.host_seg_cap * kResStride * sizeof(uint64_t);
     L.base = (uint64_t)s.base_cap * 2 * sizeof(uint64_t);
     L.glist = 2ull * s.seg_cap * sizeof(GList);
     L.misc = 256;
@@ -139,11 +141,11 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? IPSGPU_OK : IPSGPU_E_
 void free_all(Sorter &s) {
     void *dev[] = {s.d_seg,    s.d_st,     s.d_sarr,   s.d_keys,    s.d_stripe,
                    s.d_scount, s.d_sfull,  s.d_arena,  s.d_moves,   s.d_nmoves,
-                   s.d_status, s.d_cta_seg, s.d_res,   s.d_base,    s.d_flags,
+                   s.d_status, s.d_cta_seg, s.d_base,    s.d_flags,
                    s.d_waitflag, s.d_glist, s.d_gcount};
     for (void *p : dev)
         if (p) cudaFree(p);
-    void *host[] = {s.h_seg, s.h_stripe, s.h_cta_seg, s.h_res, s.h_base, s.h_flags};
+    void *host[] = {s.h_seg, s.h_stripe, s.h_cta_seg, s.h_flags};
     for (void *p : host)
         if (p) cudaFreeHost(p);
     for (auto &l : s.launches) {
@@ -156,12 +158,13 @@ void free_all(Sorter &s) {
 
 // ------------------------------------------------------------------ levels
 struct Pending {
-    uint64_t begin, n;
-    uint32_t shift;  // radix: the digit to use is bits [shift, shift+bits)
+    uint64_t addr, n;  // device byte address of the first element, elements
+    uint32_t shift;    // radix: the digit to use is bits [shift, shift+bits)
 };
 
 // class budget of a segment (the adaptive k of Sec. 3.2, re-targeted so that
-// children fit the shared-memory base case)
+// children fit the shared-memory base case); the device planner uses the
+// same rule
 uint32_t class_budget(const Sorter &s, uint64_t n) {
     uint64_t want = next_pow2((n + s.smax / 2 - 1) / (s.smax / 2));
     if (want < 4) want = 4;
@@ -174,99 +177,79 @@ struct BatchPlan {
     uint64_t arena = 0, elems = 0, sarr = 0, keys = 0;
 };
 
-// Plans segments [i, j) of `list` into the pinned descriptors, up to the
-// capacities; returns j.
-size_t plan_batch(Sorter &s, const std::vector<Pending> &list, size_t i, uint32_t mode,
-                  uint32_t nsplit, int eq_given, uint32_t radix_bits, uint64_t stripe_elems,
-                  uint64_t blocks_per_cta, BatchPlan &bp) {
+// Plans one segment of a single partitioning step (given splitters or one
+// radix digit) into the pinned descriptors.
+int plan_single(Sorter &s, const Pending &pd, uint32_t mode, uint32_t nsplit, int eq_given,
+                uint32_t radix_bits, uint64_t stripe_elems, uint64_t blocks_per_cta,
+                BatchPlan &bp) {
     const uint64_t D = s.ops->D;
-    size_t j = i;
-    for (; j < list.size(); j++) {
-        const Pending &pd = list[j];
-        uint32_t C;
-        if (mode == 1) {
-            uint64_t K = next_pow2((uint64_t)nsplit + 1);
-            C = (uint32_t)(eq_given ? 2 * K : K);
-        } else if (mode == 2) {
-            C = 1u << radix_bits;
-        } else {
-            C = class_budget(s, pd.n);
-        }
-        const uint64_t nb = (pd.n + s.b - 1) / s.b;
-        uint64_t p = (pd.n + stripe_elems - 1) / stripe_elems;
-        if (p < 1) p = 1;
-        if (p > nb) p = nb;
-        uint64_t nc = (nb + blocks_per_cta - 1) / blocks_per_cta;
-        if (nc < 1) nc = 1;
-        // arena: cleanup staging (C blocks) directly followed by the overflow
-        // block, then C leftover buffer blocks per stripe
-        const uint64_t stageb = align_up((uint64_t)C * s.b * D + (uint64_t)s.b * D, 256);
-        const uint64_t bufb = align_up((uint64_t)C * s.b * D, 256);
-        const uint64_t arena_need = stageb + p * bufb;
-        const uint64_t move_need = 2 * (p + C) + 4;
-        const uint64_t sarr_need = seg_arrays_bytes(C);
-        const uint64_t keys_need = align_up(2ull * C * s.ops->key_bytes, 16);
-        if (bp.nseg + 1 > std::min(s.seg_cap, s.host_seg_cap) || bp.nstripe + p > s.stripe_cap ||
-            bp.ncta + nc > s.cta_cap || bp.arena + arena_need > s.arena_bytes ||
-            bp.nmoves + move_need > s.move_cap || bp.ncls + C > s.cls_cap ||
-            bp.ncnt + (uint64_t)C * p > s.cnt_cap || bp.sarr + sarr_need > s.sarr_bytes ||
-            bp.keys + keys_need > s.keys_bytes) {
-            if (bp.nseg == 0) return (size_t)-1;  // one segment does not fit at all
-            break;
-        }
-        SegDesc &sd = s.h_seg[bp.nseg];
-        memset(&sd, 0, sizeof sd);
-        sd.begin = pd.begin;
-        sd.n = pd.n;
-        sd.b = s.b;
-        sd.C = C;
-        sd.stripe0 = bp.nstripe;
-        sd.nstripes = (uint32_t)p;
-        sd.cta0 = bp.ncta;
-        sd.ncta = (uint32_t)nc;
-        sd.stage_off = bp.arena;
-        sd.arr_off = bp.sarr;
-        sd.key_off = bp.keys;
-        sd.cls0 = bp.ncls;
-        sd.cnt0 = bp.ncnt;
-        sd.mode = mode;
-        sd.radix_shift = pd.shift;
-        sd.radix_bits = radix_bits;
-        sd.nsplit = nsplit;
-        sd.eq_given = eq_given ? 1 : 0;
-        uint64_t off = bp.arena + stageb;
-        for (uint64_t q = 0; q < p; q++) {
-            StripeDesc &sp = s.h_stripe[bp.nstripe + q];
-            sp.seg = bp.nseg;
-            const uint64_t b0 = q * nb / p, b1 = (q + 1) * nb / p;
-            sp.blk0 = (uint32_t)b0;
-            sp.nblk = (uint32_t)(b1 - b0);
-            sp.cnt_off = (uint32_t)(bp.ncnt + q * C);
-            sp.left_off = off;
-            off += bufb;
-        }
-        for (uint64_t c = 0; c < nc; c++) s.h_cta_seg[bp.ncta + c] = bp.nseg;
-        bp.arena += arena_need;
-        bp.nstripe += (uint32_t)p;
-        bp.ncta += (uint32_t)nc;
-        bp.nmoves += (uint32_t)move_need;
-        bp.ncls += C;
-        bp.ncnt += (uint32_t)(C * p);
-        bp.sarr += sarr_need;
-        bp.keys += keys_need;
-        bp.elems += pd.n;
-        bp.nseg++;
+    uint32_t C;
+    if (mode == 1) {
+        uint64_t K = next_pow2((uint64_t)nsplit + 1);
+        C = (uint32_t)(eq_given ? 2 * K : K);
+    } else {
+        C = 1u << radix_bits;
     }
-    return j;
+    const uint64_t nb = (pd.n + s.b - 1) / s.b;
+    uint64_t p = (pd.n + stripe_elems - 1) / stripe_elems;
+    if (p < 1) p = 1;
+    if (p > nb) p = nb;
+    uint64_t nc = (nb + blocks_per_cta - 1) / blocks_per_cta;
+    if (nc < 1) nc = 1;
+    // arena: cleanup staging (C blocks) directly followed by the overflow
+    // block, then C leftover buffer blocks per stripe
+    const uint64_t stageb = align_up((uint64_t)C * s.b * D + (uint64_t)s.b * D, 256);
+    const uint64_t bufb = align_up((uint64_t)C * s.b * D, 256);
+    if (p > s.stripe_cap || nc > s.cta_cap || stageb + p * bufb > s.arena_bytes ||
+        2 * (p + C) + 4 > s.move_cap || (uint64_t)C * p > s.cnt_cap)
+        return IPSGPU_E_NOMEM;
+    SegDesc &sd = s.h_seg[0];
+    memset(&sd, 0, sizeof sd);
+    sd.addr = pd.addr;
+    sd.n = pd.n;
+    sd.b = s.b;
+    sd.C = C;
+    sd.stripe0 = 0;
+    sd.nstripes = (uint32_t)p;
+    sd.cta0 = 0;
+    sd.ncta = (uint32_t)nc;
+    sd.stage_off = 0;
+    sd.arr_off = 0;
+    sd.key_off = 0;
+    sd.cls0 = 0;
+    sd.cnt0 = 0;
+    sd.mode = mode;
+    sd.radix_shift = pd.shift;
+    sd.radix_bits = radix_bits;
+    sd.nsplit = nsplit;
+    sd.eq_given = eq_given ? 1 : 0;
+    uint64_t off = stageb;
+    for (uint64_t q = 0; q < p; q++) {
+        StripeDesc &sp = s.h_stripe[q];
+        sp.seg = 0;
+        const uint64_t b0 = q * nb / p, b1 = (q + 1) * nb / p;
+        sp.blk0 = (uint32_t)b0;
+        sp.nblk = (uint32_t)(b1 - b0);
+        sp.cnt_off = (uint32_t)(q * C);
+        sp.left_off = off;
+        off += bufb;
+    }
+    for (uint64_t c = 0; c < nc; c++) s.h_cta_seg[c] = 0;
+    bp.nseg = 1;
+    bp.nstripe = (uint32_t)p;
+    bp.ncta = (uint32_t)nc;
+    bp.ncls = C;
+    bp.elems = pd.n;
+    return IPSGPU_OK;
 }
 
 int upload_plan(Sorter &s, const BatchPlan &bp, cudaStream_t st) {
     cudaError_t e;
     e = cudaMemcpyAsync(s.d_seg, s.h_seg, sizeof(SegDesc) * bp.nseg, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && bp.nstripe)
         e = cudaMemcpyAsync(s.d_stripe, s.h_stripe, sizeof(StripeDesc) * bp.nstripe,
                             cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && bp.ncta)
         e = cudaMemcpyAsync(s.d_cta_seg, s.h_cta_seg, sizeof(uint32_t) * bp.ncta,
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(s.h2d_done, st);
@@ -276,141 +259,108 @@ int upload_plan(Sorter &s, const BatchPlan &bp, cudaStream_t st) {
 // the pinned mirrors may be rewritten only once earlier uploads have run
 int wait_uploads(Sorter &s) { return cuda_status(cudaEventSynchronize(s.h2d_done)); }
 
-void level_sizes(const Sorter &s, const std::vector<Pending> &list, uint64_t &stripe_elems,
-                 uint64_t &blocks_per_cta) {
-    uint64_t tot = 0, blocks = 0;
-    for (auto &p : list) {
-        tot += p.n;
-        blocks += (p.n + s.b - 1) / s.b;
-    }
-    stripe_elems = std::max<uint64_t>(kMinStripe, (tot + 2 * s.nsm - 1) / (2 * (uint64_t)s.nsm));
+// stripes of about n / (2 * #SM) elements (at least kMinStripe), and about
+// 8 block-permutation CTAs per SM (at least 32 blocks each); the device
+// planner uses the same rule over a level's total
+void level_sizes(const Sorter &s, uint64_t tot, uint64_t &stripe_elems, uint64_t &blocks_per_cta) {
+    const uint64_t blocks = (tot + s.b - 1) / s.b;
+    stripe_elems = std::max<uint64_t>(kMinStripe, tot / (2 * (uint64_t)s.nsm));
     stripe_elems = align_up(stripe_elems, s.b);
-    blocks_per_cta = std::max<uint64_t>(32, (blocks + 8 * s.nsm - 1) / (8 * (uint64_t)s.nsm));
+    blocks_per_cta = std::max<uint64_t>(32, blocks / (8 * (uint64_t)s.nsm));
 }
 
 int read_status(Sorter &s, cudaStream_t st, int *code) {
-    int h = 0;
     cudaError_t e = cudaMemcpyAsync(s.h_flags + 2, s.d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return IPSGPU_E_CUDA;
-    h = s.h_flags[2];
-    *code = h;
-    return IPSGPU_OK;
-}
-
-int flush_base(Sorter &s, std::vector<Pending> &base, cudaStream_t st) {
-    size_t i = 0;
-    while (i < base.size()) {
-        int rc = wait_uploads(s);
-        if (rc) return rc;
-        // the previous chunk's copy out of h_base must have run
-        if (i > 0 && cudaStreamSynchronize(st) != cudaSuccess) return IPSGPU_E_CUDA;
-        size_t m = std::min<size_t>(base.size() - i, s.base_cap);
-        uint64_t elems = 0;
-        for (size_t q = 0; q < m; q++) {
-            s.h_base[2 * q] = base[i + q].begin;
-            s.h_base[2 * q + 1] = base[i + q].n;
-            elems += base[i + q].n;
-        }
-        cudaError_t e = cudaMemcpyAsync(s.d_base, s.h_base, sizeof(uint64_t) * 2 * m,
-                                        cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaEventRecord(s.h2d_done, st);
-        if (e != cudaSuccess) return IPSGPU_E_CUDA;
-        s.level_elems = elems;
-        e = s.ops->base(&s, s.data, s.d_base, (uint32_t)m, nullptr, (uint32_t)m, st);
-        if (e != cudaSuccess) return IPSGPU_E_CUDA;
-        i += m;
-    }
-    base.clear();
+    *code = s.h_flags[2];
     return IPSGPU_OK;
 }
 
 int check_data(const Sorter &s, const void *d) {
     if (!d) return IPSGPU_E_INVAL;
-    const int D = s.ops->D;
-    const uintptr_t al = D == 100 ? 4 : (uintptr_t)std::min(D, 16);
-    return ((uintptr_t)d % al) ? IPSGPU_E_INVAL : IPSGPU_OK;
+    return ((uintptr_t)d % elem_align(s.ops->D)) ? IPSGPU_E_INVAL : IPSGPU_OK;
 }
 
+// Level count of a device-planned batch whose largest array has max_n
+// elements: radix consumes kbits key bits per level; samplesort shrinks a
+// segment of m elements by its class budget per level (expected), plus slack
+// levels for children that an unlucky sample left above the base-case size.
+int graph_levels(const Sorter &s, uint64_t max_n) {
+    const uint32_t kbits = (uint32_t)__builtin_ctz(s.k);
+    if (max_n <= s.smax) return 0;
+    if (s.algo == IPSGPU_RADIX) {
+        const uint32_t keybits = s.ops->D == 4 ? 32 : 64;
+        return (int)((keybits + kbits - 1) / kbits);
+    }
+    int L = 0;
+    for (uint64_t m = max_n; m > s.smax; L++) {
+        const uint32_t C = class_budget(s, m);
+        m = (m + C - 1) / C;
+    }
+    return L + 2;
+}
+
+// One device-planned run (graph.cuh) over the input given by exactly one of
+// offsets (into data), segs ((address, n) pairs) or neither (data[0..n)).
+int graph_run(Sorter &s, unsigned char *data, uint64_t n_total, const uint64_t *d_offsets,
+              const uint64_t *d_segs, uint64_t nseg, uint64_t max_n, const int *skip_flags,
+              cudaStream_t st) {
+    s.data = data;
+    s.level_elems = n_total;
+    GraphArgs ga;
+    memset(&ga, 0, sizeof ga);
+    ga.lv = s.args(0, 0, 0, 0, nullptr);
+    ga.counts = reinterpret_cast<LevelCounts *>(s.d_gcount);
+    ga.list_count[0] = s.d_gcount + 4;
+    ga.list_count[1] = s.d_gcount + 5;
+    ga.base_count = s.d_gcount + 6;
+    ga.invalid = s.d_gcount + 7;
+    ga.list[0] = reinterpret_cast<GList *>(s.d_glist);
+    ga.list[1] = ga.list[0] + s.seg_cap;
+    ga.base_list = s.d_base;
+    ga.offsets = d_offsets;
+    ga.segs = d_segs;
+    ga.skip_flags = skip_flags;
+    ga.nseg_in = nseg;
+    ga.n_total = n_total;
+    ga.elem_bytes = (uint32_t)s.ops->D;
+    ga.elem_align = (uint32_t)elem_align(s.ops->D);
+    ga.list_cap = s.seg_cap;
+    ga.base_cap = s.base_cap;
+    ga.seg_cap = s.seg_cap;
+    ga.stripe_cap = s.stripe_cap;
+    ga.cta_cap = s.cta_cap;
+    ga.cls_cap = s.cls_cap;
+    ga.cnt_cap = s.cnt_cap;
+    ga.smax = s.smax;
+    ga.k = s.k;
+    ga.b = s.b;
+    ga.nsm = (uint32_t)s.nsm;
+    ga.kbits = (uint32_t)__builtin_ctz(s.k);
+    ga.keybits = s.ops->D == 4 ? 32 : 64;
+    ga.arena_bytes = s.arena_bytes;
+    ga.sarr_bytes = s.sarr_bytes;
+    ga.keys_bytes = s.keys_bytes;
+    ga.algo = s.algo == IPSGPU_RADIX ? 1 : 0;
+    ga.levels = graph_levels(s, max_n);
+    return cuda_status(s.ops->segmented(&s, ga, st));
+}
+
+// The whole sort on the device (no host synchronization): Sec. 5's check for
+// non-decreasing and non-increasing inputs (one pass, flags in device
+// memory; a non-increasing input is reversed), then the recursion, skipped
+// when a flag is set.
 int sort_impl(Sorter &s, unsigned char *data, uint64_t n, cudaStream_t st) {
     if (n < 2) return IPSGPU_OK;
     if (n > (1ull << 40)) return IPSGPU_E_INVAL;
     s.data = data;
-    int rc = wait_uploads(s);
-    if (rc) return rc;
-    // Sec. 5: sorted inputs return, decreasing ones are reversed
-    s.h_flags[0] = 1;
-    s.h_flags[1] = 1;
-    cudaError_t e = cudaMemcpyAsync(s.d_flags, s.h_flags, 2 * sizeof(int), cudaMemcpyHostToDevice, st);
+    // both flags start non-zero ("still possible")
+    cudaError_t e = cudaMemsetAsync(s.d_flags, 1, 2 * sizeof(int), st);
     if (e == cudaSuccess) e = s.ops->detect(&s, data, n, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s.h_flags, s.d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = s.ops->reverse(&s, data, n, st);
     if (e != cudaSuccess) return IPSGPU_E_CUDA;
-    if (s.h_flags[0]) return IPSGPU_OK;
-    if (s.h_flags[1]) return cuda_status(s.ops->reverse(&s, data, n, st));
-
-    const bool radix = s.algo == IPSGPU_RADIX;
-    const uint32_t kbits = (uint32_t)__builtin_ctz(s.k);
-    const uint32_t keybits = s.ops->D == 4 ? 32 : 64;
-    std::vector<Pending> cur, next, base;
-    if (n <= s.smax)
-        base.push_back({0, n, 0});
-    else
-        cur.push_back({0, n, keybits > kbits ? keybits - kbits : 0});
-    int levels = 0;
-    while (!cur.empty()) {
-        // every level strictly shrinks its segments; a deep recursion means
-        // an inconsistent partition, not a hard input
-        if (++levels > 96) return IPSGPU_E_INTERNAL;
-        uint64_t stripe_elems, bpc;
-        level_sizes(s, cur, stripe_elems, bpc);
-        size_t i = 0;
-        while (i < cur.size()) {
-            if ((rc = wait_uploads(s))) return rc;
-            BatchPlan bp;
-            // radix: the digit of a segment is key bits [shift, shift + kbits)
-            size_t j = plan_batch(s, cur, i, radix ? 2 : 0, 0, 0, kbits, stripe_elems, bpc, bp);
-            if (j == (size_t)-1 || j == i) return IPSGPU_E_INTERNAL;
-            if ((rc = upload_plan(s, bp, st))) return rc;
-            s.level_elems = bp.elems;
-            const LevelArgs a = s.args(bp.nseg, bp.nstripe, bp.ncta, bp.ncls, nullptr);
-            const LevelGrids g{bp.nseg, bp.nstripe, bp.ncta, bp.ncls};
-            if ((e = s.ops->level(&s, a, g, st)) != cudaSuccess) return IPSGPU_E_CUDA;
-            if ((e = s.ops->pack(&s, a, bp.nseg, st)) != cudaSuccess) return IPSGPU_E_CUDA;
-            e = cudaMemcpyAsync(s.h_res, s.d_res, sizeof(uint64_t) * kResStride * bp.nseg,
-                                cudaMemcpyDeviceToHost, st);
-            if (e != cudaSuccess) return IPSGPU_E_CUDA;
-            int code = 0;
-            if ((rc = read_status(s, st, &code))) return rc;
-            if (code) return code;
-            for (uint32_t q = 0; q < bp.nseg; q++) {
-                const uint64_t *r = s.h_res + (size_t)q * kResStride;
-                const uint32_t B = (uint32_t)r[0];
-                const bool eq = r[1] != 0;
-                const Pending &par = cur[i + q];
-                for (uint32_t c = 0; c < B; c++) {
-                    if (eq && (c & 1) && c + 1 < B) continue;  // equality bucket: one key
-                    const uint64_t lo = r[2 + c], hi = r[3 + c];
-                    const uint64_t m = hi - lo;
-                    if (m <= 1) continue;
-                    Pending ch{par.begin + lo, m, 0};
-                    if (radix) {
-                        if (par.shift == 0) continue;  // every key bit used: equal keys
-                        ch.shift = par.shift >= kbits ? par.shift - kbits : 0;
-                    }
-                    if (m <= s.smax)
-                        base.push_back(ch);
-                    else
-                        next.push_back(ch);
-                }
-            }
-            i = j;
-        }
-        cur.swap(next);
-        next.clear();
-    }
-    return flush_base(s, base, st);
+    return graph_run(s, data, n, nullptr, nullptr, 1, n, s.d_flags, st);
 }
 
 int single_level(Sorter &s, unsigned char *data, uint64_t n, uint32_t mode, uint32_t nsplit,
@@ -419,12 +369,12 @@ int single_level(Sorter &s, unsigned char *data, uint64_t n, uint32_t mode, uint
     s.data = data;
     int rc = wait_uploads(s);
     if (rc) return rc;
-    std::vector<Pending> one{{0, n, shift}};
     uint64_t stripe_elems, bpc;
-    level_sizes(s, one, stripe_elems, bpc);
+    level_sizes(s, n, stripe_elems, bpc);
     BatchPlan bp;
-    size_t j = plan_batch(s, one, 0, mode, nsplit, eq, bits, stripe_elems, bpc, bp);
-    if (j != 1) return IPSGPU_E_INVAL;
+    rc = plan_single(s, Pending{(uint64_t)(uintptr_t)data, n, shift}, mode, nsplit, eq, bits,
+                     stripe_elems, bpc, bp);
+    if (rc) return rc;
     if ((rc = upload_plan(s, bp, st))) return rc;
     s.level_elems = n;
     const LevelArgs a = s.args(bp.nseg, bp.nstripe, bp.ncta, bp.ncls, given);
@@ -554,7 +504,6 @@ int ipsgpu_sorter_create(const ipsgpu_params *params, int dtype, ipsgpu_sorter *
     dm((void **)&s.d_nmoves, 64);
     dm((void **)&s.d_status, 64);
     dm((void **)&s.d_cta_seg, L.cta);
-    dm((void **)&s.d_res, L.res);
     dm((void **)&s.d_base, L.base);
     dm((void **)&s.d_flags, 64);
     dm((void **)&s.d_waitflag, 64);
@@ -563,8 +512,6 @@ int ipsgpu_sorter_create(const ipsgpu_params *params, int dtype, ipsgpu_sorter *
     hm((void **)&s.h_seg, L.seg);
     hm((void **)&s.h_stripe, L.stripe);
     hm((void **)&s.h_cta_seg, L.cta);
-    hm((void **)&s.h_res, L.res);
-    hm((void **)&s.h_base, L.base);
     hm((void **)&s.h_flags, 64);
     if (ok && cudaEventCreateWithFlags(&s.h2d_done, cudaEventDisableTiming) != cudaSuccess) ok = false;
     if (ok && (cudaMemset(s.d_status, 0, 64) != cudaSuccess ||
@@ -648,63 +595,6 @@ int ipsgpu_radix_level(ipsgpu_sorter *h, void *d_data, uint64_t n, uint32_t shif
                                        cudaMemcpyDeviceToDevice, st));
 }
 
-// Level count of a device-planned batch over at most n elements: radix
-// consumes kbits key bits per level; samplesort shrinks a segment of m
-// elements by its class budget per level (expected), plus slack levels for
-// children that an unlucky sample left above the base-case size.
-static int graph_levels(const Sorter &s, uint64_t n) {
-    const uint32_t kbits = (uint32_t)__builtin_ctz(s.k);
-    if (s.algo == IPSGPU_RADIX) {
-        const uint32_t keybits = s.ops->D == 4 ? 32 : 64;
-        return (int)((keybits + kbits - 1) / kbits);
-    }
-    int L = 0;
-    for (uint64_t m = n; m > s.smax; L++) {
-        const uint32_t C = class_budget(s, m);
-        m = (m + C - 1) / C;
-    }
-    return L + 3;
-}
-
-static int segmented_impl(Sorter &s, unsigned char *data, uint64_t n, const uint64_t *d_offsets,
-                          uint64_t nseg, cudaStream_t st) {
-    s.data = data;
-    s.level_elems = n;
-    GraphArgs ga;
-    memset(&ga, 0, sizeof ga);
-    ga.lv = s.args(0, 0, 0, 0, nullptr);
-    ga.counts = reinterpret_cast<LevelCounts *>(s.d_gcount);
-    ga.list_count[0] = s.d_gcount + 4;
-    ga.list_count[1] = s.d_gcount + 5;
-    ga.base_count = s.d_gcount + 6;
-    ga.invalid = s.d_gcount + 7;
-    ga.list[0] = reinterpret_cast<GList *>(s.d_glist);
-    ga.list[1] = ga.list[0] + s.seg_cap;
-    ga.base_list = s.d_base;
-    ga.offsets = d_offsets;
-    ga.nseg_in = nseg;
-    ga.n_total = n;
-    ga.list_cap = s.seg_cap;
-    ga.base_cap = s.base_cap;
-    ga.seg_cap = s.seg_cap;
-    ga.stripe_cap = s.stripe_cap;
-    ga.cta_cap = s.cta_cap;
-    ga.cls_cap = s.cls_cap;
-    ga.cnt_cap = s.cnt_cap;
-    ga.smax = s.smax;
-    ga.k = s.k;
-    ga.b = s.b;
-    ga.nsm = (uint32_t)s.nsm;
-    ga.kbits = (uint32_t)__builtin_ctz(s.k);
-    ga.keybits = s.ops->D == 4 ? 32 : 64;
-    ga.arena_bytes = s.arena_bytes;
-    ga.sarr_bytes = s.sarr_bytes;
-    ga.keys_bytes = s.keys_bytes;
-    ga.algo = s.algo == IPSGPU_RADIX ? 1 : 0;
-    ga.levels = graph_levels(s, n);
-    return cuda_status(s.ops->segmented(&s, ga, st));
-}
-
 static int check_segmented(ipsgpu_sorter *h, void *d_data, uint64_t n, const uint64_t *d_offsets,
                            uint64_t nseg) {
     if (!h) return IPSGPU_E_INVAL;
@@ -719,8 +609,17 @@ int ipsgpu_sort_segmented(ipsgpu_sorter *h, void *d_data, uint64_t n, const uint
     int rc = check_segmented(h, d_data, n, d_offsets, num_segments);
     if (rc) return rc;
     if (n < 2 || num_segments == 0) return IPSGPU_OK;
-    return segmented_impl(h->s, (unsigned char *)d_data, n, d_offsets, num_segments,
-                          (cudaStream_t)stream);
+    return graph_run(h->s, (unsigned char *)d_data, n, d_offsets, nullptr, num_segments, n, nullptr,
+                     (cudaStream_t)stream);
+}
+
+int ipsgpu_sort_batch(ipsgpu_sorter *h, const uint64_t *d_segs, uint64_t num_segments,
+                      uint64_t max_n, void *stream) {
+    if (!h || max_n > (1ull << 40) || num_segments > 0xFFFFFFFFull) return IPSGPU_E_INVAL;
+    if (num_segments == 0 || max_n < 2) return IPSGPU_OK;
+    if (!d_segs || ((uintptr_t)d_segs % 8)) return IPSGPU_E_INVAL;
+    return graph_run(h->s, nullptr, 0, nullptr, d_segs, num_segments, max_n, nullptr,
+                     (cudaStream_t)stream);
 }
 
 struct ipsgpu_graph {
@@ -750,7 +649,8 @@ int ipsgpu_segmented_graph_create(ipsgpu_sorter *h, void *d_data, uint64_t n,
         rc = IPSGPU_E_CUDA;
     } else {
         if (n >= 2 && num_segments > 0)
-            rc = segmented_impl(s, (unsigned char *)d_data, n, d_offsets, num_segments, cs);
+            rc = graph_run(s, (unsigned char *)d_data, n, d_offsets, nullptr, num_segments, n,
+                           nullptr, cs);
         else
             rc = cuda_status(cudaMemsetAsync(s.d_gcount, 0, sizeof(uint32_t), cs));  // an empty graph node
         cudaError_t e = cudaStreamEndCapture(cs, &g->graph);
@@ -806,6 +706,7 @@ int ipsgpu_classify(ipsgpu_sorter *h, const void *d_data, uint64_t n, const void
     s.data = (unsigned char *)d_data;
     SegDesc &sd = s.h_seg[0];
     memset(&sd, 0, sizeof sd);
+    sd.addr = (uint64_t)(uintptr_t)d_data;
     sd.n = n;
     sd.b = s.b;
     sd.C = (uint32_t)B;
@@ -855,8 +756,8 @@ int ipsgpu_set_timing(ipsgpu_sorter *h, int enable) {
 
 static const char *kKindNames[KK_COUNT] = {"detect", "reverse", "sample_tree", "classify",
                                            "prep",   "fixup",   "permute",     "stage",
-                                           "fill",   "pack",    "base_case",   "classify_ids",
-                                           "debug_wait", "plan"};
+                                           "fill",   "base_case", "classify_ids", "debug_wait",
+                                           "plan"};
 
 const char *ipsgpu_kernel_name(int kind) {
     return (kind >= 0 && kind < KK_COUNT) ? kKindNames[kind] : "";

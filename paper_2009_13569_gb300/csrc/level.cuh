@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tree(LevelArgs a) {
         }
         K *gtree = reinterpret_cast<K *>(a.keys + sd.key_off);
         K *gspl = gtree + sd.C;
-        const E *base = reinterpret_cast<const E *>(a.data) + sd.begin;
+        const E *base = reinterpret_cast<const E *>(sd.addr);
 
         if (sd.mode == 1) {
             const E *g = reinterpret_cast<const E *>(a.given_spl);
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tree(LevelArgs a) {
             if (m > kMaxSortSample) m = kMaxSortSample;
             uint32_t P = 1;
             while (P < m) P <<= 1;
-            const uint64_t sseed = a.seed ^ (sd.begin * 0xD1B54A32D192ED03ull) ^ (sd.n << 17);
+            const uint64_t sseed = a.seed ^ (sd.addr * 0xD1B54A32D192ED03ull) ^ (sd.n << 17);
             for (uint32_t t = tid; t < P; t += blockDim.x) {
                 if (t < m) {
                     uint64_t idx = splitmix64(sseed + t * 0x9E3779B97F4A7C15ull) % sd.n;
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(kAuxThreads) k_fixup(LevelArgs a) {
         const Move mv = a.moves[m];
         const SegDesc &sd = a.seg[mv.seg];
         const uint32_t BB = sd.b * T::D;
-        unsigned char *base = a.data + sd.begin * (uint64_t)T::D;
+        unsigned char *base = reinterpret_cast<unsigned char *>(sd.addr);
         const int u = access_unit((uint64_t)(uintptr_t)base);
         uint4 r;
         warp_load_block(r, base + (uint64_t)(mv.src + k) * BB, BB, lane, u);
@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a) {
         const uint32_t B = st->B;
         const uint32_t nfs = st->nfull_slots;
         const uint32_t BB = sd.b * T::D;
-        unsigned char *base = a.data + sd.begin * (uint64_t)T::D;
+        unsigned char *base = reinterpret_cast<unsigned char *>(sd.addr);
         const int u = access_unit((uint64_t)(uintptr_t)base);
         const uint32_t W = sd.ncta * (kPermuteThreads / 32);
         const uint32_t wid = (v - sd.cta0) * (kPermuteThreads / 32) + warp;
@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(kAuxThreads) k_stage(LevelArgs a) {
         const SegState &st = a.st[s];
         const SegArrays ar = seg_arrays(a.sarr, sd);
         const uint32_t B = st.B, b = sd.b;
-        const E *base = reinterpret_cast<const E *>(a.data) + sd.begin;
+        const E *base = reinterpret_cast<const E *>(sd.addr);
         E *stage = reinterpret_cast<E *>(a.arena + sd.stage_off);
         const uint64_t cap = (uint64_t)st.nfull_slots * b;
         for (uint32_t j = warp; j < B; j += blockDim.x / 32) {
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(kAuxThreads) k_fill(LevelArgs a) {
         const uint32_t B = st.B, b = sd.b;
         if (j >= B) continue;
         const SegArrays ar = seg_arrays(a.sarr, sd);
-        E *base = reinterpret_cast<E *>(a.data) + sd.begin;
+        E *base = reinterpret_cast<E *>(sd.addr);
         const uint64_t lo = ar.bb[j], hi = ar.bb[j + 1];
         const uint64_t ds = (uint64_t)ar.dlm[j] * b;
         const uint64_t ws = (uint64_t)(ar.dlm[j] + ar.full[j]) * b;
@@ -714,22 +714,6 @@ __global__ void __launch_bounds__(kAuxThreads) k_fill(LevelArgs a) {
     }
 }
 
-// Copy (B, eq, bucket_begin[0..B]) of every segment into a dense array
-// res[s][kMaxClasses + 3] for one device-to-host transfer.
-static __global__ void __launch_bounds__(kAuxThreads) k_pack_results(LevelArgs a, uint64_t *res) {
-    const uint32_t nseg = lv_nseg(a);
-    for (uint32_t s = blockIdx.x; s < nseg; s += gridDim.x) {
-        const SegState &st = a.st[s];
-        const SegArrays ar = seg_arrays(a.sarr, a.seg[s]);
-        uint64_t *r = res + (size_t)s * (kMaxClasses + 3);
-        if (threadIdx.x == 0) {
-            r[0] = st.B;
-            r[1] = st.eq;
-        }
-        for (uint32_t j = threadIdx.x; j <= st.B; j += blockDim.x) r[2 + j] = ar.bb[j];
-    }
-}
-
 // Element-wise classification (the classifier alone, for ipsgpu_classify).
 template <class T>
 __global__ void __launch_bounds__(kAuxThreads) k_classify_ids(LevelArgs a, uint32_t *out) {
@@ -741,7 +725,7 @@ __global__ void __launch_bounds__(kAuxThreads) k_classify_ids(LevelArgs a, uint3
     LevelClassifier<T> cl;
     load_classifier<T>(cl, a, sd, a.st[0], s_tree, s_spl);
     __syncthreads();
-    const E *base = reinterpret_cast<const E *>(a.data) + sd.begin;
+    const E *base = reinterpret_cast<const E *>(sd.addr);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < sd.n;
          i += (uint64_t)gridDim.x * blockDim.x)
         out[i] = cl(base[i]);

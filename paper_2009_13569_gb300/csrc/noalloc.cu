@@ -70,7 +70,8 @@ DeviceSetup g_setup;
 
 // Descriptors of the single segment, its stripes and its permutation CTAs,
 // written on the device from scalar arguments (no host upload).
-__global__ void k_na_plan(unsigned char *scr, uint64_t n, uint32_t b, uint32_t C, uint32_t p,
+__global__ void k_na_plan(unsigned char *scr, uint64_t addr, uint64_t n, uint32_t b, uint32_t C,
+                          uint32_t p,
                           uint32_t nc, uint32_t nsplit, uint32_t eq, uint32_t slot_bytes) {
     SegDesc *sd = reinterpret_cast<SegDesc *>(scr + kOSeg);
     StripeDesc *sp = reinterpret_cast<StripeDesc *>(scr + kOStripe);
@@ -80,7 +81,7 @@ __global__ void k_na_plan(unsigned char *scr, uint64_t n, uint32_t b, uint32_t C
     if (t == 0) {
         SegDesc d;
         memset(&d, 0, sizeof d);
-        d.begin = 0;
+        d.addr = addr;
         d.n = n;
         d.b = b;
         d.C = C;
@@ -213,8 +214,8 @@ extern "C" int ipsgpu_partition_level_noalloc(int dtype, void *d_data, uint64_t 
     const uint32_t threads = 256;
     const uint32_t work = (uint32_t)(p > nc ? p : nc);
     k_na_plan<<<(work + threads - 1) / threads, threads, 0, st>>>(
-        scr, n, b, (uint32_t)B, (uint32_t)p, (uint32_t)nc, num_splitters, equal_buckets ? 1u : 0u,
-        (uint32_t)kNaSlot);
+        scr, (uint64_t)(uintptr_t)d_data, n, b, (uint32_t)B, (uint32_t)p, (uint32_t)nc,
+        num_splitters, equal_buckets ? 1u : 0u, (uint32_t)kNaSlot);
     if (cudaGetLastError() != cudaSuccess) return IPSGPU_E_CUDA;
     const LevelArgs a = s.args(1, (uint32_t)p, (uint32_t)nc, (uint32_t)B,
                                static_cast<const unsigned char *>(d_splitters));

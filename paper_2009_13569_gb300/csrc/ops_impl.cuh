@@ -62,18 +62,11 @@ struct OpsImpl {
         return cudaGetLastError();
     }
 
-    static cudaError_t pack(Sorter *s, const LevelArgs &a, uint32_t nseg, cudaStream_t st) {
-        s->tbegin(KK_PACK, 0, st);
-        k_pack_results<<<nseg, kAuxThreads, 0, st>>>(a, s->d_res);
-        s->tend(st);
-        return cudaGetLastError();
-    }
-
-    static cudaError_t base(Sorter *s, unsigned char *data, const uint64_t *d_segs, uint32_t nsegs,
+    static cudaError_t base(Sorter *s, const uint64_t *d_segs, uint32_t nsegs,
                             const uint32_t *nsegs_dev, uint32_t grid, cudaStream_t st) {
         if (grid == 0) return cudaSuccess;
         s->tbegin(KK_BASE, 2.0 * (double)s->level_elems * T::D, st);
-        k_base<T><<<grid, kBaseThreads, base_smem_bytes(), st>>>(data, d_segs, nsegs, nsegs_dev,
+        k_base<T><<<grid, kBaseThreads, base_smem_bytes(), st>>>(d_segs, nsegs, nsegs_dev,
                                                                  s->d_status);
         s->tend(st);
         return cudaGetLastError();
@@ -95,7 +88,7 @@ struct OpsImpl {
         uint32_t grid = (uint32_t)(g < (uint64_t)s->nsm * 16 ? g : (uint64_t)s->nsm * 16);
         if (grid == 0) return cudaSuccess;
         s->tbegin(KK_REVERSE, 2.0 * n * T::D, st);
-        k_reverse<T><<<grid, 256, 0, st>>>(data, n);
+        k_reverse<T><<<grid, 256, 0, st>>>(data, n, s->d_flags);
         s->tend(st);
         return cudaGetLastError();
     }
@@ -130,7 +123,7 @@ struct OpsImpl {
             s->tbegin(KK_PLAN, 0, st);
             k_g_init<<<big, kAuxThreads, 0, st>>>(ga, i0, i1);
             s->tend(st);
-            if ((e = base(s, ga.lv.data, ga.base_list, 0, ga.base_count, s->nsm, st)) != cudaSuccess)
+            if ((e = base(s, ga.base_list, 0, ga.base_count, s->nsm, st)) != cudaSuccess)
                 return e;
         }
         for (int L = 0; L < ga.levels; L++) {
@@ -150,7 +143,7 @@ struct OpsImpl {
             k_g_emit<T><<<big, kAuxThreads, 0, st>>>(ga, L);
             s->tend(st);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            if ((e = base(s, ga.lv.data, ga.base_list, 0, ga.base_count, s->nsm, st)) != cudaSuccess)
+            if ((e = base(s, ga.base_list, 0, ga.base_count, s->nsm, st)) != cudaSuccess)
                 return e;
         }
         k_g_finish<<<1, 32, 0, st>>>(ga);
@@ -163,7 +156,6 @@ struct OpsImpl {
         o.key_bytes = sizeof(K);
         o.init = &init;
         o.level = &level;
-        o.pack = &pack;
         o.base = &base;
         o.detect = &detect;
         o.reverse = &reverse;

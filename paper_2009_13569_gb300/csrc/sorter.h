@@ -21,7 +21,6 @@ enum KernelKind {
     KK_PERMUTE,
     KK_STAGE,
     KK_FILL,
-    KK_PACK,
     KK_BASE,
     KK_CLASSIFY_IDS,
     KK_WAIT,
@@ -44,8 +43,7 @@ struct TypeOps {
     int key_bytes; // sizeof(K)
     cudaError_t (*init)(Sorter *);  // one-time kernel attributes
     cudaError_t (*level)(Sorter *, const LevelArgs &, const LevelGrids &, cudaStream_t);
-    cudaError_t (*pack)(Sorter *, const LevelArgs &, uint32_t nseg, cudaStream_t);
-    cudaError_t (*base)(Sorter *, unsigned char *data, const uint64_t *d_segs, uint32_t nsegs,
+    cudaError_t (*base)(Sorter *, const uint64_t *d_segs, uint32_t nsegs,
                         const uint32_t *nsegs_dev, uint32_t grid, cudaStream_t);
     cudaError_t (*detect)(Sorter *, const unsigned char *data, uint64_t n, cudaStream_t);
     cudaError_t (*reverse)(Sorter *, unsigned char *data, uint64_t n, cudaStream_t);
@@ -78,7 +76,6 @@ struct Sorter {
     uint32_t smax = 24576;  // largest segment of the base case
     // capacities of one level (device-planned) or one host-planned batch
     uint32_t seg_cap = 1u << 16;     // segments
-    uint32_t host_seg_cap = 4096;    // segments of a host-planned batch (result rows)
     uint32_t stripe_cap = 1u << 16;  // classification stripes
     uint32_t cta_cap = 1u << 17;     // block-permutation CTAs
     uint32_t cls_cap = 1u << 20;     // (segment, class) pairs
@@ -97,7 +94,6 @@ struct Sorter {
     uint32_t *d_nmoves = nullptr;
     int *d_status = nullptr;
     uint32_t *d_cta_seg = nullptr;
-    uint64_t *d_res = nullptr;
     uint64_t *d_base = nullptr;
     int *d_flags = nullptr;
     uint32_t *d_waitflag = nullptr;
@@ -107,8 +103,6 @@ struct Sorter {
     SegDesc *h_seg = nullptr;
     StripeDesc *h_stripe = nullptr;
     uint32_t *h_cta_seg = nullptr;
-    uint64_t *h_res = nullptr;
-    uint64_t *h_base = nullptr;
     int *h_flags = nullptr;
     uint64_t scratch_bytes = 0;
     cudaEvent_t h2d_done = nullptr;  // last upload out of the pinned mirrors

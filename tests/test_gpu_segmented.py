@@ -107,7 +107,6 @@ def test_segmented_many_tiny():
 def test_segmented_partial_cover_leaves_rest():
     # segments cover [100, 60100) and [70000, 190000) only; the gaps stay as they were
     host = inputs.generate("uniform", "u64", 200_000, seed=4)
-    offsets = np.array([100, 60_100, 60_100, 70_000], dtype=np.int64)
     d = to_dev(host)
     off = _offsets_dev([100, 60_100, 70_000, 190_000])
     with ipsgpu.Sorter("u64") as s:
@@ -118,7 +117,6 @@ def test_segmented_partial_cover_leaves_rest():
     np.testing.assert_array_equal(got[:100], inp[:100])
     np.testing.assert_array_equal(got[190_000:], inp[190_000:])
     _check_segments(got, inp, [100, 60_100, 70_000, 190_000], "u64")
-    del offsets
 
 
 def test_segmented_invalid_offsets_reported():
@@ -179,3 +177,33 @@ def test_segmented_matches_per_array_sort():
             s.sort(d[lo:hi].data_ptr(), hi - lo, stream())
         assert s.status(stream()) == ipsgpu.OK
     np.testing.assert_array_equal(batch, inputs.to_numpy(d.cpu(), "u64"))
+
+
+def test_sort_batch_separate_arrays():
+    # separate device tensors of one type, sorted by one batch call
+    lengths = [70_000, 5, 0, 1, 23_552, 140_001, 999]
+    hosts = [inputs.generate(("uniform", "twodup", "zipf")[i % 3], "u64", m, seed=40 + i)
+             for i, m in enumerate(lengths)]
+    devs = [to_dev(h) if h.numel() else torch.empty(0, dtype=torch.int64, device=DEV)
+            for h in hosts]
+    segs = torch.tensor([[t.data_ptr(), t.numel()] for t in devs], dtype=torch.int64).to(DEV)
+    with ipsgpu.Sorter("u64") as s:
+        s.sort_batch(segs.data_ptr(), len(devs), max(lengths), stream())
+        assert s.status(stream()) == ipsgpu.OK
+    for h, t in zip(hosts, devs):
+        got = inputs.to_numpy(t.cpu(), "u64")
+        if h.numel() > 1:
+            assert_sorted_parity(got, inputs.to_numpy(h, "u64"), "u64")
+
+
+def test_sort_batch_pairs_and_bad_entry():
+    hosts = [inputs.generate("rootdup", "pair", m, seed=50 + m) for m in (30_000, 90_000, 300)]
+    devs = [to_dev(h) for h in hosts]
+    rows_ = [[t.data_ptr(), t.shape[0]] for t in devs]
+    rows_.append([devs[0].data_ptr() + 8, 100])  # misaligned for 16-byte pairs: skipped
+    segs = torch.tensor(rows_, dtype=torch.int64).to(DEV)
+    with ipsgpu.Sorter("pair") as s:
+        s.sort_batch(segs.data_ptr(), len(rows_), 90_000, stream())
+        assert s.status(stream()) == ipsgpu.E_INVAL
+    for h, t in zip(hosts, devs):
+        assert_sorted_parity(inputs.to_numpy(t.cpu(), "pair"), inputs.to_numpy(h, "pair"), "pair")
