@@ -148,22 +148,20 @@ int ipsgpu_radix_level(ipsgpu_sorter *s, void *d_data, uint64_t n, uint32_t shif
 
 /* Sort many independent arrays in one call (segmented sort): segment i is
  * d_data[d_offsets[i] .. d_offsets[i+1]) for i < num_segments, sorted in
- * place exactly as ipsgpu_sort would sort it alone (Sec. 3.2 recursion run
- * breadth-first over all segments of the batch at once).
+ * place exactly as ipsgpu_sort would sort it alone.
  *   - d_offsets: num_segments + 1 u64 element offsets in device memory,
  *     non-decreasing, the last one <= n; n is the length of d_data.  A
  *     segment that violates this is left untouched and E_INVAL is recorded
  *     in the status word.  Elements outside every segment are not touched.
- *   - Every level is planned on the device, so the call never synchronizes:
- *     it enqueues a launch sequence that depends only on (n, num_segments)
- *     and the sorter's parameters, and it can be captured into a CUDA graph
- *     (or use ipsgpu_segmented_graph_create).  Unlike ipsgpu_sort it does not
- *     look for already sorted or reversed inputs.
- *   - Limits of one level: the sorter's segment, stripe, class and arena
- *     capacities (ipsgpu_params.arena_bytes).  A level that exceeds one
- *     records E_NOMEM in the status word and stops the recursion; the data
- *     then still holds a permutation of every segment.
- *   - Kernel-side errors go to the status word (ipsgpu_status).
+ *   - The recursion of Sec. 3.2 runs on the device over all segments at
+ *     once: segments that need a partitioning step wait in a FIFO ring and
+ *     are taken in waves sized to the sorter's fixed scratch, so scratch
+ *     does not grow with n or with the number of segments.  The waves run
+ *     inside one CUDA graph launch (a conditional WHILE node); the call
+ *     never synchronizes.  Unlike ipsgpu_sort it does not look for already
+ *     sorted or reversed inputs.
+ *   - Kernel-side errors go to the status word (ipsgpu_status); after an
+ *     error the data still holds a permutation of every segment.
  * Errors: E_INVAL (NULL or misaligned pointers, n > 2^40), E_CUDA. */
 int ipsgpu_sort_segmented(ipsgpu_sorter *s, void *d_data, uint64_t n,
                           const uint64_t *d_offsets, uint64_t num_segments, void *stream);
@@ -172,28 +170,26 @@ int ipsgpu_sort_segmented(ipsgpu_sorter *s, void *d_data, uint64_t n,
  * address d_segs[2i] (aligned as for ipsgpu_sort) and has d_segs[2i+1]
  * elements; d_segs holds 2 * num_segments u64 in device memory.  Each array
  * is sorted in place exactly as ipsgpu_sort_segmented would sort it; the
- * arrays must not overlap.  max_n must be at least the largest length (it
- * fixes the number of levels that are launched).  Asynchronous, never
- * synchronizes, capturable; an entry with a NULL or misaligned address (and
- * n > 0) or n > 2^40 is skipped and recorded as E_INVAL in the status word.
- * Errors: E_INVAL (max_n > 2^40, misaligned d_segs), E_CUDA. */
+ * arrays must not overlap.  Asynchronous, never synchronizes; an entry with
+ * a NULL or misaligned address (and n > 0) or n > 2^40 is skipped and
+ * recorded as E_INVAL in the status word.
+ * Errors: E_INVAL (misaligned d_segs), E_CUDA. */
 int ipsgpu_sort_batch(ipsgpu_sorter *s, const uint64_t *d_segs, uint64_t num_segments,
-                      uint64_t max_n, void *stream);
+                      void *stream);
 
-/* A segmented sort captured once into an instantiated CUDA graph: the same
- * launch sequence as ipsgpu_sort_segmented over fixed buffers (d_data,
- * d_offsets), replayed by ipsgpu_graph_launch with one host call per batch.
- * The graph reads the offsets and data at launch time, so the caller may
- * refill both buffers between launches.  The graph uses the sorter's
- * scratch: launches of graphs of one sorter, and its other calls, must not
- * overlap on the GPU.  Errors: as ipsgpu_sort_segmented, plus E_CUDA if the
- * capture or instantiation fails. */
+/* A segmented sort over fixed buffers (d_data, d_offsets) as one
+ * instantiated CUDA graph: a node that sets up the run, then the WHILE loop
+ * over waves.  ipsgpu_graph_launch replays it with one call; it reads the
+ * offsets and data at launch time, so the caller may refill both buffers
+ * between launches.  The graph uses the sorter's scratch: launches of graphs
+ * of one sorter, and its other calls, must not overlap on the GPU.  Errors:
+ * as ipsgpu_sort_segmented, plus E_CUDA if building the graph fails. */
 typedef struct ipsgpu_graph ipsgpu_graph;
 int ipsgpu_segmented_graph_create(ipsgpu_sorter *s, void *d_data, uint64_t n,
                                   const uint64_t *d_offsets, uint64_t num_segments,
                                   ipsgpu_graph **out);
 int ipsgpu_graph_launch(ipsgpu_graph *g, void *stream);
-/* Number of nodes (kernel launches and memsets) in the captured graph. */
+/* Number of top-level nodes of the graph (the setup node and the WHILE node). */
 int ipsgpu_graph_nodes(ipsgpu_graph *g, uint64_t *nodes);
 int ipsgpu_graph_destroy(ipsgpu_graph *g);
 

@@ -1,18 +1,26 @@
-// graph.cuh -- the segmented batch run entirely on the device: the recursion
-// of Sec. 3.2 planned level by level by kernels instead of the host, so the
-// whole batch is one fixed sequence of launches (capturable in a CUDA graph).
+// graph.cuh -- the recursion of Sec. 3.2 run entirely on the device.
 //
-//   k_g_init          splits the input arrays (offsets into one array, a list
-//                     of (address, length) pairs, or one whole array): one
-//                     element or fewer: done; at most the base-case size:
-//                     base list; else level 0
-//   k_g_plan          one CTA plans a level: class budget, stripes, CTAs and
-//                     arena offsets of every segment (prefix sums)
+// Segments that still need a partitioning step wait in a FIFO ring.  The
+// work proceeds in waves; one wave is
+//   k_g_feed          takes the next input arrays: one element or fewer:
+//                     done; at most the base-case size: base list; else ring
+//   k_g_plan          one CTA takes the longest prefix of the ring whose
+//                     class budgets, stripes, CTAs and arena bytes fit the
+//                     sorter's fixed capacities, and lays it out
 //   k_g_fill_stripes  stripe descriptors and the CTA -> segment map
-//   level kernels     as for a host-planned level, counts read from memory
+//   level kernels     one partitioning step of every taken segment (level.cuh,
+//                     classify.cuh; work counts read from memory)
 //   k_g_emit          children of every bucket: done (equality bucket, at
 //                     most one element, radix digits exhausted), base list,
-//                     or the next level's list
+//                     or the ring's tail
+//   k_base            the base case of the wave's base list
+//   k_g_advance       consumes the taken prefix and the fed inputs and
+//                     decides whether another wave follows
+// so scratch is bounded by the capacities, not by n, however many segments
+// a level has (the paper bounds it by the number of threads in the same
+// way).  The waves run inside a conditional WHILE node of one CUDA graph
+// (k_g_advance sets its condition), or, when per-kernel timing is on, from a
+// host loop that reads the same decision back.
 #pragma once
 
 #include "common.cuh"
@@ -23,31 +31,50 @@ constexpr int kPlanThreads = 1024;
 constexpr uint32_t kMinStripeElems = 1u << 15;
 
 struct GList {
-    uint64_t addr, n;          // device byte address of the first element, elements
-    uint32_t shift, pad;
+    uint64_t addr, n;  // device byte address of the first element, elements
+    uint32_t shift;    // radix: next digit is key bits [shift, shift + kbits)
+    uint32_t pad;
 };
 
+// What one run sorts; written by k_g_job before the run.
+struct GJob {
+    unsigned char *data;      // offsets mode and single-array mode
+    const uint64_t *offsets;  // nseg_in + 1 element offsets into data, or null
+    const uint64_t *segs;     // nseg_in (address, n) pairs, or null
+    const int *skip_flags;    // if non-null and flags[0] or flags[1]: skip the input
+    uint64_t nseg_in;         // input arrays (1 in single-array mode)
+    uint64_t n_total;         // elements of data (offsets and single-array mode)
+    uint32_t max_waves;
+    uint32_t pad;
+};
+
+// Progress of a run, in device memory.
+struct GState {
+    LevelCounts counts;  // work counts of the wave's partitioning step
+    uint64_t in_head;    // input arrays consumed
+    uint64_t head, tail; // ring counters (entry i lives at ring[i % ring_cap])
+    uint32_t feed;       // input arrays the current wave feeds
+    uint32_t take;       // ring entries the current wave partitions
+    uint32_t base_count; // base list entries of the current wave
+    uint32_t wave;
+    uint32_t invalid;    // an input array had bad offsets or a bad address
+    uint32_t more;       // decision of the last k_g_advance
+    uint64_t elems;      // elements partitioned by the current wave
+    uint64_t base_elems; // elements of the current wave's base list
+};
+
+// Fixed for a sorter: its scratch and capacities.
 struct GraphArgs {
-    LevelArgs lv;              // the level's arrays (counts come from `counts`)
-    LevelCounts *counts;       // device: counts of the level being run
-    GList *list[2];            // ping-pong lists of segments to partition
-    uint32_t *list_count[2];
-    uint64_t *base_list;       // (address, n) pairs for the base case
-    uint32_t *base_count;
-    uint32_t *invalid;         // set when an input segment had bad offsets
-    // input, one of: offsets (nseg_in + 1 element offsets into lv.data),
-    // segs (nseg_in (address, n) pairs), or neither (all of lv.data)
-    const uint64_t *offsets;
-    const uint64_t *segs;
-    const int *skip_flags;     // if set: skip the input when flags[0] or flags[1]
-    uint64_t nseg_in;
-    uint64_t n_total;          // elements of lv.data (offsets mode, single array)
-    uint32_t elem_bytes, elem_align;
-    uint32_t list_cap, base_cap, seg_cap, stripe_cap, cta_cap, cls_cap, cnt_cap;
-    uint32_t smax, k, b, nsm, kbits, keybits;
+    LevelArgs lv;       // arrays of a partitioning step (lv.cnt -> state->counts)
+    GJob *job;
+    GState *state;
+    GList *ring;
+    uint64_t *base_list;  // (address, n) pairs for the base case
+    uint32_t ring_cap, base_cap, feed_cap, seg_cap, stripe_cap, cta_cap, cls_cap, cnt_cap;
+    uint32_t smax, k, b, nsm, kbits, keybits, elem_bytes, elem_align;
     uint64_t arena_bytes, sarr_bytes, keys_bytes;
-    int algo;                  // 0 samplesort, 1 radix
-    int levels;
+    int algo;  // 0 samplesort, 1 radix
+    int pad;
 };
 
 __device__ inline uint32_t g_next_pow2(uint64_t x) {
@@ -68,25 +95,31 @@ __device__ inline uint32_t g_class_budget(const GraphArgs &g, uint64_t n) {
 
 __device__ inline uint64_t g_al256(uint64_t x) { return (x + 255) & ~(uint64_t)255; }
 
-// Appends to a bounded list.  An append past the capacity is undone, so once
-// the appending kernel has finished the count never exceeds the capacity and
-// every entry below it is written; the overflow is reported as E_NOMEM.
+// Appends to the bounded base list.  An append past the capacity is undone,
+// so once the appending kernel has finished the count never exceeds the
+// capacity and every entry below it is written; the overflow is reported as
+// E_NOMEM.
 __device__ inline void g_push_base(const GraphArgs &g, uint64_t addr, uint64_t n) {
-    const uint32_t q = atomicAdd(g.base_count, 1u);
+    GState *s = g.state;
+    const uint32_t q = atomicAdd(&s->base_count, 1u);
     if (q < g.base_cap) {
         g.base_list[2 * q] = addr;
         g.base_list[2 * q + 1] = n;
+        atomicAdd(reinterpret_cast<unsigned long long *>(&s->base_elems), (unsigned long long)n);
     } else {
-        atomicSub(g.base_count, 1u);
+        atomicSub(&s->base_count, 1u);
         set_status(g.lv.status, IPSGPU_E_NOMEM);
     }
 }
-__device__ inline void g_push_list(const GraphArgs &g, int which, const GList &e) {
-    const uint32_t q = atomicAdd(g.list_count[which], 1u);
-    if (q < g.list_cap) {
-        g.list[which][q] = e;
+
+// Appends to the ring; `floor` is the first entry still in use.
+__device__ inline void g_push_ring(const GraphArgs &g, uint64_t floor, const GList &e) {
+    unsigned long long *tail = reinterpret_cast<unsigned long long *>(&g.state->tail);
+    const uint64_t q = atomicAdd(tail, 1ull);
+    if (q - floor < g.ring_cap) {
+        g.ring[q % g.ring_cap] = e;
     } else {
-        atomicSub(g.list_count[which], 1u);
+        atomicAdd(tail, ~0ull);  // undo
         set_status(g.lv.status, IPSGPU_E_NOMEM);
     }
 }
@@ -102,47 +135,80 @@ __device__ inline uint64_t g_left_bytes(uint32_t C, uint32_t b) {
     return g_al256((uint64_t)C * b * T::D);
 }
 
-// Input segments [i0, i1).  Offsets must be non-decreasing and within the
-// data array, listed arrays aligned to the element type; a segment that is
-// not is skipped, and k_g_finish reports E_INVAL once the valid segments are
-// sorted.  Segments of at most the base-case size go to the base list, the
-// others to the first level.
-static __global__ void __launch_bounds__(256) k_g_init(GraphArgs g, uint64_t i0, uint64_t i1) {
-    if (g.skip_flags && (g.skip_flags[0] || g.skip_flags[1])) return;  // sorted (or reversed)
+// Input arrays fed by a wave that starts with the given state: what is left,
+// at most feed_cap (the base list must hold them next to the children of
+// the wave) and at most the free ring entries.
+__device__ inline uint32_t g_feed_count(const GraphArgs &g, const GJob &j, uint64_t in_head,
+                                        uint64_t used) {
+    uint64_t f = j.nseg_in > in_head ? j.nseg_in - in_head : 0;
+    if (f > g.feed_cap) f = g.feed_cap;
+    const uint64_t room = used < g.ring_cap ? g.ring_cap - used : 0;
+    if (f > room) f = room;
+    return (uint32_t)f;
+}
+
+// Starts a run: job and state (one thread).
+static __global__ void k_g_job(GraphArgs g, GJob j) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    *g.job = j;
+    GState s;
+    s.counts = LevelCounts{0, 0, 0, 0};
+    s.in_head = 0;
+    s.head = 0;
+    s.tail = 0;
+    s.feed = g_feed_count(g, j, 0, 0);
+    s.take = 0;
+    s.base_count = 0;
+    s.wave = 0;
+    s.invalid = 0;
+    s.more = 1;
+    s.elems = 0;
+    s.base_elems = 0;
+    *g.state = s;
+}
+
+// Input arrays [in_head, in_head + feed).  Offsets must be non-decreasing and
+// within the data array, listed arrays aligned to the element type; an array
+// that is not is skipped, and k_g_advance reports E_INVAL at the end.
+static __global__ void __launch_bounds__(256) k_g_feed(GraphArgs g) {
+    const GJob j = *g.job;
+    const uint64_t i0 = g.state->in_head, i1 = i0 + g.state->feed;
+    const uint64_t floor = g.state->head;
+    if (j.skip_flags && (j.skip_flags[0] || j.skip_flags[1])) return;  // sorted (or reversed)
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = i0 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < i1; i += stride) {
         uint64_t addr, n;
-        if (g.offsets) {
-            const uint64_t b0 = g.offsets[i], b1 = g.offsets[i + 1];
-            if (b1 < b0 || b1 > g.n_total) {
-                *g.invalid = 1;
+        if (j.offsets) {
+            const uint64_t b0 = j.offsets[i], b1 = j.offsets[i + 1];
+            if (b1 < b0 || b1 > j.n_total) {
+                g.state->invalid = 1;
                 continue;
             }
-            addr = (uint64_t)(uintptr_t)g.lv.data + b0 * g.elem_bytes;
+            addr = (uint64_t)(uintptr_t)j.data + b0 * g.elem_bytes;
             n = b1 - b0;
-        } else if (g.segs) {
-            addr = g.segs[2 * i];
-            n = g.segs[2 * i + 1];
+        } else if (j.segs) {
+            addr = j.segs[2 * i];
+            n = j.segs[2 * i + 1];
             if ((n > 0 && (addr == 0 || addr % g.elem_align)) || n > (1ull << 40)) {
-                *g.invalid = 1;
+                g.state->invalid = 1;
                 continue;
             }
         } else {
-            addr = (uint64_t)(uintptr_t)g.lv.data;
-            n = g.n_total;
+            addr = (uint64_t)(uintptr_t)j.data;
+            n = j.n_total;
         }
         if (n <= 1) continue;
         if (n <= g.smax)
             g_push_base(g, addr, n);
         else
-            g_push_list(g, 0, GList{addr, n, g.keybits > g.kbits ? g.keybits - g.kbits : 0u, 0u});
+            g_push_ring(g, floor, GList{addr, n, g.keybits > g.kbits ? g.keybits - g.kbits : 0u, 0u});
     }
 }
 
 // Per-segment plan quantities.
 struct GPlanItem {
     uint32_t C, p, nc;
-    uint64_t arena, sarr, keys, cnt;
+    uint64_t arena, sarr, keys, cnt, moves;
 };
 
 template <class T>
@@ -152,43 +218,55 @@ __device__ inline GPlanItem g_item(const GraphArgs &g, uint64_t n, uint64_t stri
     it.C = g.algo == 1 ? (1u << g.kbits) : g_class_budget(g, n);
     const uint64_t nb = (n + g.b - 1) / g.b;
     uint64_t p = (n + stripe_elems - 1) / stripe_elems;
-    if (p < 1) p = 1;
+    // one segment alone always fits the arena and the counters (the sorter
+    // checks at creation that one stripe of k classes does)
+    const uint64_t stage = g_stage_bytes<T>(it.C, g.b), left = g_left_bytes<T>(it.C, g.b);
+    const uint64_t pfit = g.arena_bytes > stage ? (g.arena_bytes - stage) / left : 1;
+    if (p > pfit) p = pfit;
+    if (p > g.cnt_cap / it.C) p = g.cnt_cap / it.C;
+    if (p > g.stripe_cap) p = g.stripe_cap;
     if (p > nb) p = nb;
+    if (p < 1) p = 1;
     uint64_t nc = (nb + bpc - 1) / bpc;
+    if (nc > g.cta_cap) nc = g.cta_cap;
     if (nc < 1) nc = 1;
     it.p = (uint32_t)p;
     it.nc = (uint32_t)nc;
-    it.arena = g_stage_bytes<T>(it.C, g.b) + p * g_left_bytes<T>(it.C, g.b);
+    it.arena = stage + p * left;
     it.sarr = seg_arrays_bytes(it.C);
     it.keys = ((uint64_t)2 * it.C * sizeof(typename T::K) + 15) & ~(uint64_t)15;
     it.cnt = (uint64_t)it.C * p;
+    it.moves = 2 * ((uint64_t)p + it.C) + 4;
     return it;
 }
 
+// Plans the wave: the longest prefix of the ring (at most seg_cap entries)
+// whose summed needs fit every capacity.  Stripe and CTA sizes follow the
+// host planner's rule over the elements waiting in the ring window.
 template <class T>
-__global__ void __launch_bounds__(kPlanThreads) k_g_plan(GraphArgs g, int L) {
-    constexpr int NV = 7;  // stripes, ctas, classes, arena, sarr, keys, counts
+__global__ void __launch_bounds__(kPlanThreads) k_g_plan(GraphArgs g) {
+    constexpr int NV = 8;  // stripes, ctas, classes, arena, sarr, keys, counts, moves
     __shared__ unsigned long long red[2][32];
     __shared__ unsigned long long wsum[NV][32];
-    __shared__ int sh_bad;
+    __shared__ uint32_t sh_cut;
+    __shared__ unsigned long long sh_elems;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const GList *in = g.list[L & 1];
-    uint32_t nin = *g.list_count[L & 1];
+    GState *S = g.state;
+    const uint64_t head = S->head;
+    uint64_t avail = S->tail - head;
+    uint32_t nin = (uint32_t)(avail < g.seg_cap ? avail : g.seg_cap);
+    if (*(volatile int *)g.lv.status != 0) nin = 0;  // an error: stop partitioning
     if (tid == 0) {
-        *g.list_count[(L + 1) & 1] = 0;
-        *g.base_count = 0;  // the previous base-case launch has consumed it
-        sh_bad = 0;
+        sh_cut = nin;
+        sh_elems = 0;
+        *g.lv.nmoves = 0;  // the fix-up moves of this wave start at 0
     }
-    if (nin > g.list_cap) nin = g.list_cap;
-    if (nin > g.seg_cap) {
-        if (tid == 0) set_status(g.lv.status, IPSGPU_E_NOMEM);
-        nin = 0;
-    }
-    // pass 1: elements and blocks of the level
+    // pass 1: elements and blocks waiting in the window
     unsigned long long te = 0, tb = 0;
     for (uint32_t i = tid; i < nin; i += kPlanThreads) {
-        te += in[i].n;
-        tb += (in[i].n + g.b - 1) / g.b;
+        const uint64_t n = g.ring[(head + i) % g.ring_cap].n;
+        te += n;
+        tb += (n + g.b - 1) / g.b;
     }
     for (int o = 16; o > 0; o >>= 1) {
         te += __shfl_xor_sync(0xffffffffu, te, o);
@@ -210,12 +288,12 @@ __global__ void __launch_bounds__(kPlanThreads) k_g_plan(GraphArgs g, int L) {
     stripe_elems = (stripe_elems + g.b - 1) / g.b * g.b;
     uint64_t bpc = tb / (8 * (uint64_t)g.nsm);
     if (bpc < 32) bpc = 32;
-    // pass 2: each thread owns a contiguous range of segments
+    // pass 2: each thread owns a contiguous range of the window
     const uint32_t per = (nin + kPlanThreads - 1) / kPlanThreads;
     const uint32_t r0 = min(nin, tid * per), r1 = min(nin, r0 + per);
-    unsigned long long loc[NV] = {0, 0, 0, 0, 0, 0, 0};
+    unsigned long long loc[NV] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (uint32_t i = r0; i < r1; i++) {
-        const GPlanItem it = g_item<T>(g, in[i].n, stripe_elems, bpc);
+        const GPlanItem it = g_item<T>(g, g.ring[(head + i) % g.ring_cap].n, stripe_elems, bpc);
         loc[0] += it.p;
         loc[1] += it.nc;
         loc[2] += it.C;
@@ -223,9 +301,10 @@ __global__ void __launch_bounds__(kPlanThreads) k_g_plan(GraphArgs g, int L) {
         loc[4] += it.sarr;
         loc[5] += it.keys;
         loc[6] += it.cnt;
+        loc[7] += it.moves;
     }
-    // exclusive scan of the seven sums over threads
-    unsigned long long incl[NV], excl[NV], tot[NV];
+    // exclusive scan of the sums over threads
+    unsigned long long excl[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) {
         unsigned long long x = loc[v];
@@ -233,74 +312,101 @@ __global__ void __launch_bounds__(kPlanThreads) k_g_plan(GraphArgs g, int L) {
             unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        incl[v] = x;
+        excl[v] = x - loc[v];
         if (lane == 31) wsum[v][warp] = x;
     }
     __syncthreads();
 #pragma unroll
     for (int v = 0; v < NV; v++) {
-        unsigned long long before = 0, all = 0;
-        for (int w = 0; w < kPlanThreads / 32; w++) {
-            if (w < warp) before += wsum[v][w];
-            all += wsum[v][w];
-        }
-        excl[v] = before + incl[v] - loc[v];
-        tot[v] = all;
+        unsigned long long before = 0;
+        for (int w = 0; w < warp; w++) before += wsum[v][w];
+        excl[v] += before;
     }
-    if (tid == 0 &&
-        (tot[0] > g.stripe_cap || tot[1] > g.cta_cap || tot[2] > g.cls_cap || tot[3] > g.arena_bytes ||
-         tot[4] > g.sarr_bytes || tot[5] > g.keys_bytes || tot[6] > g.cnt_cap ||
-         2 * (tot[0] + tot[2]) + 4 * (uint64_t)nin > g.lv.move_cap)) {
-        set_status(g.lv.status, IPSGPU_E_NOMEM);
-        sh_bad = 1;
+    const unsigned long long cap[NV] = {g.stripe_cap, g.cta_cap,    g.cls_cap,    g.arena_bytes,
+                                        g.sarr_bytes, g.keys_bytes, g.cnt_cap,    g.lv.move_cap};
+    // pass 3: the first entry whose running totals exceed a capacity
+    {
+        unsigned long long run[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) run[v] = excl[v];
+        for (uint32_t i = r0; i < r1; i++) {
+            const GPlanItem it = g_item<T>(g, g.ring[(head + i) % g.ring_cap].n, stripe_elems, bpc);
+            run[0] += it.p;
+            run[1] += it.nc;
+            run[2] += it.C;
+            run[3] += it.arena;
+            run[4] += it.sarr;
+            run[5] += it.keys;
+            run[6] += it.cnt;
+            run[7] += it.moves;
+            bool over = false;
+#pragma unroll
+            for (int v = 0; v < NV; v++) over |= run[v] > cap[v];
+            if (over) {
+                atomicMin(&sh_cut, i);
+                break;
+            }
+        }
     }
     __syncthreads();
-    if (sh_bad) nin = 0;
-    // pass 3: descriptors with running offsets
-    for (uint32_t i = r0; i < r1 && nin; i++) {
-        const GPlanItem it = g_item<T>(g, in[i].n, stripe_elems, bpc);
-        SegDesc d;
-        d.addr = in[i].addr;
-        d.n = in[i].n;
-        d.b = g.b;
-        d.C = it.C;
-        d.stripe0 = (uint32_t)excl[0];
-        d.nstripes = it.p;
-        d.cta0 = (uint32_t)excl[1];
-        d.ncta = it.nc;
-        d.cls0 = (uint32_t)excl[2];
-        d.stage_off = excl[3];
-        d.arr_off = excl[4];
-        d.key_off = excl[5];
-        d.cnt0 = (uint32_t)excl[6];
-        d.mode = g.algo == 1 ? 2u : 0u;
-        d.radix_shift = in[i].shift;
-        d.radix_bits = g.kbits;
-        d.nsplit = 0;
-        d.eq_given = 0;
-        const_cast<SegDesc *>(g.lv.seg)[i] = d;
-        excl[0] += it.p;
-        excl[1] += it.nc;
-        excl[2] += it.C;
-        excl[3] += it.arena;
-        excl[4] += it.sarr;
-        excl[5] += it.keys;
-        excl[6] += it.cnt;
+    const uint32_t cut = sh_cut;
+    // pass 4: descriptors of the taken prefix [0, cut)
+    unsigned long long my_elems = 0;
+    {
+        unsigned long long run[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) run[v] = excl[v];
+        for (uint32_t i = r0; i < r1 && i < cut; i++) {
+            const GList e = g.ring[(head + i) % g.ring_cap];
+            const GPlanItem it = g_item<T>(g, e.n, stripe_elems, bpc);
+            SegDesc d;
+            d.addr = e.addr;
+            d.n = e.n;
+            d.b = g.b;
+            d.C = it.C;
+            d.stripe0 = (uint32_t)run[0];
+            d.nstripes = it.p;
+            d.cta0 = (uint32_t)run[1];
+            d.ncta = it.nc;
+            d.cls0 = (uint32_t)run[2];
+            d.stage_off = run[3];
+            d.arr_off = run[4];
+            d.key_off = run[5];
+            d.cnt0 = (uint32_t)run[6];
+            d.mode = g.algo == 1 ? 2u : 0u;
+            d.radix_shift = e.shift;
+            d.radix_bits = g.kbits;
+            d.nsplit = 0;
+            d.eq_given = 0;
+            const_cast<SegDesc *>(g.lv.seg)[i] = d;
+            my_elems += e.n;
+            run[0] += it.p;
+            run[1] += it.nc;
+            run[2] += it.C;
+            run[3] += it.arena;
+            run[4] += it.sarr;
+            run[5] += it.keys;
+            run[6] += it.cnt;
+            run[7] += it.moves;
+            if (i + 1 == cut) {  // the last taken entry knows the totals
+                S->counts = LevelCounts{cut, (uint32_t)run[0], (uint32_t)run[1], (uint32_t)run[2]};
+            }
+        }
     }
+    if (my_elems) atomicAdd(&sh_elems, my_elems);
+    __syncthreads();
     if (tid == 0) {
-        LevelCounts c;
-        c.nseg = nin;
-        c.nstripe = nin ? (uint32_t)tot[0] : 0u;
-        c.ncta = nin ? (uint32_t)tot[1] : 0u;
-        c.ncls = nin ? (uint32_t)tot[2] : 0u;
-        *g.counts = c;
+        S->elems = sh_elems;
+        S->take = cut;
+        if (cut == 0) S->counts = LevelCounts{0, 0, 0, 0};
+        if (cut == 0 && nin > 0) set_status(g.lv.status, IPSGPU_E_NOMEM);  // cannot happen
     }
 }
 
-// Stripe descriptors and the CTA -> segment map of the planned level.
+// Stripe descriptors and the CTA -> segment map of the planned wave.
 template <class T>
 __global__ void __launch_bounds__(256) k_g_fill_stripes(GraphArgs g) {
-    const LevelCounts c = *g.counts;
+    const LevelCounts c = g.state->counts;
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
     for (uint32_t i = t0; i < c.nstripe; i += stride) {
@@ -338,11 +444,12 @@ __global__ void __launch_bounds__(256) k_g_fill_stripes(GraphArgs g) {
     }
 }
 
-// Children of every (segment, class) of level L.
+// Children of every (segment, class) of the wave.
 template <class T>
-__global__ void __launch_bounds__(256) k_g_emit(GraphArgs g, int L) {
+__global__ void __launch_bounds__(256) k_g_emit(GraphArgs g) {
     if (*(volatile int *)g.lv.status != 0) return;  // an error: leave the data as is
-    const LevelCounts c = *g.counts;
+    const LevelCounts c = g.state->counts;
+    const uint64_t floor = g.state->head + g.state->take;  // taken entries are free now
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < c.ncls; q += stride) {
         uint32_t lo = 0, hi = c.nseg;  // last segment with cls0 <= q
@@ -367,23 +474,43 @@ __global__ void __launch_bounds__(256) k_g_emit(GraphArgs g, int L) {
             if (sd.radix_shift == 0) continue;  // every key bit used: equal keys
             shift = sd.radix_shift >= g.kbits ? sd.radix_shift - g.kbits : 0u;
         }
-        if (n <= g.smax) {
+        if (n <= g.smax)
             g_push_base(g, sd.addr + b0 * T::D, n);
-        } else if (L + 1 < g.levels) {
-            g_push_list(g, (L + 1) & 1, GList{sd.addr + b0 * T::D, n, shift, 0u});
-        } else {
-            set_status(g.lv.status, IPSGPU_E_INTERNAL);  // deeper than planned
-        }
+        else
+            g_push_ring(g, floor, GList{sd.addr + b0 * T::D, n, shift, 0u});
     }
 }
 
-// Last launch of a batch: bad input offsets become E_INVAL in the status word
-// (unless an earlier error is already recorded) and the flag is cleared.
-static __global__ void k_g_finish(GraphArgs g) {
-    if (threadIdx.x == 0 && blockIdx.x == 0 && *g.invalid) {
-        set_status(g.lv.status, IPSGPU_E_INVAL);
-        *g.invalid = 0;
+// Ends a wave (one thread): consumes the taken ring entries and the fed
+// inputs, clears the base list, and decides whether another wave runs:
+// while inputs or ring entries remain, no error is recorded and the wave
+// bound is not reached.  Every wave feeds or partitions at least one
+// segment, and children are smaller than their parent (or, for radix, have
+// fewer key bits left), so the loop ends; max_waves only guards against an
+// inconsistency.  When the run ends, bad inputs become E_INVAL.
+static __global__ void k_g_advance(GraphArgs g, cudaGraphConditionalHandle h, int in_graph) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    GState *S = g.state;
+    const GJob j = *g.job;
+    S->head += S->take;
+    S->in_head += S->feed;
+    S->take = 0;
+    S->base_count = 0;
+    S->elems = 0;
+    S->base_elems = 0;
+    S->counts = LevelCounts{0, 0, 0, 0};
+    S->wave += 1;
+    const bool work = S->in_head < j.nseg_in || S->head < S->tail;
+    const int status = *(volatile int *)g.lv.status;
+    uint32_t more = (work && status == 0) ? 1u : 0u;
+    if (more && S->wave >= j.max_waves) {
+        set_status(g.lv.status, IPSGPU_E_INTERNAL);
+        more = 0;
     }
+    S->feed = more ? g_feed_count(g, j, S->in_head, S->tail - S->head) : 0u;
+    if (!more && S->invalid) set_status(g.lv.status, IPSGPU_E_INVAL);
+    S->more = more;
+    if (in_graph) cudaGraphSetConditional(h, more);
 }
 
 }  // namespace ipsgpu

@@ -83,6 +83,8 @@ int resolve(const ipsgpu_params *p, int dtype, Resolved *r) {
     if (r->base_case < 32 || r->base_case > cap) return IPSGPU_E_INVAL;
     uint32_t b = block_elems(r->block_bytes, ops->D);
     if (b == 0 || (uint64_t)b * ops->D * r->k > 160u * 1024 || (b * ops->D) % 16) return IPSGPU_E_INVAL;
+    // the arena holds at least one segment with one stripe of k classes
+    if (r->arena_bytes < 2ull * r->k * b * ops->D + (uint64_t)b * ops->D + 1024) return IPSGPU_E_INVAL;
     if (r->algo != IPSGPU_SAMPLESORT && r->algo != IPSGPU_RADIX) return IPSGPU_E_INVAL;
     if (r->algo == IPSGPU_RADIX &&
         !(dtype == IPSGPU_U32 || dtype == IPSGPU_U64 || dtype == IPSGPU_PAIR_U64))
@@ -91,9 +93,9 @@ int resolve(const ipsgpu_params *p, int dtype, Resolved *r) {
 }
 
 struct Layout {
-    uint64_t seg, st, sarr, keys, stripe, scount, sfull, arena, moves, cta, base, glist, misc;
+    uint64_t seg, st, sarr, keys, stripe, scount, sfull, arena, moves, cta, base, ring, misc;
     uint64_t total() const {
-        return seg + st + sarr + keys + stripe + scount + sfull + arena + moves + cta + base + glist +
+        return seg + st + sarr + keys + stripe + scount + sfull + arena + moves + cta + base + ring +
                misc;
     }
 };
@@ -114,8 +116,8 @@ Layout layout(const Sorter &s, int key_bytes) {
     L.moves = (uint64_t)s.move_cap * sizeof(Move);
     L.cta = (uint64_t)s.cta_cap * sizeof(uint32_t);
     L.base = (uint64_t)s.base_cap * 2 * sizeof(uint64_t);
-    L.glist = 2ull * s.seg_cap * sizeof(GList);
-    L.misc = 256;
+    L.ring = (uint64_t)s.ring_cap * sizeof(GList);
+    L.misc = 1024;
     return L;
 }
 
@@ -142,10 +144,13 @@ void free_all(Sorter &s) {
     void *dev[] = {s.d_seg,    s.d_st,     s.d_sarr,   s.d_keys,    s.d_stripe,
                    s.d_scount, s.d_sfull,  s.d_arena,  s.d_moves,   s.d_nmoves,
                    s.d_status, s.d_cta_seg, s.d_base,    s.d_flags,
-                   s.d_waitflag, s.d_glist, s.d_gcount};
+                   s.d_waitflag, s.d_ring, s.d_gjob, s.d_gstate};
     for (void *p : dev)
         if (p) cudaFree(p);
-    void *host[] = {s.h_seg, s.h_stripe, s.h_cta_seg, s.h_flags};
+    if (s.wave_exec) cudaGraphExecDestroy(s.wave_exec);
+    if (s.wave_graph) cudaGraphDestroy(s.wave_graph);
+    if (s.cap_stream) cudaStreamDestroy(s.cap_stream);
+    void *host[] = {s.h_seg, s.h_stripe, s.h_cta_seg, s.h_flags, s.h_gstate};
     for (void *p : host)
         if (p) cudaFreeHost(p);
     for (auto &l : s.launches) {
@@ -282,52 +287,19 @@ int check_data(const Sorter &s, const void *d) {
     return ((uintptr_t)d % elem_align(s.ops->D)) ? IPSGPU_E_INVAL : IPSGPU_OK;
 }
 
-// Level count of a device-planned batch whose largest array has max_n
-// elements: radix consumes kbits key bits per level; samplesort shrinks a
-// segment of m elements by its class budget per level (expected), plus slack
-// levels for children that an unlucky sample left above the base-case size.
-int graph_levels(const Sorter &s, uint64_t max_n) {
-    const uint32_t kbits = (uint32_t)__builtin_ctz(s.k);
-    if (max_n <= s.smax) return 0;
-    if (s.algo == IPSGPU_RADIX) {
-        const uint32_t keybits = s.ops->D == 4 ? 32 : 64;
-        return (int)((keybits + kbits - 1) / kbits);
-    }
-    int L = 0;
-    for (uint64_t m = max_n; m > s.smax; L++) {
-        const uint32_t C = class_budget(s, m);
-        m = (m + C - 1) / C;
-    }
-    return L + 2;
-}
-
-// One device-planned run (graph.cuh) over the input given by exactly one of
-// offsets (into data), segs ((address, n) pairs) or neither (data[0..n)).
-int graph_run(Sorter &s, unsigned char *data, uint64_t n_total, const uint64_t *d_offsets,
-              const uint64_t *d_segs, uint64_t nseg, uint64_t max_n, const int *skip_flags,
-              cudaStream_t st) {
-    s.data = data;
-    s.level_elems = n_total;
+// Fixed arguments of the device-planned recursion of this sorter.
+GraphArgs graph_args(Sorter &s) {
     GraphArgs ga;
     memset(&ga, 0, sizeof ga);
     ga.lv = s.args(0, 0, 0, 0, nullptr);
-    ga.counts = reinterpret_cast<LevelCounts *>(s.d_gcount);
-    ga.list_count[0] = s.d_gcount + 4;
-    ga.list_count[1] = s.d_gcount + 5;
-    ga.base_count = s.d_gcount + 6;
-    ga.invalid = s.d_gcount + 7;
-    ga.list[0] = reinterpret_cast<GList *>(s.d_glist);
-    ga.list[1] = ga.list[0] + s.seg_cap;
+    ga.job = reinterpret_cast<GJob *>(s.d_gjob);
+    ga.state = reinterpret_cast<GState *>(s.d_gstate);
+    ga.lv.cnt = &ga.state->counts;
+    ga.ring = reinterpret_cast<GList *>(s.d_ring);
     ga.base_list = s.d_base;
-    ga.offsets = d_offsets;
-    ga.segs = d_segs;
-    ga.skip_flags = skip_flags;
-    ga.nseg_in = nseg;
-    ga.n_total = n_total;
-    ga.elem_bytes = (uint32_t)s.ops->D;
-    ga.elem_align = (uint32_t)elem_align(s.ops->D);
-    ga.list_cap = s.seg_cap;
+    ga.ring_cap = s.ring_cap;
     ga.base_cap = s.base_cap;
+    ga.feed_cap = s.base_cap - s.cls_cap;
     ga.seg_cap = s.seg_cap;
     ga.stripe_cap = s.stripe_cap;
     ga.cta_cap = s.cta_cap;
@@ -339,12 +311,140 @@ int graph_run(Sorter &s, unsigned char *data, uint64_t n_total, const uint64_t *
     ga.nsm = (uint32_t)s.nsm;
     ga.kbits = (uint32_t)__builtin_ctz(s.k);
     ga.keybits = s.ops->D == 4 ? 32 : 64;
+    ga.elem_bytes = (uint32_t)s.ops->D;
+    ga.elem_align = (uint32_t)elem_align(s.ops->D);
     ga.arena_bytes = s.arena_bytes;
     ga.sarr_bytes = s.sarr_bytes;
     ga.keys_bytes = s.keys_bytes;
     ga.algo = s.algo == IPSGPU_RADIX ? 1 : 0;
-    ga.levels = graph_levels(s, max_n);
-    return cuda_status(s.ops->segmented(&s, ga, st));
+    return ga;
+}
+
+// Bound on the waves of one run; the loop ends by itself long before (every
+// wave makes progress), the bound only stops an inconsistent run.
+constexpr uint32_t kMaxWaves = 1u << 20;
+
+// Builds a graph that runs waves while k_g_advance says so: an optional
+// k_g_job node (the run's input) followed by a conditional WHILE node whose
+// body is one wave.
+int build_wave_graph(Sorter &s, const GJob *job, cudaGraph_t *out_graph, cudaGraphExec_t *out_exec) {
+    *out_graph = nullptr;
+    *out_exec = nullptr;
+    if (!s.cap_stream &&
+        cudaStreamCreateWithFlags(&s.cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return IPSGPU_E_CUDA;
+    const GraphArgs ga = graph_args(s);
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    const bool timing = s.timing;
+    s.timing = false;  // no event records inside a graph
+    int rc = IPSGPU_OK;
+    do {
+        if (cudaGraphCreate(&g, 0) != cudaSuccess) { rc = IPSGPU_E_CUDA; break; }
+        cudaGraphNode_t jobnode = nullptr;
+        if (job) {
+            if (cudaStreamBeginCaptureToGraph(s.cap_stream, g, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                rc = IPSGPU_E_CUDA;
+                break;
+            }
+            k_g_job<<<1, 32, 0, s.cap_stream>>>(ga, *job);
+            cudaGraph_t g2 = nullptr;
+            if (cudaStreamEndCapture(s.cap_stream, &g2) != cudaSuccess) { rc = IPSGPU_E_CUDA; break; }
+            size_t nn = 1;
+            if (cudaGraphGetNodes(g, &jobnode, &nn) != cudaSuccess || nn != 1) {
+                rc = IPSGPU_E_CUDA;
+                break;
+            }
+        }
+        cudaGraphConditionalHandle h;
+        if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+            rc = IPSGPU_E_CUDA;
+            break;
+        }
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t cond;
+        if (cudaGraphAddNode(&cond, g, job ? &jobnode : nullptr, nullptr, job ? 1 : 0, &p) !=
+            cudaSuccess) {
+            rc = IPSGPU_E_CUDA;
+            break;
+        }
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(s.cap_stream, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            rc = IPSGPU_E_CUDA;
+            break;
+        }
+        rc = cuda_status(s.ops->wave(&s, ga, s.cap_stream, 1, h));
+        cudaGraph_t body2 = nullptr;
+        if (cudaStreamEndCapture(s.cap_stream, &body2) != cudaSuccess && rc == IPSGPU_OK)
+            rc = IPSGPU_E_CUDA;
+        if (rc) break;
+        if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) rc = IPSGPU_E_CUDA;
+    } while (0);
+    s.timing = timing;
+    if (rc) {
+        if (ex) cudaGraphExecDestroy(ex);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc;
+    }
+    *out_graph = g;
+    *out_exec = ex;
+    return IPSGPU_OK;
+}
+
+// One device-planned run (graph.cuh) over `job`: the sorter's WHILE graph
+// after a k_g_job launch, or, with per-kernel timing on, the same waves from
+// a host loop (one synchronization per wave to read the decision back).
+int graph_run(Sorter &s, const GJob &job, cudaStream_t st) {
+    const GraphArgs ga = graph_args(s);
+    k_g_job<<<1, 32, 0, st>>>(ga, job);
+    if (cudaGetLastError() != cudaSuccess) return IPSGPU_E_CUDA;
+    if (!s.timing) {
+        if (!s.wave_exec) {
+            int rc = build_wave_graph(s, nullptr, &s.wave_graph, &s.wave_exec);
+            if (rc) return rc;
+        }
+        return cuda_status(cudaGraphLaunch(s.wave_exec, st));
+    }
+    for (uint32_t w = 0; w < kMaxWaves; w++) {
+        const size_t l0 = s.launches.size();
+        cudaError_t e = s.ops->wave(&s, ga, st, 0, cudaGraphConditionalHandle());
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s.h_gstate, ga.state, sizeof(GState), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return IPSGPU_E_CUDA;
+        const GState &gs = *reinterpret_cast<const GState *>(s.h_gstate);
+        // algorithmic bytes of the wave's launches (2 D per element moved)
+        for (size_t q = l0; q < s.launches.size(); q++) {
+            TimedLaunch &l = s.launches[q];
+            if (l.kind == KK_CLASSIFY || l.kind == KK_PERMUTE)
+                l.bytes = 2.0 * (double)gs.elems * s.ops->D;
+            else if (l.kind == KK_BASE)
+                l.bytes = 2.0 * (double)gs.base_elems * s.ops->D;
+        }
+        if (!gs.more) break;
+    }
+    return IPSGPU_OK;
+}
+
+GJob make_job(unsigned char *data, uint64_t n_total, const uint64_t *offsets, const uint64_t *segs,
+              uint64_t nseg, const int *skip_flags) {
+    GJob j;
+    memset(&j, 0, sizeof j);
+    j.data = data;
+    j.offsets = offsets;
+    j.segs = segs;
+    j.skip_flags = skip_flags;
+    j.nseg_in = nseg;
+    j.n_total = n_total;
+    j.max_waves = kMaxWaves;
+    return j;
 }
 
 // The whole sort on the device (no host synchronization): Sec. 5's check for
@@ -360,7 +460,8 @@ int sort_impl(Sorter &s, unsigned char *data, uint64_t n, cudaStream_t st) {
     if (e == cudaSuccess) e = s.ops->detect(&s, data, n, st);
     if (e == cudaSuccess) e = s.ops->reverse(&s, data, n, st);
     if (e != cudaSuccess) return IPSGPU_E_CUDA;
-    return graph_run(s, data, n, nullptr, nullptr, 1, n, s.d_flags, st);
+    s.level_elems = n;
+    return graph_run(s, make_job(data, n, nullptr, nullptr, 1, s.d_flags), st);
 }
 
 int single_level(Sorter &s, unsigned char *data, uint64_t n, uint32_t mode, uint32_t nsplit,
@@ -507,12 +608,14 @@ int ipsgpu_sorter_create(const ipsgpu_params *params, int dtype, ipsgpu_sorter *
     dm((void **)&s.d_base, L.base);
     dm((void **)&s.d_flags, 64);
     dm((void **)&s.d_waitflag, 64);
-    dm((void **)&s.d_glist, L.glist);
-    dm((void **)&s.d_gcount, 64);
+    dm((void **)&s.d_ring, L.ring);
+    dm((void **)&s.d_gjob, 256);
+    dm((void **)&s.d_gstate, 256);
     hm((void **)&s.h_seg, L.seg);
     hm((void **)&s.h_stripe, L.stripe);
     hm((void **)&s.h_cta_seg, L.cta);
     hm((void **)&s.h_flags, 64);
+    hm((void **)&s.h_gstate, 256);
     if (ok && cudaEventCreateWithFlags(&s.h2d_done, cudaEventDisableTiming) != cudaSuccess) ok = false;
     if (ok && (cudaMemset(s.d_status, 0, 64) != cudaSuccess ||
                cudaMemset(s.d_waitflag, 0, 64) != cudaSuccess))
@@ -609,16 +712,19 @@ int ipsgpu_sort_segmented(ipsgpu_sorter *h, void *d_data, uint64_t n, const uint
     int rc = check_segmented(h, d_data, n, d_offsets, num_segments);
     if (rc) return rc;
     if (n < 2 || num_segments == 0) return IPSGPU_OK;
-    return graph_run(h->s, (unsigned char *)d_data, n, d_offsets, nullptr, num_segments, n, nullptr,
+    h->s.level_elems = n;
+    return graph_run(h->s, make_job((unsigned char *)d_data, n, d_offsets, nullptr, num_segments,
+                                    nullptr),
                      (cudaStream_t)stream);
 }
 
 int ipsgpu_sort_batch(ipsgpu_sorter *h, const uint64_t *d_segs, uint64_t num_segments,
-                      uint64_t max_n, void *stream) {
-    if (!h || max_n > (1ull << 40) || num_segments > 0xFFFFFFFFull) return IPSGPU_E_INVAL;
-    if (num_segments == 0 || max_n < 2) return IPSGPU_OK;
+                      void *stream) {
+    if (!h || num_segments > 0xFFFFFFFFull) return IPSGPU_E_INVAL;
+    if (num_segments == 0) return IPSGPU_OK;
     if (!d_segs || ((uintptr_t)d_segs % 8)) return IPSGPU_E_INVAL;
-    return graph_run(h->s, nullptr, 0, nullptr, d_segs, num_segments, max_n, nullptr,
+    h->s.level_elems = 0;
+    return graph_run(h->s, make_job(nullptr, 0, nullptr, d_segs, num_segments, nullptr),
                      (cudaStream_t)stream);
 }
 
@@ -634,36 +740,12 @@ int ipsgpu_segmented_graph_create(ipsgpu_sorter *h, void *d_data, uint64_t n,
     *out = nullptr;
     int rc = check_segmented(h, d_data, n, d_offsets, num_segments);
     if (rc) return rc;
-    Sorter &s = h->s;
     ipsgpu_graph *g = new (std::nothrow) ipsgpu_graph;
     if (!g) return IPSGPU_E_NOMEM;
-    cudaStream_t cs = nullptr;
-    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
-        delete g;
-        return IPSGPU_E_CUDA;
-    }
-    const bool timing = s.timing;
-    s.timing = false;  // no event records inside the graph
-    rc = IPSGPU_OK;
-    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        rc = IPSGPU_E_CUDA;
-    } else {
-        if (n >= 2 && num_segments > 0)
-            rc = graph_run(s, (unsigned char *)d_data, n, d_offsets, nullptr, num_segments, n,
-                           nullptr, cs);
-        else
-            rc = cuda_status(cudaMemsetAsync(s.d_gcount, 0, sizeof(uint32_t), cs));  // an empty graph node
-        cudaError_t e = cudaStreamEndCapture(cs, &g->graph);
-        if (rc == IPSGPU_OK && e != cudaSuccess) rc = IPSGPU_E_CUDA;
-    }
-    s.timing = timing;
-    if (rc == IPSGPU_OK && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) rc = IPSGPU_E_CUDA;
-    cudaStreamDestroy(cs);
+    const GJob job = make_job((unsigned char *)d_data, n, d_offsets, nullptr, num_segments, nullptr);
+    rc = build_wave_graph(h->s, &job, &g->graph, &g->exec);
     if (rc) {
-        if (g->exec) cudaGraphExecDestroy(g->exec);
-        if (g->graph) cudaGraphDestroy(g->graph);
         delete g;
-        cudaGetLastError();
         return rc;
     }
     *out = g;

@@ -37,7 +37,9 @@ struct OpsImpl {
     static cudaError_t level(Sorter *s, const LevelArgs &a, const LevelGrids &g, cudaStream_t st) {
         const double lvl = (double)s->level_elems * T::D;
         cudaError_t e;
-        if ((e = cudaMemsetAsync(s->d_nmoves, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+        // a device-planned wave clears the move counter in k_g_plan
+        if (!a.cnt && (e = cudaMemsetAsync(a.nmoves, 0, sizeof(uint32_t), st)) != cudaSuccess)
+            return e;
         s->tbegin(KK_SAMPLE, 0, st);
         k_sample_tree<T><<<g.seg, kSampleThreads, sample_smem(), st>>>(a);
         s->tend(st);
@@ -107,46 +109,33 @@ struct OpsImpl {
         return cudaGetLastError();
     }
 
-    // The device-planned segmented batch (graph.cuh): the input segments in
-    // chunks of at most base_cap (split, then base case), then ga.levels
-    // levels of plan -> level kernels -> emit -> base case.  Every launch
+    // One wave of the device-planned recursion (graph.cuh).  Every launch
     // has a fixed grid and reads its work counts from device memory, so the
-    // sequence depends only on (nseg_in, levels) and can be captured.
-    static cudaError_t segmented(Sorter *s, const GraphArgs &ga, cudaStream_t st) {
-        cudaError_t e;
+    // same sequence serves as the body of the graph's WHILE loop (in_graph)
+    // and as one step of the host-driven loop used when timing kernels.
+    static cudaError_t wave(Sorter *s, const GraphArgs &ga, cudaStream_t st, int in_graph,
+                            cudaGraphConditionalHandle h) {
         const uint32_t big = (uint32_t)s->nsm * 8;
-        if ((e = cudaMemsetAsync(ga.list_count[0], 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(ga.invalid, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
-        for (uint64_t i0 = 0; i0 < ga.nseg_in; i0 += ga.base_cap) {
-            const uint64_t i1 = i0 + ga.base_cap < ga.nseg_in ? i0 + ga.base_cap : ga.nseg_in;
-            if ((e = cudaMemsetAsync(ga.base_count, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
-            s->tbegin(KK_PLAN, 0, st);
-            k_g_init<<<big, kAuxThreads, 0, st>>>(ga, i0, i1);
-            s->tend(st);
-            if ((e = base(s, ga.base_list, 0, ga.base_count, s->nsm, st)) != cudaSuccess)
-                return e;
-        }
-        for (int L = 0; L < ga.levels; L++) {
-            s->tbegin(KK_PLAN, 0, st);
-            k_g_plan<T><<<1, kPlanThreads, 0, st>>>(ga, L);
-            k_g_fill_stripes<T><<<big, kAuxThreads, 0, st>>>(ga);
-            s->tend(st);
-            LevelArgs a = ga.lv;
-            a.cnt = ga.counts;
-            LevelGrids g;
-            g.seg = (uint32_t)s->nsm * 4;
-            g.stripe = (uint32_t)s->nsm;
-            g.cta = (uint32_t)s->nsm * 8;
-            g.cls = big;
-            if ((e = level(s, a, g, st)) != cudaSuccess) return e;
-            s->tbegin(KK_PLAN, 0, st);
-            k_g_emit<T><<<big, kAuxThreads, 0, st>>>(ga, L);
-            s->tend(st);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            if ((e = base(s, ga.base_list, 0, ga.base_count, s->nsm, st)) != cudaSuccess)
-                return e;
-        }
-        k_g_finish<<<1, 32, 0, st>>>(ga);
+        s->tbegin(KK_PLAN, 0, st);
+        k_g_feed<<<big, kAuxThreads, 0, st>>>(ga);
+        k_g_plan<T><<<1, kPlanThreads, 0, st>>>(ga);
+        k_g_fill_stripes<T><<<big, kAuxThreads, 0, st>>>(ga);
+        s->tend(st);
+        LevelArgs a = ga.lv;
+        a.cnt = &ga.state->counts;
+        LevelGrids g;
+        g.seg = (uint32_t)s->nsm * 4;
+        g.stripe = (uint32_t)s->nsm;
+        g.cta = (uint32_t)s->nsm * 8;
+        g.cls = big;
+        cudaError_t e;
+        if ((e = level(s, a, g, st)) != cudaSuccess) return e;
+        s->tbegin(KK_PLAN, 0, st);
+        k_g_emit<T><<<big, kAuxThreads, 0, st>>>(ga);
+        s->tend(st);
+        if ((e = base(s, ga.base_list, 0, &ga.state->base_count, s->nsm, st)) != cudaSuccess)
+            return e;
+        k_g_advance<<<1, 32, 0, st>>>(ga, h, in_graph);
         return cudaGetLastError();
     }
 
@@ -160,7 +149,7 @@ struct OpsImpl {
         o.detect = &detect;
         o.reverse = &reverse;
         o.classify_ids = &classify_ids;
-        o.segmented = &segmented;
+        o.wave = &wave;
         return o;
     }
 };

@@ -48,7 +48,8 @@ struct TypeOps {
     cudaError_t (*detect)(Sorter *, const unsigned char *data, uint64_t n, cudaStream_t);
     cudaError_t (*reverse)(Sorter *, unsigned char *data, uint64_t n, cudaStream_t);
     cudaError_t (*classify_ids)(Sorter *, const LevelArgs &, uint32_t *out, cudaStream_t);
-    cudaError_t (*segmented)(Sorter *, const GraphArgs &, cudaStream_t);
+    cudaError_t (*wave)(Sorter *, const GraphArgs &, cudaStream_t, int in_graph,
+                        cudaGraphConditionalHandle);
 };
 
 extern const TypeOps ops_u32, ops_u64, ops_f64, ops_pair, ops_rec100;
@@ -81,7 +82,8 @@ struct Sorter {
     uint32_t cls_cap = 1u << 20;     // (segment, class) pairs
     uint32_t cnt_cap = 1u << 21;     // per-stripe class counters
     uint32_t move_cap = 1u << 22;    // fix-up moves
-    uint32_t base_cap = 1u << 20;    // base-case segments per launch (>= cls_cap)
+    uint32_t base_cap = 1u << 21;    // base-case segments per wave (>= cls_cap + feed)
+    uint32_t ring_cap = 1u << 20;    // segments waiting for a partitioning step
     uint64_t sarr_bytes = 0, keys_bytes = 0;
     // device scratch
     SegDesc *d_seg = nullptr;
@@ -97,8 +99,13 @@ struct Sorter {
     uint64_t *d_base = nullptr;
     int *d_flags = nullptr;
     uint32_t *d_waitflag = nullptr;
-    unsigned char *d_glist = nullptr;  // two segment lists of the device planner
-    uint32_t *d_gcount = nullptr;      // LevelCounts, two list counts, base count
+    unsigned char *d_ring = nullptr;   // device planner: segments waiting (GList)
+    unsigned char *d_gjob = nullptr;   // GJob of the current run
+    unsigned char *d_gstate = nullptr; // GState of the current run
+    unsigned char *h_gstate = nullptr; // pinned: GState read back by the host-driven loop
+    cudaStream_t cap_stream = nullptr; // stream used to capture the wave graph
+    cudaGraph_t wave_graph = nullptr;  // WHILE loop over waves (built on first use)
+    cudaGraphExec_t wave_exec = nullptr;
     // pinned host mirrors
     SegDesc *h_seg = nullptr;
     StripeDesc *h_stripe = nullptr;

@@ -60,7 +60,7 @@ def load():
         "ipsgpu_debug_bounded_wait": (i32, [vp, u32, vp]),
         "ipsgpu_partition_level_noalloc": (i32, [i32, vp, u64, vp, u32, i32, vp, vp]),
         "ipsgpu_sort_segmented": (i32, [vp, vp, u64, vp, u64, vp]),
-        "ipsgpu_sort_batch": (i32, [vp, vp, u64, u64, vp]),
+        "ipsgpu_sort_batch": (i32, [vp, vp, u64, vp]),
         "ipsgpu_segmented_graph_create": (i32, [vp, vp, u64, vp, u64, ctypes.POINTER(vp)]),
         "ipsgpu_graph_launch": (i32, [vp, vp]),
         "ipsgpu_graph_nodes": (i32, [vp, ctypes.POINTER(u64)]),
@@ -153,10 +153,10 @@ class Sorter:
         _check(load().ipsgpu_sort_segmented(self._h, ptr, n, offsets_ptr, num_segments, stream),
                "ipsgpu_sort_segmented")
 
-    def sort_batch(self, segs_ptr, num_segments, max_n, stream=0):
+    def sort_batch(self, segs_ptr, num_segments, stream=0):
         """Sort separate arrays in place; segs_ptr points to num_segments
         (device address, length) u64 pairs in device memory."""
-        _check(load().ipsgpu_sort_batch(self._h, segs_ptr, num_segments, max_n, stream),
+        _check(load().ipsgpu_sort_batch(self._h, segs_ptr, num_segments, stream),
                "ipsgpu_sort_batch")
 
     def segmented_graph(self, ptr, n, offsets_ptr, num_segments):

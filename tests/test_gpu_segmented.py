@@ -154,7 +154,7 @@ def test_segmented_graph_replay_refilled():
     off = offsets.to(DEV)
     with ipsgpu.Sorter("u64") as s:
         g = s.segmented_graph(d.data_ptr(), n, off.data_ptr(), len(lengths))
-        assert g.nodes() > 10
+        assert g.nodes() == 2  # the run's setup node and the WHILE loop over waves
         for host in (data1, data2, data1):
             d.copy_(host.to(DEV))
             g.launch(stream())
@@ -188,7 +188,7 @@ def test_sort_batch_separate_arrays():
             for h in hosts]
     segs = torch.tensor([[t.data_ptr(), t.numel()] for t in devs], dtype=torch.int64).to(DEV)
     with ipsgpu.Sorter("u64") as s:
-        s.sort_batch(segs.data_ptr(), len(devs), max(lengths), stream())
+        s.sort_batch(segs.data_ptr(), len(devs), stream())
         assert s.status(stream()) == ipsgpu.OK
     for h, t in zip(hosts, devs):
         got = inputs.to_numpy(t.cpu(), "u64")
@@ -203,7 +203,36 @@ def test_sort_batch_pairs_and_bad_entry():
     rows_.append([devs[0].data_ptr() + 8, 100])  # misaligned for 16-byte pairs: skipped
     segs = torch.tensor(rows_, dtype=torch.int64).to(DEV)
     with ipsgpu.Sorter("pair") as s:
-        s.sort_batch(segs.data_ptr(), len(rows_), 90_000, stream())
+        s.sort_batch(segs.data_ptr(), len(rows_), stream())
         assert s.status(stream()) == ipsgpu.E_INVAL
     for h, t in zip(hosts, devs):
         assert_sorted_parity(inputs.to_numpy(t.cpu(), "pair"), inputs.to_numpy(h, "pair"), "pair")
+
+
+@pytest.mark.parametrize("timing", [False, True])
+def test_small_arena_forces_many_waves(timing):
+    # a 2 MiB arena holds only a few segments per wave, so every level is
+    # split over many waves; the host-driven loop (timing on) must agree
+    lengths = inputs.segment_lengths(400, 10, 19, seed=61)
+    data, offsets = inputs.segmented_batch(lengths, seed=61)
+    n = data.numel()
+    d = to_dev(data)
+    off = offsets.to(DEV)
+    big = inputs.generate("exponential", "u64", 3_000_000, seed=62)
+    db = to_dev(big)
+    with ipsgpu.Sorter("u64", arena_bytes=2 << 20) as s:
+        s.set_timing(timing)
+        s.sort_segmented(d.data_ptr(), n, off.data_ptr(), len(lengths), stream())
+        s.sort(db.data_ptr(), big.numel(), stream())
+        assert s.status(stream()) == ipsgpu.OK
+        if timing:
+            st = s.kernel_stats()
+            assert st["classify"][0] > 10 and st["plan"][0] > 10
+    _check_segments(inputs.to_numpy(d.cpu(), "u64"), inputs.to_numpy(data, "u64"),
+                    offsets.numpy(), "u64")
+    assert_sorted_parity(inputs.to_numpy(db.cpu(), "u64"), inputs.to_numpy(big, "u64"), "u64")
+
+
+def test_arena_too_small_rejected():
+    with pytest.raises(ipsgpu.IpsgpuError):
+        ipsgpu.Sorter("u64", arena_bytes=64 << 10)
