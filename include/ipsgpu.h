@@ -107,6 +107,12 @@ typedef struct ipsgpu_sorter ipsgpu_sorter;
  * REC100), E_NOMEM, E_CUDA. */
 int ipsgpu_sorter_create(const ipsgpu_params *params, int dtype, ipsgpu_sorter **out);
 
+/* Build now what a sorter otherwise builds on its first sort: the CUDA graph
+ * of the device-planned recursion (a capture on a private stream).  Call it
+ * before capturing other work if the first sort would fall inside a capture
+ * window.  Errors: E_INVAL, E_CUDA. */
+int ipsgpu_sorter_prepare(ipsgpu_sorter *s);
+
 /* Free a sorter and its scratch (synchronizes the device first). */
 int ipsgpu_sorter_destroy(ipsgpu_sorter *s);
 
@@ -223,6 +229,71 @@ const char *ipsgpu_kernel_name(int kind);
  * flag that nothing sets, so the wait must give up and record
  * IPSGPU_E_TIMEOUT in the status word (read it with ipsgpu_status). */
 int ipsgpu_debug_bounded_wait(ipsgpu_sorter *s, uint32_t spin_limit, void *stream);
+
+/* ------------------------------------------------------------------ serving
+ * A server sorts requests that arrive at any time: it admits them by HBM
+ * footprint and runs them on a few CUDA streams ("lanes") while others are
+ * in flight.  The caller owns every request's device buffer.
+ *   - Footprint: a request of n elements of type t needs n * sizeof(t) bytes,
+ *     its own data, because the sort is in place; the server adds the fixed
+ *     scratch of one sorter per (lane, served type), allocated at creation.
+ *     A request is admitted while the admitted requests plus that scratch
+ *     stay within hbm_budget_bytes.
+ *   - Batching: started requests wait in one FIFO queue.  Requests of at most
+ *     batch_max_elems elements are batched (oldest first, one type per batch,
+ *     at most batch_max_requests) into one ipsgpu_sort_batch run on a
+ *     high-priority lane; larger ones run alone (ipsgpu_sort) on lane 0 at
+ *     low priority.  A request that cannot run yet does not hold back those
+ *     behind it.
+ *   - Each request's result is exactly what ipsgpu_sort gives for it alone
+ *     (for PAIR_U64 and REC100: the same keys, records with equal keys in
+ *     some order).
+ * Thread safety: every server call may be made from any host thread. */
+typedef struct ipsgpu_server ipsgpu_server;
+typedef struct {
+    uint64_t hbm_budget_bytes;    /* admitted request bytes + server scratch */
+    uint64_t batch_max_elems;     /* 0: 2^22 */
+    uint32_t lanes;               /* 0: 4 (lane 0 runs the large requests) */
+    uint32_t dtype_mask;          /* bit t serves ipsgpu_dtype t; 0: U32|U64|PAIR_U64 */
+    uint32_t batch_max_requests;  /* 0: 4096 */
+    uint32_t reserved;
+} ipsgpu_server_config;
+
+/* Create a server on the current device: lanes, sorters (params as for
+ * ipsgpu_sorter_create) and a scheduler thread.
+ * Errors: E_INVAL, E_NOMEM (scratch above the budget, or allocation), E_CUDA. */
+int ipsgpu_server_create(const ipsgpu_server_config *cfg, const ipsgpu_params *params,
+                         ipsgpu_server **out);
+/* Drain, stop the scheduler and free everything. */
+int ipsgpu_server_destroy(ipsgpu_server *srv);
+/* Admit a request of n elements of dtype: reserves its footprint and
+ * returns a ticket.  E_BUSY: it does not fit now (retry after releases);
+ * E_NOMEM: it never fits; E_UNSUPPORTED: dtype not served. */
+int ipsgpu_server_reserve(ipsgpu_server *srv, uint64_t n, int dtype, uint64_t *ticket);
+/* Start a reserved request on d_data (n elements, aligned as for
+ * ipsgpu_sort).  If ready_stream is not NULL the sort waits for the work
+ * enqueued on it so far (the caller may still be filling d_data there). */
+int ipsgpu_server_start(ipsgpu_server *srv, uint64_t ticket, void *d_data, void *ready_stream);
+/* reserve + start(ready_stream = NULL). */
+int ipsgpu_server_submit(ipsgpu_server *srv, void *d_data, uint64_t n, int dtype,
+                         uint64_t *ticket);
+/* done = 1 once the request's sort has finished on the GPU; status = its
+ * status code (IPSGPU_OK, or the error its run reported). */
+int ipsgpu_server_poll(ipsgpu_server *srv, uint64_t ticket, int *done, int *status);
+/* Block until the request is done; returns its status. */
+int ipsgpu_server_wait(ipsgpu_server *srv, uint64_t ticket);
+/* Host steady-clock times in microseconds: started, launched, seen done. */
+int ipsgpu_server_times(ipsgpu_server *srv, uint64_t ticket, double *t_submit_us,
+                        double *t_launch_us, double *t_done_us);
+/* The clock of ipsgpu_server_times. */
+double ipsgpu_server_now_us(void);
+/* Return a request's footprint (reserved or done; E_BUSY while it runs) and
+ * forget its ticket. */
+int ipsgpu_server_release(ipsgpu_server *srv, uint64_t ticket);
+/* Block until every started request is done. */
+int ipsgpu_server_drain(ipsgpu_server *srv);
+/* Bytes admitted now (scratch included), the budget, the scratch. */
+int ipsgpu_server_usage(ipsgpu_server *srv, uint64_t *used, uint64_t *budget, uint64_t *scratch);
 
 /* One partitioning level with given splitters, like ipsgpu_partition_level,
  * for callers that cannot allocate memory: code running while a CUDA graph is

@@ -70,7 +70,7 @@ def build(force=False, verbose=False, extra=()):
         msg = "\n".join("--- %s ---\n%s" % f for f in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
     tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
+    subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"])
     os.replace(tmp, LIB)
     with open(stamp, "w") as f:
         f.write(dig)

@@ -640,6 +640,13 @@ int ipsgpu_sorter_create(const ipsgpu_params *params, int dtype, ipsgpu_sorter *
     return IPSGPU_OK;
 }
 
+int ipsgpu_sorter_prepare(ipsgpu_sorter *h) {
+    if (!h) return IPSGPU_E_INVAL;
+    Sorter &s = h->s;
+    if (s.wave_exec) return IPSGPU_OK;
+    return build_wave_graph(s, nullptr, &s.wave_graph, &s.wave_exec);
+}
+
 int ipsgpu_sorter_destroy(ipsgpu_sorter *h) {
     if (!h) return IPSGPU_E_INVAL;
     cudaDeviceSynchronize();

@@ -31,6 +31,12 @@ class Params(ctypes.Structure):
                 ("spin_limit", ctypes.c_uint32), ("arena_bytes", ctypes.c_uint64)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("batch_max_elems", ctypes.c_uint64),
+                ("lanes", ctypes.c_uint32), ("dtype_mask", ctypes.c_uint32),
+                ("batch_max_requests", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
 _lib = None
 
 
@@ -65,6 +71,23 @@ def load():
         "ipsgpu_graph_launch": (i32, [vp, vp]),
         "ipsgpu_graph_nodes": (i32, [vp, ctypes.POINTER(u64)]),
         "ipsgpu_graph_destroy": (i32, [vp]),
+        "ipsgpu_sorter_prepare": (i32, [vp]),
+        "ipsgpu_server_create": (i32, [ctypes.POINTER(ServerConfig), ctypes.POINTER(Params),
+                                       ctypes.POINTER(vp)]),
+        "ipsgpu_server_destroy": (i32, [vp]),
+        "ipsgpu_server_reserve": (i32, [vp, u64, i32, ctypes.POINTER(u64)]),
+        "ipsgpu_server_start": (i32, [vp, u64, vp, vp]),
+        "ipsgpu_server_submit": (i32, [vp, vp, u64, i32, ctypes.POINTER(u64)]),
+        "ipsgpu_server_poll": (i32, [vp, u64, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "ipsgpu_server_wait": (i32, [vp, u64]),
+        "ipsgpu_server_times": (i32, [vp, u64, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]),
+        "ipsgpu_server_now_us": (ctypes.c_double, []),
+        "ipsgpu_server_release": (i32, [vp, u64]),
+        "ipsgpu_server_drain": (i32, [vp]),
+        "ipsgpu_server_usage": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                      ctypes.POINTER(u64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -82,7 +105,11 @@ def exported_symbols():
         "ipsgpu_strerror", "ipsgpu_set_timing", "ipsgpu_kernel_stats", "ipsgpu_kernel_name",
         "ipsgpu_debug_bounded_wait", "ipsgpu_partition_level_noalloc", "ipsgpu_sort_segmented",
         "ipsgpu_sort_batch", "ipsgpu_segmented_graph_create", "ipsgpu_graph_launch",
-        "ipsgpu_graph_nodes", "ipsgpu_graph_destroy",
+        "ipsgpu_graph_nodes", "ipsgpu_graph_destroy", "ipsgpu_sorter_prepare",
+        "ipsgpu_server_create", "ipsgpu_server_destroy", "ipsgpu_server_reserve",
+        "ipsgpu_server_start", "ipsgpu_server_submit", "ipsgpu_server_poll", "ipsgpu_server_wait",
+        "ipsgpu_server_times", "ipsgpu_server_now_us", "ipsgpu_server_release",
+        "ipsgpu_server_drain", "ipsgpu_server_usage",
     ]
 
 
@@ -143,6 +170,10 @@ class Sorter:
 
     def __exit__(self, *exc):
         self.close()
+
+    def prepare(self):
+        """Build the sorter's recursion graph now instead of on first use."""
+        _check(load().ipsgpu_sorter_prepare(self._h), "ipsgpu_sorter_prepare")
 
     def sort(self, ptr, n, stream=0):
         _check(load().ipsgpu_sort(self._h, ptr, n, stream), "ipsgpu_sort")
@@ -231,3 +262,94 @@ class SegmentedGraph:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """An ipsgpu_server: admission by HBM footprint and continuous batching
+    over CUDA streams.  Buffers stay owned by the caller."""
+
+    def __init__(self, hbm_budget_bytes, lanes=0, dtypes=("u32", "u64", "pair"),
+                 batch_max_elems=0, batch_max_requests=0, **params):
+        mask = 0
+        for d in dtypes:
+            mask |= 1 << DTYPES[d]
+        cfg = ServerConfig(hbm_budget_bytes, batch_max_elems, lanes, mask, batch_max_requests, 0)
+        p = make_params(**params)
+        h = ctypes.c_void_p()
+        _check(load().ipsgpu_server_create(ctypes.byref(cfg), ctypes.byref(p), ctypes.byref(h)),
+               "ipsgpu_server_create")
+        self._h = h
+
+    def reserve(self, n, dtype):
+        """Ticket, or None if the footprint does not fit now (E_BUSY)."""
+        t = ctypes.c_uint64()
+        rc = load().ipsgpu_server_reserve(self._h, n, DTYPES[dtype], ctypes.byref(t))
+        if rc == E_BUSY:
+            return None
+        _check(rc, "ipsgpu_server_reserve")
+        return int(t.value)
+
+    def start(self, ticket, ptr, ready_stream=0):
+        _check(load().ipsgpu_server_start(self._h, ticket, ptr, ready_stream),
+               "ipsgpu_server_start")
+
+    def submit(self, ptr, n, dtype):
+        """Ticket, or None if the footprint does not fit now (E_BUSY)."""
+        t = ctypes.c_uint64()
+        rc = load().ipsgpu_server_submit(self._h, ptr, n, DTYPES[dtype], ctypes.byref(t))
+        if rc == E_BUSY:
+            return None
+        _check(rc, "ipsgpu_server_submit")
+        return int(t.value)
+
+    def poll(self, ticket):
+        """(done, status)."""
+        d, st = ctypes.c_int(), ctypes.c_int()
+        _check(load().ipsgpu_server_poll(self._h, ticket, ctypes.byref(d), ctypes.byref(st)),
+               "ipsgpu_server_poll")
+        return bool(d.value), int(st.value)
+
+    def wait(self, ticket):
+        """Block until done; returns the request's status."""
+        return load().ipsgpu_server_wait(self._h, ticket)
+
+    def times(self, ticket):
+        """(submit, launch, done) in microseconds of now_us()'s clock."""
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(load().ipsgpu_server_times(self._h, ticket, ctypes.byref(a), ctypes.byref(b),
+                                          ctypes.byref(c)), "ipsgpu_server_times")
+        return a.value, b.value, c.value
+
+    @staticmethod
+    def now_us():
+        return load().ipsgpu_server_now_us()
+
+    def release(self, ticket):
+        _check(load().ipsgpu_server_release(self._h, ticket), "ipsgpu_server_release")
+
+    def drain(self):
+        _check(load().ipsgpu_server_drain(self._h), "ipsgpu_server_drain")
+
+    def usage(self):
+        """(used bytes incl. scratch, budget, scratch)."""
+        u, b, s = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().ipsgpu_server_usage(self._h, ctypes.byref(u), ctypes.byref(b),
+                                          ctypes.byref(s)), "ipsgpu_server_usage")
+        return int(u.value), int(b.value), int(s.value)
+
+    def close(self):
+        if self._h:
+            load().ipsgpu_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -48,3 +48,9 @@ def test_strerror_and_scratch_bytes(lib):
 def test_params_struct_layout():
     assert ctypes.sizeof(ipsgpu.Params) == 40
     assert ipsgpu.Params.arena_bytes.offset == 32
+
+
+def test_server_config_struct_layout():
+    assert ctypes.sizeof(ipsgpu.ServerConfig) == 32
+    assert ipsgpu.ServerConfig.lanes.offset == 16
+    assert ipsgpu.ServerConfig.batch_max_requests.offset == 24

@@ -227,7 +227,8 @@ def test_small_arena_forces_many_waves(timing):
         assert s.status(stream()) == ipsgpu.OK
         if timing:
             st = s.kernel_stats()
-            assert st["classify"][0] > 10 and st["plan"][0] > 10
+            # several waves, each with its own classification launch
+            assert st["classify"][0] >= 5 and st["plan"][0] >= 2 * st["classify"][0]
     _check_segments(inputs.to_numpy(d.cpu(), "u64"), inputs.to_numpy(data, "u64"),
                     offsets.numpy(), "u64")
     assert_sorted_parity(inputs.to_numpy(db.cpu(), "u64"), inputs.to_numpy(big, "u64"), "u64")

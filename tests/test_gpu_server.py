@@ -1,0 +1,112 @@
+"""GPU tests of the serving loop (ipsgpu_server_*): requests of mixed sizes,
+types and input distributions, started while others run, must each give
+exactly what the oracle (and a plain sort of the same input alone) gives;
+admission by HBM footprint; the large-request lane; times and accounting."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2009_13569_gb300 import inputs, ipsgpu
+from _util import DEV, assert_sorted_parity, stream, to_dev
+
+pytestmark = pytest.mark.gpu
+
+DISTS = ("uniform", "twodup", "zipf", "rootdup", "sorted", "reversesorted", "almostsorted")
+
+
+def _requests(count, lo, hi, seed):
+    lengths = inputs.segment_lengths(count, lo, hi, seed=seed).tolist()
+    types = ("u32", "u64", "pair")
+    return [(types[i % 3], DISTS[i % len(DISTS)], int(m), seed * 1000 + i)
+            for i, m in enumerate(lengths)]
+
+
+def _alone(dtype, host):
+    d = to_dev(host)
+    with ipsgpu.Sorter(dtype) as s:
+        s.sort(d.data_ptr(), host.shape[0], stream())
+        assert s.status(stream()) == ipsgpu.OK
+    return inputs.to_numpy(d.cpu(), dtype)
+
+
+@pytest.mark.parametrize("batch_max_elems", [0, 4096])
+def test_server_mix_matches_alone_and_oracle(batch_max_elems):
+    reqs = _requests(48, 3, 20, seed=7 + batch_max_elems)
+    side = torch.cuda.Stream(DEV)
+    with ipsgpu.Server(8 << 30, lanes=3, batch_max_elems=batch_max_elems) as srv:
+        live = []
+        for i, (dtype, dist, m, seed) in enumerate(reqs):
+            host = inputs.generate(dist, dtype, m, seed=seed)
+            t = srv.reserve(m, dtype)
+            assert t is not None
+            if i % 2:
+                # filled on a side stream; the sort waits for that stream's work
+                with torch.cuda.stream(side):
+                    d = host.to(DEV, non_blocking=False)
+                srv.start(t, d.data_ptr(), side.cuda_stream)
+            else:
+                d = to_dev(host)
+                torch.cuda.synchronize()
+                srv.start(t, d.data_ptr())
+            live.append((t, dtype, host, d))
+        for t, dtype, host, d in live:
+            assert srv.wait(t) == ipsgpu.OK
+            a, b, c = srv.times(t)
+            assert a <= b <= c
+            got = inputs.to_numpy(d.cpu(), dtype)
+            inp = inputs.to_numpy(host, dtype)
+            assert_sorted_parity(got, inp, dtype)
+            alone = _alone(dtype, host)
+            if dtype in ("u32", "u64"):
+                np.testing.assert_array_equal(got, alone)
+            else:
+                np.testing.assert_array_equal(got[:, 0], alone[:, 0])
+            srv.release(t)
+        used, budget, scratch = srv.usage()
+        assert used == scratch and budget == 8 << 30
+
+
+def test_server_admission_by_footprint():
+    with ipsgpu.Server(64 << 30, lanes=1, dtypes=("u64",)) as probe:
+        scratch = probe.usage()[2]
+    budget = scratch + (1 << 20)
+    with ipsgpu.Server(budget, lanes=1, dtypes=("u64",)) as srv:
+        t1 = srv.reserve(100_000, "u64")  # 800 KB
+        assert t1 is not None
+        assert srv.reserve(100_000, "u64") is None  # does not fit now
+        with pytest.raises(ipsgpu.IpsgpuError) as e:
+            srv.reserve(200_000, "u64")  # 1.6 MB never fits
+        assert e.value.code == ipsgpu.E_NOMEM
+        with pytest.raises(ipsgpu.IpsgpuError) as e:
+            srv.reserve(10, "u32")  # type not served
+        assert e.value.code == ipsgpu.E_UNSUPPORTED
+        host = inputs.generate("uniform", "u64", 100_000, seed=3)
+        d = to_dev(host)
+        torch.cuda.synchronize()
+        srv.start(t1, d.data_ptr())
+        assert srv.wait(t1) == ipsgpu.OK
+        assert srv.usage()[0] == scratch + 800_000
+        srv.release(t1)
+        assert srv.usage()[0] == scratch
+        t2 = srv.submit(d.data_ptr(), 100_000, "u64")  # fits again
+        assert t2 is not None
+        srv.drain()
+        assert srv.poll(t2) == (True, ipsgpu.OK)
+        srv.release(t2)
+        assert_sorted_parity(inputs.to_numpy(d.cpu(), "u64"), inputs.to_numpy(host, "u64"), "u64")
+        with pytest.raises(ipsgpu.IpsgpuError):
+            srv.release(t2)  # forgotten
+
+
+def test_server_tiny_and_empty_requests():
+    with ipsgpu.Server(4 << 30, lanes=2, dtypes=("u32",)) as srv:
+        d = torch.tensor([5], dtype=torch.int32, device=DEV)
+        t0 = srv.submit(d.data_ptr(), 0, "u32")
+        t1 = srv.submit(d.data_ptr(), 1, "u32")
+        assert srv.poll(t0) == (True, ipsgpu.OK) and srv.poll(t1) == (True, ipsgpu.OK)
+        srv.release(t0)
+        srv.release(t1)
+        bad = torch.zeros(8, dtype=torch.int32, device=DEV)
+        with pytest.raises(ipsgpu.IpsgpuError):
+            srv.submit(bad.data_ptr() + 2, 4, "u32")  # misaligned
+        assert srv.usage()[0] == srv.usage()[2]
