@@ -42,6 +42,8 @@ def _args():
     p.add_argument("--log2n", type=int, default=LOG2N)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-segmented", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
     return p.parse_args()
 
 
@@ -193,6 +195,274 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _segments_sorted(torch, d, offsets):
+    """Every adjacent pair inside a segment is ordered (as unsigned)."""
+    x = d ^ (-(1 << 63))
+    ok = x[1:] >= x[:-1]
+    inner = offsets[1:-1]
+    inner = inner[(inner > 0) & (inner < d.numel())]
+    ok[inner - 1] = True
+    return bool(ok.all().item())
+
+
+SEG_WORKLOADS = (
+    # (name, arrays, log2 of the shortest and longest length, total elements)
+    ("100k_arrays", 100_000, 4.0, 17.65, None),
+    ("loguniform_2^4_2^24", None, 4.0, 24.0, 1 << 31),
+)
+
+
+def run_segmented(torch, inputs, ipsgpu, dev, steps):
+    """Batched form: many uint64 arrays of log-uniform lengths, mixed
+    Uniform / TwoDup / AlmostSorted, sorted by one launch of a captured CUDA
+    graph, against one plain ipsgpu_sort call per array on the same GPU."""
+    out = {}
+    st = torch.cuda.Stream(dev)
+    for name, count, lo, hi, total in SEG_WORKLOADS:
+        if count is None:
+            lengths = inputs.segment_lengths(4096, lo, hi, seed=SEED)
+            c = torch.cumsum(lengths, 0)
+            lengths = lengths[:int((c <= total).sum())]
+        else:
+            lengths = inputs.segment_lengths(count, lo, hi, seed=SEED)
+        src, offsets = inputs.segmented_batch(lengths, seed=SEED, device=dev)
+        N = src.numel()
+        work = torch.empty_like(src)
+        sorter = ipsgpu.Sorter("u64")
+        g = sorter.segmented_graph(work.data_ptr(), N, offsets.data_ptr(), lengths.numel())
+        ts = []
+        for i in range(2 + steps):
+            work.copy_(src)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            g.launch(st.cuda_stream)
+            e1.record(st)
+            st.synchronize()
+            if i >= 2:
+                ts.append(e0.elapsed_time(e1))
+        ok = sorter.status(st.cuda_stream) == ipsgpu.OK and _segments_sorted(torch, work, offsets)
+        gms = sum(ts) / len(ts)
+        # one plain sort call per array (the per-array baseline), one pass
+        work.copy_(src)
+        torch.cuda.synchronize(dev)
+        o = offsets.cpu().tolist()
+        base = work.data_ptr()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for i in range(lengths.numel()):
+            a, b = o[i], o[i + 1]
+            if b - a > 1:
+                sorter.sort(base + 8 * a, b - a, st.cuda_stream)
+        e1.record(st)
+        st.synchronize()
+        pms = e0.elapsed_time(e1)
+        ok2 = sorter.status(st.cuda_stream) == ipsgpu.OK and _segments_sorted(torch, work, offsets)
+        out[name] = {"arrays": int(lengths.numel()), "elements": N,
+                     "lengths": "log-uniform [2^%g, 2^%g]" % (lo, hi),
+                     "dists": "Uniform/TwoDup/AlmostSorted by array",
+                     "graph_ms": gms, "value": N / (gms * 1e-3) / 1e9, "unit": UNIT,
+                     "plain_per_array_ms": pms, "plain_value": N / (pms * 1e-3) / 1e9,
+                     "speedup_vs_plain": pms / gms, "graph_nodes": g.nodes(),
+                     "result_sorted": ok and ok2, "steps": steps,
+                     "l2": "inputs larger than L2 (%.1f GiB)" % (N * 8 / 2 ** 30)}
+        g.close()
+        sorter.close()
+        del src, work, offsets
+        torch.cuda.empty_cache()
+    return out
+
+
+SERVE = {"requests": 600, "log2_lo": 10, "log2_hi": 30, "huge_log2": 33, "budget_gb": 96,
+         "lanes": 4, "load": 0.8}
+
+
+def run_serve(torch, inputs, ipsgpu, dev):
+    """Serving form: Poisson arrivals of sort requests (sizes log-uniform,
+    uint32 / uint64 / Pair keys, distributions of the plain-sort configs) and
+    one huge in-place uint64 request, admitted by HBM footprint under a
+    fixed budget; the server (continuous batching over streams) against the
+    same trace served first-in first-out by one plain sort at a time."""
+    import numpy as np
+    cfg = SERVE
+    R = cfg["requests"]
+    rng = np.random.default_rng(SEED & 0xFFFFFFFF)
+    sizes = inputs.segment_lengths(R, cfg["log2_lo"], cfg["log2_hi"], seed=SEED + 5).tolist()
+    types = ["u32", "u64", "pair"]
+    reqs = [{"dtype": types[i % 3], "n": int(m)} for i, m in enumerate(sizes)]
+    huge_n = 1 << cfg["huge_log2"]
+    reqs.insert(R // 2, {"dtype": "u64", "n": huge_n, "huge": True})
+    # source pools (one per type, every distribution in turn) and the huge
+    # request's own buffer; a request copies its slice of a pool into a
+    # fresh buffer when it arrives, as data arriving in HBM
+    pmax = 1 << cfg["log2_hi"]
+    pools = {}
+    for t in types:
+        shape = (pmax, 2) if t == "pair" else (pmax,)
+        pool = torch.empty(shape, dtype=torch.int32 if t == "u32" else torch.int64, device=dev)
+        dists = inputs.INT_DISTS[:8]  # all but the already-sorted ones' twins
+        step = pmax // len(dists)
+        for j, d in enumerate(dists):
+            part = pool[j * step:(j + 1) * step if j + 1 < len(dists) else pmax]
+            inputs.generate_into(part, d, t, seed=SEED + 17 * j)
+        pools[t] = pool
+    for r in reqs:
+        if not r.get("huge"):
+            r["off"] = int(rng.integers(0, pmax - r["n"] + 1))
+    huge = torch.empty(huge_n, dtype=torch.int64, device=dev)
+    elem = {"u32": 4, "u64": 8, "pair": 16}
+
+    def fill(r, buf, stream):
+        with torch.cuda.stream(stream):
+            if r.get("huge"):
+                inputs.generate_into(buf, "uniform", "u64", seed=SEED + 99)
+            else:
+                buf.copy_(pools[r["dtype"]][r["off"]:r["off"] + r["n"]])
+
+    def alloc(r):
+        if r.get("huge"):
+            return huge
+        shape = (r["n"], 2) if r["dtype"] == "pair" else (r["n"],)
+        return torch.empty(shape, dtype=torch.int32 if r["dtype"] == "u32" else torch.int64,
+                           device=dev)
+
+    def sorted_ok(buf, t, chunk=1 << 27):
+        # non-decreasing keys as unsigned, checked in chunks (bounded temporaries)
+        k = buf[:, 0] if t == "pair" else buf
+        res = torch.ones((), dtype=torch.bool, device=dev)
+        for a in range(0, max(k.shape[0] - 1, 0), chunk):
+            x = k[a:a + chunk + 1]
+            x = x.to(torch.int64) & 0xFFFFFFFF if t == "u32" else x ^ (-(1 << 63))
+            res &= (x[1:] >= x[:-1]).all()
+        return res
+
+    # phase A: first-in first-out, one plain sort at a time (service times)
+    st = torch.cuda.Stream(dev)
+    sorters = {t: ipsgpu.Sorter(t) for t in types}
+    for t in types:
+        sorters[t].prepare()
+    service, checks = [], []
+    for r in reqs:
+        buf = alloc(r)
+        if r.get("huge"):
+            fill(r, buf, st)  # regenerated outside the timed copy + sort
+            st.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        if not r.get("huge"):
+            fill(r, buf, st)
+        sorters[r["dtype"]].sort(buf.data_ptr(), r["n"], st.cuda_stream)
+        e1.record(st)
+        with torch.cuda.stream(st):
+            checks.append(sorted_ok(buf, r["dtype"]))
+        st.synchronize()
+        service.append(e0.elapsed_time(e1) * 1e3)  # us
+        del buf
+    fifo_ok = all(bool(c.item()) for c in checks) and all(
+        sorters[t].status(st.cuda_stream) == ipsgpu.OK for t in types)
+    for t in types:
+        sorters[t].close()
+    total_service = sum(service)
+    lam = cfg["load"] * len(reqs) / total_service  # arrivals per us
+    gaps = rng.exponential(1.0 / lam, size=len(reqs))
+    arrival = np.cumsum(gaps) - gaps[0]
+    fin, prev = [], 0.0
+    for a, sv in zip(arrival, service):
+        prev = max(prev, a) + sv
+        fin.append(prev)
+    fifo_lat = np.array(fin) - arrival
+    elems = sum(r["n"] for r in reqs)
+
+    # phase B: the server, live, on the same arrival times; then on all
+    # requests arriving at once (throughput at saturation)
+    def serve_live(arr):
+        fill(reqs[R // 2], huge, st)  # the huge request's data, regenerated
+        st.synchronize()
+        srv = ipsgpu.Server(cfg["budget_gb"] << 30, lanes=cfg["lanes"], dtypes=types)
+        copy_st = torch.cuda.Stream(dev)
+        t0 = srv.now_us() + 20_000.0
+        pending = collections.deque(range(len(reqs)))
+        live, lat, waits, checks_ = {}, [0.0] * len(reqs), [0.0] * len(reqs), []
+        t_last = t0
+        while pending or live:
+            now = srv.now_us()
+            progressed = False
+            for tk in list(live):
+                done, stt = srv.poll(tk)
+                if done:
+                    i, buf = live.pop(tk)
+                    _, _, td = srv.times(tk)
+                    lat[i] = td - (t0 + arr[i])
+                    t_last = max(t_last, td)
+                    with torch.cuda.stream(copy_st):
+                        checks_.append((sorted_ok(buf, reqs[i]["dtype"]), stt))
+                    srv.release(tk)
+                    progressed = True
+            # admission in arrival order; while a large request waits for
+            # memory, small ones behind it may still enter (the server keeps
+            # a slice of the budget for them), large ones keep their order
+            large_blocked = False
+            for i in list(pending):
+                if t0 + arr[i] > now:
+                    break
+                r = reqs[i]
+                small = r["n"] <= srv.batch_max_elems
+                if large_blocked and not small:
+                    continue
+                tk = srv.reserve(r["n"], r["dtype"])
+                if tk is None:
+                    if small:
+                        break
+                    large_blocked = True
+                    continue
+                waits[i] = srv.now_us() - (t0 + arr[i])
+                buf = alloc(r)
+                if not r.get("huge"):
+                    fill(r, buf, copy_st)
+                srv.start(tk, buf.data_ptr(), copy_st.cuda_stream)
+                live[tk] = (i, buf)
+                pending.remove(i)
+                progressed = True
+            if not progressed:
+                time.sleep(20e-6)
+        srv.drain()
+        torch.cuda.synchronize(dev)
+        ok_ = all(bool(c.item()) and x == ipsgpu.OK for c, x in checks_)
+        srv.close()
+        return np.array(lat), max(waits), (t_last - t0) * 1e-6, ok_
+
+    import collections
+    lat, wait_max, span, srv_ok = serve_live(arrival)
+    _, _, sat_span, sat_ok = serve_live(np.zeros(len(reqs)))
+    del pools, huge
+    fifo_span = (fin[-1] - arrival[0]) * 1e-6
+    return {"requests": len(reqs), "elements": int(elems),
+            "trace": "Poisson arrivals at %.0f%% of the plain sort's capacity; sizes log-uniform "
+                     "[2^%d, 2^%d]; u32/u64/Pair in turn; pool slices over 8 distributions; "
+                     "one 2^%d-element uint64 request (%d GiB) in place"
+                     % (100 * cfg["load"], cfg["log2_lo"], cfg["log2_hi"], cfg["huge_log2"],
+                        huge_n * 8 >> 30),
+            "budget_gb": cfg["budget_gb"], "lanes": cfg["lanes"],
+            "server": {"p50_ms": float(np.percentile(lat, 50)) * 1e-3,
+                       "p99_ms": float(np.percentile(lat, 99)) * 1e-3,
+                       "max_admission_wait_ms": wait_max * 1e-3,
+                       "value_at_load": elems / span / 1e9,
+                       "value_saturated": elems / sat_span / 1e9, "unit": UNIT,
+                       "result_sorted": srv_ok and sat_ok},
+            "plain_fifo": {"p50_ms": float(np.percentile(fifo_lat, 50)) * 1e-3,
+                           "p99_ms": float(np.percentile(fifo_lat, 99)) * 1e-3,
+                           "value_at_load": elems / fifo_span / 1e9,
+                           "value_saturated": elems / (total_service * 1e-6) / 1e9, "unit": UNIT,
+                           "result_sorted": fifo_ok},
+            "latency": "arrival to completion, copy of the request's data into its buffer "
+                       "included; plain_fifo latencies follow from the measured service time of "
+                       "each request sorted alone, one after another in arrival order",
+            "saturated": "every request available at once: elements / makespan"}
+
+
 def run_ours(args):
     import torch
     import __graft_entry__ as entry
@@ -242,6 +512,20 @@ def run_ours(args):
     clk = clocks.stop()
     sorter.set_timing(False)
     stats = sorter.kernel_stats()
+    # the same steps through the sorter's CUDA graph (the production path:
+    # all waves inside one graph launch, no per-kernel events)
+    gtimes = []
+    for _ in range(args.steps):
+        work.copy_(src)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sorter.sort(work.data_ptr(), n, stream.cuda_stream)
+        e1.record(stream)
+        barrier()
+        gtimes.append(e0.elapsed_time(e1))
+    graph_ms = sum(gtimes) / len(gtimes)
     st = sorter.status(stream.cuda_stream)
     # result check outside the timed region: non-decreasing as unsigned
     sgn = -(1 << 63)
@@ -303,6 +587,17 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline()
+    sorter.close()
+    del work, src
+    torch.cuda.empty_cache()
+    seg = None
+    if world == 1 and not args.no_segmented:
+        seg = run_segmented(torch, inputs, ipsgpu, dev, min(args.steps, 5))
+        torch.cuda.empty_cache()
+    serve = None
+    if world == 1 and not args.no_serve:
+        serve = run_serve(torch, inputs, ipsgpu, dev)
+        torch.cuda.empty_cache()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -315,9 +610,10 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (8 GiB per array)"},
                 "result_sorted": ok, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches // args.steps * args.steps, "clocks": clk,
-                "kernels": per_kernel}
+                "graph_ms_per_step": graph_ms,
+                "graph_value": world * n / (graph_ms * 1e-3) / 1e9,
+                "kernels": per_kernel, "segmented": seg, "serve": serve}
         print(json.dumps(line))
-    sorter.close()
     if pg:
         pg.destroy_process_group()
 

@@ -238,12 +238,15 @@ int ipsgpu_debug_bounded_wait(ipsgpu_sorter *s, uint32_t spin_limit, void *strea
  *     its own data, because the sort is in place; the server adds the fixed
  *     scratch of one sorter per (lane, served type), allocated at creation.
  *     A request is admitted while the admitted requests plus that scratch
- *     stay within hbm_budget_bytes.
+ *     stay within hbm_budget_bytes; the last small_reserve_bytes of it admit
+ *     small requests (at most batch_max_elems elements) only, so a large
+ *     request that waits for memory does not keep small ones out.
  *   - Batching: started requests wait in one FIFO queue.  Requests of at most
  *     batch_max_elems elements are batched (oldest first, one type per batch,
- *     at most batch_max_requests) into one ipsgpu_sort_batch run on a
- *     high-priority lane; larger ones run alone (ipsgpu_sort) on lane 0 at
- *     low priority.  A request that cannot run yet does not hold back those
+ *     at most batch_max_requests) into one ipsgpu_sort_batch run at high
+ *     stream priority, preferably on the last lane, which takes nothing
+ *     else; larger ones run alone (ipsgpu_sort) at low priority on any other
+ *     free lane.  A request that cannot run yet does not hold back those
  *     behind it.
  *   - Each request's result is exactly what ipsgpu_sort gives for it alone
  *     (for PAIR_U64 and REC100: the same keys, records with equal keys in
@@ -253,7 +256,8 @@ typedef struct ipsgpu_server ipsgpu_server;
 typedef struct {
     uint64_t hbm_budget_bytes;    /* admitted request bytes + server scratch */
     uint64_t batch_max_elems;     /* 0: 2^22 */
-    uint32_t lanes;               /* 0: 4 (lane 0 runs the large requests) */
+    uint64_t small_reserve_bytes; /* budget only small requests may use; 0: budget / 32 */
+    uint32_t lanes;               /* 0: 4 (the last one runs batches only) */
     uint32_t dtype_mask;          /* bit t serves ipsgpu_dtype t; 0: U32|U64|PAIR_U64 */
     uint32_t batch_max_requests;  /* 0: 4096 */
     uint32_t reserved;

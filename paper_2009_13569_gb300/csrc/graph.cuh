@@ -61,6 +61,7 @@ struct GState {
     uint32_t more;       // decision of the last k_g_advance
     uint64_t elems;      // elements partitioned by the current wave
     uint64_t base_elems; // elements of the current wave's base list
+    uint64_t last_elems, last_base_elems;  // the same of the wave that ended last
 };
 
 // Fixed for a sorter: its scratch and capacities.
@@ -164,6 +165,8 @@ static __global__ void k_g_job(GraphArgs g, GJob j) {
     s.more = 1;
     s.elems = 0;
     s.base_elems = 0;
+    s.last_elems = 0;
+    s.last_base_elems = 0;
     *g.state = s;
 }
 
@@ -496,6 +499,8 @@ static __global__ void k_g_advance(GraphArgs g, cudaGraphConditionalHandle h, in
     S->in_head += S->feed;
     S->take = 0;
     S->base_count = 0;
+    S->last_elems = S->elems;
+    S->last_base_elems = S->base_elems;
     S->elems = 0;
     S->base_elems = 0;
     S->counts = LevelCounts{0, 0, 0, 0};

@@ -424,9 +424,9 @@ int graph_run(Sorter &s, const GJob &job, cudaStream_t st) {
         for (size_t q = l0; q < s.launches.size(); q++) {
             TimedLaunch &l = s.launches[q];
             if (l.kind == KK_CLASSIFY || l.kind == KK_PERMUTE)
-                l.bytes = 2.0 * (double)gs.elems * s.ops->D;
+                l.bytes = 2.0 * (double)gs.last_elems * s.ops->D;
             else if (l.kind == KK_BASE)
-                l.bytes = 2.0 * (double)gs.base_elems * s.ops->D;
+                l.bytes = 2.0 * (double)gs.last_base_elems * s.ops->D;
         }
         if (!gs.more) break;
     }

@@ -78,7 +78,7 @@ struct OpsImpl {
         uint64_t chunks = (n + kDetectChunk - 1) / kDetectChunk;
         uint32_t grid = (uint32_t)(chunks < (uint64_t)s->nsm * 8 ? chunks : (uint64_t)s->nsm * 8);
         if (grid == 0) grid = 1;
-        s->tbegin(KK_DETECT, 0, st);
+        s->tbegin(KK_DETECT, (double)n * T::D, st);  // one read pass
         k_detect<T><<<grid, kDetectThreads, 0, st>>>(data, n, s->d_flags);
         s->tend(st);
         return cudaGetLastError();
@@ -89,7 +89,9 @@ struct OpsImpl {
         uint64_t g = (pairs + 255) / 256;
         uint32_t grid = (uint32_t)(g < (uint64_t)s->nsm * 16 ? g : (uint64_t)s->nsm * 16);
         if (grid == 0) return cudaSuccess;
-        s->tbegin(KK_REVERSE, 2.0 * n * T::D, st);
+        // moves 2 n D bytes only when the input was non-increasing (decided on
+        // the device), so no bytes are attributed to the launch
+        s->tbegin(KK_REVERSE, 0, st);
         k_reverse<T><<<grid, 256, 0, st>>>(data, n, s->d_flags);
         s->tend(st);
         return cudaGetLastError();

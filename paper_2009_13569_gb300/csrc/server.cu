@@ -8,18 +8,23 @@
 // scratch of one sorter per (lane, type), allocated at creation.  A request
 // is admitted while the admitted data plus that scratch stays within the
 // budget; otherwise the caller gets IPSGPU_E_BUSY and retries once earlier
-// requests are released.
+// requests are released.  A slice of the budget (small_reserve_bytes) is
+// open to small requests only (at most batch_max_elems elements), so a large
+// request waiting for memory never keeps small ones out.
 //
 // Scheduling.  Started requests wait in one FIFO queue.  A scheduler thread
-// hands them to free lanes: a request larger than batch_max_elems runs alone
-// (ipsgpu_sort) on the large-request lane; smaller ones are batched, oldest
-// first and one type per batch, into one ipsgpu_sort_batch run on a free
-// small-request lane.  Small lanes run at the highest stream priority, so
-// their blocks are scheduled ahead of a large sort's whenever SMs free up.
-// The queue is scanned past requests that cannot run yet, so a large
-// request waiting for its lane does not hold back small ones, nor the
-// reverse.  A host callback after each run wakes the scheduler, which reads
-// the run's status and marks its requests done.
+// hands them to free lanes (one run per lane at a time): a request larger
+// than batch_max_elems runs alone (ipsgpu_sort) on any free lane but the
+// last, which is kept for small requests; smaller ones are batched, oldest
+// first and one type per batch, into one ipsgpu_sort_batch run, preferably
+// on the last lane.  Each lane has a low-priority stream for large runs and
+// a high-priority one for batches, so the blocks of a batch are scheduled
+// ahead of a large sort's whenever SMs free up, and large sorts share the
+// GPU instead of queueing behind one another.  The queue is scanned past
+// requests that cannot run yet, so a large request waiting for a lane does
+// not hold back small ones, nor the reverse.  A host callback after each run
+// wakes the scheduler, which reads the run's status and marks its requests
+// done.
 //
 // Locking.  One mutex guards the queue, the request table and the lanes.
 // No CUDA call is made while it is held: a host callback takes the mutex,
@@ -78,9 +83,10 @@ struct Req {
 struct Lane {
     ipsgpu_server *srv = nullptr;
     int idx = 0;
-    bool large = false;  // runs requests above batch_max_elems
+    bool small_only = false;  // kept for batches of small requests
     bool busy = false;
-    cudaStream_t st = nullptr;
+    cudaStream_t st_lo = nullptr, st_hi = nullptr;  // large runs / batches
+    cudaStream_t st = nullptr;                      // stream of the current run
     ipsgpu_sorter *sorter[kTypes] = {};
     uint64_t *h_segs = nullptr;  // pinned (address, n) pairs of the running batch
     uint64_t *d_segs = nullptr;
@@ -135,10 +141,9 @@ bool choose(ipsgpu_server *s, Plan &plan) {
     Lane *large = nullptr, *small = nullptr;
     for (Lane *l : s->lanes) {
         if (l->busy) continue;
-        if (l->large && !large) large = l;
-        if (!l->large && !small) small = l;
+        if (!l->small_only && !large) large = l;
+        if (l->small_only || !small) small = l;  // prefer the small-only lane
     }
-    if (s->lanes.size() == 1 && !s->lanes[0]->busy) small = large = s->lanes[0];
     if (!large && !small) return false;
     const uint64_t lim = s->cfg.batch_max_elems;
     int batch_type = -1;
@@ -189,6 +194,8 @@ bool choose(ipsgpu_server *s, Plan &plan) {
     plan.lane->busy = true;
     plan.lane->dtype = plan.dtype;
     plan.lane->tickets = plan.tickets;
+    const bool alone = plan.tickets.size() == 1 && plan.ns[0] > lim;
+    plan.lane->st = alone ? plan.lane->st_lo : plan.lane->st_hi;
     return true;
 }
 
@@ -273,12 +280,14 @@ void scheduler(ipsgpu_server *s) {
 
 void destroy_lanes(ipsgpu_server *s) {
     for (Lane *l : s->lanes) {
-        if (l->st) cudaStreamSynchronize(l->st);
+        for (cudaStream_t x : {l->st_lo, l->st_hi})
+            if (x) cudaStreamSynchronize(x);
         for (int t = 0; t < kTypes; t++)
             if (l->sorter[t]) ipsgpu_sorter_destroy(l->sorter[t]);
         if (l->h_segs) cudaFreeHost(l->h_segs);
         if (l->d_segs) cudaFree(l->d_segs);
-        if (l->st) cudaStreamDestroy(l->st);
+        for (cudaStream_t x : {l->st_lo, l->st_hi})
+            if (x) cudaStreamDestroy(x);
         delete l;
     }
     s->lanes.clear();
@@ -302,7 +311,9 @@ int ipsgpu_server_create(const ipsgpu_server_config *cfg, const ipsgpu_params *p
         s->cfg.dtype_mask = (1u << IPSGPU_U32) | (1u << IPSGPU_U64) | (1u << IPSGPU_PAIR_U64);
     if (s->cfg.batch_max_elems == 0) s->cfg.batch_max_elems = 1ull << 22;
     if (s->cfg.batch_max_requests == 0) s->cfg.batch_max_requests = 4096;
-    if (s->cfg.lanes > 64 || (s->cfg.dtype_mask >> kTypes) != 0) {
+    if (s->cfg.small_reserve_bytes == 0) s->cfg.small_reserve_bytes = s->cfg.hbm_budget_bytes / 32;
+    if (s->cfg.lanes > 64 || (s->cfg.dtype_mask >> kTypes) != 0 ||
+        s->cfg.small_reserve_bytes >= s->cfg.hbm_budget_bytes) {
         delete s;
         return IPSGPU_E_INVAL;
     }
@@ -338,9 +349,10 @@ int ipsgpu_server_create(const ipsgpu_server_config *cfg, const ipsgpu_params *p
         s->lanes.push_back(l);
         l->srv = s;
         l->idx = (int)i;
-        l->large = (i == 0);
-        const int prio = (l->large && s->cfg.lanes > 1) ? least : greatest;
-        if (cudaStreamCreateWithPriority(&l->st, cudaStreamNonBlocking, prio) != cudaSuccess ||
+        l->small_only = s->cfg.lanes > 1 && i + 1 == s->cfg.lanes;
+        if (cudaStreamCreateWithPriority(&l->st_lo, cudaStreamNonBlocking, least) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&l->st_hi, cudaStreamNonBlocking, greatest) !=
+                cudaSuccess ||
             cudaMallocHost((void **)&l->h_segs, 16ull * s->cfg.batch_max_requests) != cudaSuccess ||
             cudaMalloc((void **)&l->d_segs, 16ull * s->cfg.batch_max_requests) != cudaSuccess) {
             rc = IPSGPU_E_NOMEM;
@@ -368,10 +380,13 @@ int ipsgpu_server_reserve(ipsgpu_server *s, uint64_t n, int dtype, uint64_t *tic
     if (!(s->cfg.dtype_mask >> dtype & 1u)) return IPSGPU_E_UNSUPPORTED;
     if (n > (1ull << 40)) return IPSGPU_E_INVAL;
     const uint64_t bytes = n * (uint64_t)elem_bytes(dtype);
-    if (bytes > s->cfg.hbm_budget_bytes - s->scratch) return IPSGPU_E_NOMEM;
+    const bool small = n <= s->cfg.batch_max_elems;
+    const uint64_t limit =
+        small ? s->cfg.hbm_budget_bytes : s->cfg.hbm_budget_bytes - s->cfg.small_reserve_bytes;
+    if (s->scratch + bytes > limit) return IPSGPU_E_NOMEM;
     std::lock_guard<std::mutex> g(s->mu);
     if (s->stop) return IPSGPU_E_INVAL;
-    if (s->used + bytes > s->cfg.hbm_budget_bytes) return IPSGPU_E_BUSY;
+    if (s->used + bytes > limit) return IPSGPU_E_BUSY;
     s->used += bytes;
     const uint64_t t = s->next_ticket++;
     Req &r = s->reqs[t];

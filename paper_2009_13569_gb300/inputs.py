@@ -74,6 +74,11 @@ def _draw(n, seed, stream, device):
     return splitmix64(idx, _stream(seed, stream))
 
 
+def _draw_at(idx, seed, stream):
+    """Draws of stream `stream` at the given indices (same values as _draw)."""
+    return splitmix64(idx, _stream(seed, stream))
+
+
 def _umod(x, n):
     """Unsigned (x mod 2^64) mod n for int64 bit patterns, 0 < n < 2^62."""
     if n & (n - 1) == 0:
@@ -88,18 +93,21 @@ def _zipf_cdf(nvals=1_000_000, s=0.75):
     return c / c[-1]
 
 
-def _int_values(dist, n, width, seed, device):
-    """Values of an integer distribution as int64 tensors in [0, 2^width)."""
+def _int_values(dist, n, width, seed, device, i=None):
+    """Values of an integer distribution as int64 tensors in [0, 2^width):
+    the values at global positions i (an int64 tensor; default all of
+    0..n-1) of an n-element input."""
     top = 1 << width
-    i = torch.arange(n, dtype=torch.int64, device=device)
+    if i is None:
+        i = torch.arange(n, dtype=torch.int64, device=device)
     if dist == "uniform":
-        r = _draw(n, seed, 1, device)
+        r = _draw_at(i, seed, 1)
         return r if width == 64 else _lsr(r, 64 - width)
     if dist == "exponential":
         # pick e uniform in [0, log2 n), value uniform in [2^e, 2^(e+1))
         lg = max(1, int(math.floor(math.log2(max(n, 2)))))
-        e = _umod(_draw(n, seed, 2, device), lg)
-        r = _lsr(_draw(n, seed, 3, device), 1)
+        e = _umod(_draw_at(i, seed, 2), lg)
+        r = _lsr(_draw_at(i, seed, 3), 1)
         return (torch.ones_like(e) << e) + (r & ((torch.ones_like(e) << e) - 1))
     if dist == "rootdup":
         return i % max(1, math.isqrt(n))
@@ -119,24 +127,50 @@ def _int_values(dist, n, width, seed, device):
             for q in p:  # adjacent swaps applied in sequence
                 x, y = cur.get(q, q), cur.get(q + 1, q + 1)
                 cur[q], cur[q + 1] = y, x
-            pos = torch.tensor(list(cur.keys()), dtype=torch.int64)
-            val = torch.tensor(list(cur.values()), dtype=torch.int64)
-            a[pos.to(device)] = val.to(device)
+            pos = torch.tensor(list(cur.keys()), dtype=torch.int64, device=device)
+            val = torch.tensor(list(cur.values()), dtype=torch.int64, device=device)
+            if i.numel():
+                i0, i1 = int(i[0]), int(i[-1]) + 1  # i is a contiguous range
+                keep = (pos >= i0) & (pos < i1)
+                a[pos[keep] - i0] = val[keep]
         return a
     if dist == "zipf":
         cdf = torch.from_numpy(_zipf_cdf()).to(device)
-        u = _lsr(_draw(n, seed, 5, device), 11).to(torch.float64) * 2.0 ** -53
+        u = _lsr(_draw_at(i, seed, 5), 11).to(torch.float64) * 2.0 ** -53
         v = torch.searchsorted(cdf, u, right=True) + 1
         return torch.clamp(v, max=cdf.numel())
     if dist in ("sorted", "reversesorted"):
-        # sorted uniform input, stratified: value i lies in [i*w, (i+1)*w)
+        # sorted uniform input, stratified: value j lies in [j*w, (j+1)*w)
         w = min(max(1, top // max(n, 1)), 1 << 62)
-        r = _draw(n, seed, 6, device)
-        v = i * w + _umod(r, w) if w > 1 else i
-        return v if dist == "sorted" else v.flip(0)
+        j = i if dist == "sorted" else (n - 1) - i
+        r = _draw_at(j, seed, 6)
+        return j * w + _umod(r, w) if w > 1 else j
     if dist == "zero":
-        return torch.zeros(n, dtype=torch.int64, device=device)
+        return torch.zeros_like(i)
     raise ValueError("unknown distribution %r" % dist)
+
+
+def generate_into(out, dist, dtype, seed=DEFAULT_SEED, chunk=1 << 26):
+    """Fill `out` (storage format above, any device) with the same values as
+    generate(dist, dtype, len(out), seed), chunk by chunk, so that inputs of
+    many GiB need little temporary memory.  u32, u64 and pair only."""
+    n = out.shape[0]
+    width = 32 if dtype == "u32" else 64
+    for i0 in range(0, n, chunk):
+        i1 = min(n, i0 + chunk)
+        i = torch.arange(i0, i1, dtype=torch.int64, device=out.device)
+        v = _int_values(dist, n, width, seed, out.device, i)
+        if dtype == "u64":
+            out[i0:i1] = v
+        elif dtype == "u32":
+            out[i0:i1] = (v - ((v >> 31) & 1) * (1 << 32)).to(torch.int32)
+        elif dtype == "pair":
+            out[i0:i1, 0] = v
+            out[i0:i1, 1] = i
+        else:
+            raise ValueError("generate_into: u32, u64 and pair only")
+        del i, v
+    return out
 
 
 def generate(dist, dtype, n, seed=DEFAULT_SEED, device="cpu"):
@@ -201,10 +235,6 @@ def segment_lengths(nseg, lo_log2, hi_log2, seed=DEFAULT_SEED):
     Returns an int64 CPU tensor."""
     u = _lsr(_draw(nseg, seed, 40, "cpu"), 11).to(torch.float64) * 2.0 ** -53
     return torch.floor(torch.pow(2.0, lo_log2 + u * (hi_log2 - lo_log2))).to(torch.int64)
-
-
-def _draw_at(idx, seed, stream):
-    return splitmix64(idx, _stream(seed, stream))
 
 
 def segmented_batch(lengths, dists=SEG_DISTS, seed=DEFAULT_SEED, device="cpu",

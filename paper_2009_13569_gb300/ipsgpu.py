@@ -33,6 +33,7 @@ class Params(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("batch_max_elems", ctypes.c_uint64),
+                ("small_reserve_bytes", ctypes.c_uint64),
                 ("lanes", ctypes.c_uint32), ("dtype_mask", ctypes.c_uint32),
                 ("batch_max_requests", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
@@ -269,11 +270,13 @@ class Server:
     over CUDA streams.  Buffers stay owned by the caller."""
 
     def __init__(self, hbm_budget_bytes, lanes=0, dtypes=("u32", "u64", "pair"),
-                 batch_max_elems=0, batch_max_requests=0, **params):
+                 batch_max_elems=0, batch_max_requests=0, small_reserve_bytes=0, **params):
         mask = 0
         for d in dtypes:
             mask |= 1 << DTYPES[d]
-        cfg = ServerConfig(hbm_budget_bytes, batch_max_elems, lanes, mask, batch_max_requests, 0)
+        self.batch_max_elems = batch_max_elems or (1 << 22)
+        cfg = ServerConfig(hbm_budget_bytes, batch_max_elems, small_reserve_bytes, lanes, mask,
+                           batch_max_requests, 0)
         p = make_params(**params)
         h = ctypes.c_void_p()
         _check(load().ipsgpu_server_create(ctypes.byref(cfg), ctypes.byref(p), ctypes.byref(h)),

@@ -51,6 +51,6 @@ def test_params_struct_layout():
 
 
 def test_server_config_struct_layout():
-    assert ctypes.sizeof(ipsgpu.ServerConfig) == 32
-    assert ipsgpu.ServerConfig.lanes.offset == 16
-    assert ipsgpu.ServerConfig.batch_max_requests.offset == 24
+    assert ctypes.sizeof(ipsgpu.ServerConfig) == 40
+    assert ipsgpu.ServerConfig.lanes.offset == 24
+    assert ipsgpu.ServerConfig.batch_max_requests.offset == 32

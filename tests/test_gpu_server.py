@@ -70,7 +70,9 @@ def test_server_admission_by_footprint():
     with ipsgpu.Server(64 << 30, lanes=1, dtypes=("u64",)) as probe:
         scratch = probe.usage()[2]
     budget = scratch + (1 << 20)
-    with ipsgpu.Server(budget, lanes=1, dtypes=("u64",)) as srv:
+    # batch_max_elems = 2^20: every request here is small
+    with ipsgpu.Server(budget, lanes=1, dtypes=("u64",), batch_max_elems=1 << 20,
+                       small_reserve_bytes=1 << 19) as srv:
         t1 = srv.reserve(100_000, "u64")  # 800 KB
         assert t1 is not None
         assert srv.reserve(100_000, "u64") is None  # does not fit now
@@ -110,3 +112,24 @@ def test_server_tiny_and_empty_requests():
         with pytest.raises(ipsgpu.IpsgpuError):
             srv.submit(bad.data_ptr() + 2, 4, "u32")  # misaligned
         assert srv.usage()[0] == srv.usage()[2]
+
+
+def test_server_small_reserve_keeps_small_requests_admitted():
+    with ipsgpu.Server(64 << 30, lanes=2, dtypes=("u64",)) as probe:
+        scratch = probe.usage()[2]
+    budget = scratch + (8 << 20)
+    # requests above 2^16 elements are large; the last 2 MiB admit small ones only
+    with ipsgpu.Server(budget, lanes=2, dtypes=("u64",), batch_max_elems=1 << 16,
+                       small_reserve_bytes=2 << 20) as srv:
+        big = srv.reserve(700_000, "u64")  # 5.6 MB of the 6 MB open to large requests
+        assert big is not None
+        assert srv.reserve(100_000, "u64") is None  # large: only 0.4 MB left for it
+        smalls = [srv.reserve(60_000, "u64") for _ in range(5)]  # 5 x 480 KB small
+        assert all(t is not None for t in smalls)
+        assert srv.reserve(60_000, "u64") is None  # budget exhausted
+        with pytest.raises(ipsgpu.IpsgpuError) as e:
+            srv.reserve(800_000, "u64")  # large and above budget minus the reserve
+        assert e.value.code == ipsgpu.E_NOMEM
+        for t in smalls + [big]:
+            srv.release(t)
+        assert srv.usage()[0] == scratch
