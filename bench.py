@@ -44,6 +44,9 @@ def _args():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-segmented", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--instrumented", action="store_true",
+                   help="run every sort from the host-driven wave loop (the same kernels, no "
+                        "CUDA graph): the form the ncu captures in profiles/ use")
     return p.parse_args()
 
 
@@ -488,6 +491,7 @@ def run_ours(args):
     work = torch.empty_like(src)
     stream = torch.cuda.Stream(dev)
     sorter = ipsgpu.Sorter("u64")
+    sorter.set_timing(args.instrumented)
     for _ in range(args.warmup):
         work.copy_(src)
         torch.cuda.synchronize(dev)
@@ -515,7 +519,7 @@ def run_ours(args):
     # the same steps through the sorter's CUDA graph (the production path:
     # all waves inside one graph launch, no per-kernel events)
     gtimes = []
-    for _ in range(args.steps):
+    for _ in range(0 if args.instrumented else args.steps):
         work.copy_(src)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -525,7 +529,7 @@ def run_ours(args):
         e1.record(stream)
         barrier()
         gtimes.append(e0.elapsed_time(e1))
-    graph_ms = sum(gtimes) / len(gtimes)
+    graph_ms = sum(gtimes) / len(gtimes) if gtimes else None
     st = sorter.status(stream.cuda_stream)
     # result check outside the timed region: non-decreasing as unsigned
     sgn = -(1 << 63)
@@ -611,7 +615,7 @@ def run_ours(args):
                 "result_sorted": ok, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches // args.steps * args.steps, "clocks": clk,
                 "graph_ms_per_step": graph_ms,
-                "graph_value": world * n / (graph_ms * 1e-3) / 1e9,
+                "graph_value": world * n / (graph_ms * 1e-3) / 1e9 if graph_ms else None,
                 "kernels": per_kernel, "segmented": seg, "serve": serve}
         print(json.dumps(line))
     if pg:
