@@ -16,8 +16,8 @@ namespace ipsgpu {
 
 constexpr int kDetectThreads = 256;
 constexpr int kDetectChunk = 8192;
-constexpr int kBaseThreads = 512;
-constexpr int kBaseDigitBits = 13;       // at most 8192 sub-buckets per pass
+constexpr int kBaseThreads = 1024;
+constexpr int kBaseDigitBits = 14;       // at most 16384 sub-buckets per pass
 constexpr int kBaseInsertion = 24;       // sub-buckets up to this size: ranked directly
 constexpr int kBaseStack = 2048;         // pending ranges: >= 188416 B / 4 B / 25
 
@@ -78,16 +78,38 @@ __device__ __forceinline__ Key80 shfl_key<TRec100>(Key80 k, int src) {
     return r;
 }
 
+// Bulk prefetch of [addr, addr + bytes) into L2 (both multiples of 16).
+__device__ __forceinline__ void prefetch_l2(uint64_t addr, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(addr), "r"(bytes) : "memory");
+}
+
+// Copies one U-byte unit (U = 4, 8 or 16) from shared to global memory.
+template <int U>
+__device__ __forceinline__ void store_unit(unsigned char *dst, const unsigned char *src) {
+    if (U == 16)
+        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(src);
+    else if (U == 8)
+        *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(src);
+    else
+        *reinterpret_cast<uint32_t *>(dst) = *reinterpret_cast<const uint32_t *>(src);
+}
+
 // Sorts each listed segment (segs[2i] = device byte address, segs[2i+1] = n,
-// n <= smax)
-// in place; the number of segments is *nsegs_dev if given, else nsegs_host.  The segment is first staged into shared memory with cp.async
-// (one round trip).  A pass over a range [a0, a0+len) then takes min/max and
-// a histogram of an MSD radix digit of (key - min) from shared memory, and
-// scatters the range by digit from its global copy (which equals the
-// shared one) into shared memory.  Sub-buckets of at most kBaseInsertion
-// elements are finished by insertion sort; larger ones get another pass.
-// Every pass writes its range back to global memory, so the global copy of
-// a pending range always matches the shared one.
+// n <= smax) in place; the number of segments is *nsegs_dev if given, else
+// nsegs_host.  One CTA per segment at a time; its bytes were prefetched into
+// L2 while the CTA sorted its previous segment.
+//
+// The segment is staged into shared memory through registers, taking the
+// min/max of its radix key on the way.  A pass over a range [a0, a0+len)
+// then counts an MSD radix digit of (key - min) (up to 2^kBaseDigitBits
+// digits, packed 16-bit counters), turns the counts into cursors, and
+// scatters the range by digit from its global copy (which equals the shared
+// one) into shared memory; afterwards the cursor of digit d is the end of
+// its sub-bucket.  Sub-buckets of at most kBaseInsertion elements are
+// finished by insertion sort in shared memory, one thread per sub-bucket;
+// larger ones get another pass (with their own min/max).  Every pass writes
+// its range back to global memory (coalesced), so the global copy of a
+// pending range always matches the shared one.
 template <class T>
 __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
                                                           uint32_t nsegs_host,
@@ -95,27 +117,57 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
     typedef typename T::E E;
     typedef typename T::K K;
     constexpr int ND = 1 << kBaseDigitBits;
-    constexpr int NB = 8;  // elements loaded per thread before use
+    constexpr int NB = T::D <= 8 ? 8 : (T::D <= 16 ? 4 : 1);  // elements in flight per thread
     constexpr int U = (T::D == 4 || T::D == 8 || T::D == 16) ? T::D : 4;
     constexpr int DPT = ND / kBaseThreads;  // digits per thread in the scan
     extern __shared__ __align__(16) unsigned char smem[];
-    // layout: buf | stk | off16 (ND+2 u16) | cur (ND/2 words, two u16
-    // counters each) | wtmp.  Ranges are < 2^16 elements, so 16-bit
-    // counters and offsets suffice; packing two per word keeps 8192 digits.
+    // layout: buf | stk | cur (ND/2 words, two 16-bit counters each) | wtmp.
+    // Ranges are < 2^16 elements, so 16-bit counters and cursors suffice.
+    // Digits 2w and 2w + 1 share word w.
     E *buf = reinterpret_cast<E *>(smem);
     uint32_t *stk = reinterpret_cast<uint32_t *>(smem + kBaseSmemBytes);   // (a0 << 16) | len
-    uint16_t *off = reinterpret_cast<uint16_t *>(stk + kBaseStack);        // ND + 2
-    uint32_t *cur = reinterpret_cast<uint32_t *>(off + ND + 2);            // ND / 2
+    uint32_t *cur = stk + kBaseStack;                                      // ND / 2
     uint32_t *wtmp = cur + ND / 2;                                         // 34
     __shared__ unsigned long long red[2][32];
     __shared__ uint32_t sp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = kBaseThreads / 32;
 
+    // CTA-wide min and max of per-thread values (all threads call it)
+    auto minmax = [&](unsigned long long lmin, unsigned long long lmax, uint64_t &gmn,
+                      uint64_t &gmx) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lmin = min(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+            lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        }
+        if (lane == 0) {
+            red[0][warp] = lmin;
+            red[1][warp] = lmax;
+        }
+        __syncthreads();
+        unsigned long long a = red[0][0], b = red[1][0];
+        for (int w = 1; w < NW; w++) {
+            a = min(a, red[0][w]);
+            b = max(b, red[1][w]);
+        }
+        __syncthreads();
+        gmn = a;
+        gmx = b;
+    };
+    auto word = [](uint32_t d) -> uint32_t { return d >> 1; };
+    // end of digit d's sub-bucket once the scatter has run
+    auto dend = [&](uint32_t d) -> uint32_t { return (cur[word(d)] >> (16 * (d & 1))) & 0xFFFFu; };
+
     const uint32_t nsegs = nsegs_dev ? *nsegs_dev : nsegs_host;
     for (uint32_t si = blockIdx.x; si < nsegs; si += gridDim.x) {
         const uint64_t addr = segs[2 * si], n = segs[2 * si + 1];
         E *g = reinterpret_cast<E *>(addr);
+        if (tid == 0 && si + gridDim.x < nsegs) {
+            // the CTA's next segment streams into L2 while this one is sorted
+            const uint64_t na = segs[2 * (si + gridDim.x)], nn = segs[2 * (si + gridDim.x) + 1];
+            const uint64_t lo = (na + 15) & ~15ull, hi = (na + nn * T::D) & ~15ull;
+            if (hi > lo) prefetch_l2(lo, (uint32_t)(hi - lo));
+        }
         if (n <= 1) continue;
         if (n <= 32) {
             // rank sort by one warp
@@ -137,21 +189,37 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
             __syncthreads();
             continue;
         }
+        // stage the segment into shared memory through registers, with the
+        // min / max of the high radix-key word
+        uint64_t seg_mn, seg_mx;
         {
-            // stage the segment into shared memory
-            const uint32_t units = (uint32_t)(n * T::D / U);
-            const unsigned char *src = reinterpret_cast<const unsigned char *>(g);
-            unsigned char *dst = reinterpret_cast<unsigned char *>(buf);
-            for (uint32_t u = tid; u < units; u += kBaseThreads)
-                cp_async<U>(dst + (size_t)u * U, src + (size_t)u * U);
-            cp_async_commit();
-            cp_async_wait_all();
+            unsigned long long lmin = ~0ull, lmax = 0;
+            for (uint32_t i0 = 0; i0 < n; i0 += NB * kBaseThreads) {
+                E x[NB];
+#pragma unroll
+                for (int q = 0; q < NB; q++) {
+                    const uint32_t i = i0 + q * kBaseThreads + tid;
+                    if (i < n) x[q] = g[i];
+                }
+#pragma unroll
+                for (int q = 0; q < NB; q++) {
+                    const uint32_t i = i0 + q * kBaseThreads + tid;
+                    if (i < n) {
+                        const unsigned long long v = T::rkey(x[q]);
+                        lmin = min(lmin, v);
+                        lmax = max(lmax, v);
+                        buf[i] = x[q];
+                    }
+                }
+            }
+            minmax(lmin, lmax, seg_mn, seg_mx);  // (its barrier also publishes buf)
         }
         if (tid == 0) {
             sp = 1;
             stk[0] = (uint32_t)n;
         }
         __syncthreads();
+        bool first = true;
         while (sp > 0) {
             const uint32_t top = stk[sp - 1];
             __syncthreads();
@@ -159,40 +227,35 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
             // a range is packed as (a0 << 16) | len; both are < 2^16 because
             // a segment holds at most kBaseSmemBytes / 4 < 2^16 elements
             const uint32_t a0 = top >> 16, len = top & 0xFFFFu;
-            // min / max of the radix key over the range (two key words)
-            int mode = 0;  // 0: high word, 1: low word (keys wider than 64 bits)
+            // min / max of the radix key over the range (a second key word
+            // for keys wider than 64 bits when the first one is constant)
+            int mode = 0;  // 0: high word, 1: low word
             uint64_t mn = 0, rng = 0;
             for (int pass = 0; pass < 2; pass++) {
-                unsigned long long lmin = ~0ull, lmax = 0;
-                for (uint32_t i = tid; i < len; i += kBaseThreads) {
-                    const uint64_t v = pass == 0 ? T::rkey(buf[a0 + i]) : rk_lo<T>(buf[a0 + i]);
-                    lmin = min(lmin, (unsigned long long)v);
-                    lmax = max(lmax, (unsigned long long)v);
+                uint64_t gmn, gmx;
+                if (first && pass == 0) {
+                    gmn = seg_mn;
+                    gmx = seg_mx;
+                } else {
+                    unsigned long long lmin = ~0ull, lmax = 0;
+                    for (uint32_t i = tid; i < len; i += kBaseThreads) {
+                        const uint64_t v =
+                            pass == 0 ? T::rkey(buf[a0 + i]) : rk_lo<T>(buf[a0 + i]);
+                        lmin = min(lmin, (unsigned long long)v);
+                        lmax = max(lmax, (unsigned long long)v);
+                    }
+                    minmax(lmin, lmax, gmn, gmx);
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    lmin = min(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
-                    lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-                }
-                if (lane == 0) {
-                    red[0][warp] = lmin;
-                    red[1][warp] = lmax;
-                }
-                __syncthreads();
-                unsigned long long gmin = red[0][0], gmax = red[1][0];
-                for (int w = 1; w < NW; w++) {
-                    gmin = min(gmin, red[0][w]);
-                    gmax = max(gmax, red[1][w]);
-                }
-                __syncthreads();
                 mode = pass;
-                mn = gmin;
-                rng = gmax - gmin;
+                mn = gmn;
+                rng = gmx - gmn;
                 if (rng != 0 || sizeof(typename T::K) <= 8) break;
             }
+            first = false;
             if (rng == 0) continue;  // all keys equal: the range is final
             const uint32_t nbits = 64 - __clzll((long long)rng);
             uint32_t want = 1;
-            while (want < kBaseDigitBits && ((uint64_t)2 << want) < len) want++;
+            while (want < kBaseDigitBits && (1u << want) < len) want++;
             const uint32_t dbits = min(nbits, want);
             const uint32_t shift = nbits - dbits;
             const uint32_t nd = 1u << dbits;
@@ -201,7 +264,7 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
             for (uint32_t i = tid; i < len; i += kBaseThreads) {
                 const uint64_t v = mode == 0 ? T::rkey(buf[a0 + i]) : rk_lo<T>(buf[a0 + i]);
                 const uint32_t d = (uint32_t)((v - mn) >> shift);
-                atomicAdd(&cur[d >> 1], 1u << (16 * (d & 1)));
+                atomicAdd(&cur[word(d)], 1u << (16 * (d & 1)));
             }
             __syncthreads();
             {
@@ -237,15 +300,12 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
                 for (int q = 0; q < DPT / 2; q++) {
                     const uint32_t o0 = run, o1 = run + cnt[2 * q];
                     run = o1 + cnt[2 * q + 1];
-                    off[tid * DPT + 2 * q] = (uint16_t)o0;
-                    off[tid * DPT + 2 * q + 1] = (uint16_t)o1;
                     cur[tid * (DPT / 2) + q] = o0 | (o1 << 16);
                 }
-                if (tid == kBaseThreads - 1) off[ND] = (uint16_t)len;
             }
             __syncthreads();
-            // digits >= nd are empty: their offsets equal len
-            // scatter by digit, reading the range's global copy in batches
+            // scatter by digit, reading the range's global copy in batches;
+            // each cursor ends at the end of its digit's sub-bucket
             for (uint32_t i0 = 0; i0 < len; i0 += NB * kBaseThreads) {
                 E x[NB];
 #pragma unroll
@@ -260,42 +320,46 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
                         const uint64_t v = mode == 0 ? T::rkey(x[q]) : rk_lo<T>(x[q]);
                         const uint32_t d = (uint32_t)((v - mn) >> shift);
                         const uint32_t h = 16 * (d & 1);
-                        const uint32_t p = (atomicAdd(&cur[d >> 1], 1u << h) >> h) & 0xFFFFu;
+                        const uint32_t p = (atomicAdd(&cur[word(d)], 1u << h) >> h) & 0xFFFFu;
                         buf[a0 + p] = x[q];
                     }
                 }
             }
             __syncthreads();
-            // sub-buckets larger than kBaseInsertion get another pass
+            // per sub-bucket (one thread each): a large one gets another
+            // pass; a small one is finished by insertion sort in shared
+            // memory (its elements are in arbitrary order after the scatter)
             for (uint32_t d = tid; d < nd; d += kBaseThreads) {
-                const uint32_t c = (uint32_t)off[d + 1] - off[d];
+                const uint32_t lo = d ? dend(d - 1) : 0u, c = dend(d) - lo;
                 if (c > kBaseInsertion) {
                     uint32_t q = atomicAdd(&sp, 1u);
                     if (q < kBaseStack)
-                        stk[q] = ((a0 + off[d]) << 16) | c;
+                        stk[q] = ((a0 + lo) << 16) | c;
                     else
                         set_status(status, IPSGPU_E_INTERNAL);
+                } else if (c > 1) {
+                    E *r = buf + a0 + lo;
+                    for (uint32_t i = 1; i < c; i++) {
+                        const E x = r[i];
+                        const K kx = T::key(x);
+                        uint32_t j = i;
+                        while (j > 0 && kx < T::key(r[j - 1])) {
+                            r[j] = r[j - 1];
+                            j--;
+                        }
+                        r[j] = x;
+                    }
                 }
             }
-            // every position: inside a small sub-bucket the element's final
-            // place is its rank among the sub-bucket (ties by position); in a
-            // large one it keeps its grouped place for the next pass
-            for (uint32_t p = tid; p < len; p += kBaseThreads) {
-                const E x = buf[a0 + p];
-                const uint64_t v = mode == 0 ? T::rkey(x) : rk_lo<T>(x);
-                const uint32_t d = (uint32_t)((v - mn) >> shift);
-                const uint32_t lo = off[d], c = (uint32_t)off[d + 1] - lo;
-                uint32_t dst = p;
-                if (c <= kBaseInsertion) {
-                    const K kx = T::key(x);
-                    uint32_t rank = 0;
-                    for (uint32_t q = 0; q < c; q++) {
-                        const K kq = T::key(buf[a0 + lo + q]);
-                        rank += (kq < kx || (!(kx < kq) && lo + q < p)) ? 1u : 0u;
-                    }
-                    dst = lo + rank;
-                }
-                g[a0 + dst] = x;
+            __syncthreads();
+            // the range back to global memory, coalesced: final where the
+            // sub-buckets were small, grouped by digit where they were large
+            {
+                const uint32_t units = (uint32_t)((uint64_t)len * T::D / U);
+                const unsigned char *src = reinterpret_cast<const unsigned char *>(buf + a0);
+                unsigned char *dst = reinterpret_cast<unsigned char *>(g + a0);
+                for (uint32_t u = tid; u < units; u += kBaseThreads)
+                    store_unit<U>(dst + (size_t)u * U, src + (size_t)u * U);
             }
             __syncthreads();
             if (sp > kBaseStack) {
@@ -309,7 +373,6 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
 
 inline size_t base_smem_bytes() {
     return kBaseSmemBytes + sizeof(uint32_t) * kBaseStack +
-           sizeof(uint16_t) * ((1 << kBaseDigitBits) + 2) +
            sizeof(uint32_t) * ((1 << kBaseDigitBits) / 2 + 34) + 16;
 }
 

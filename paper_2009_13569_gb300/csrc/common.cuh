@@ -11,7 +11,11 @@ namespace ipsgpu {
 
 // ---------------------------------------------------------------- limits
 constexpr int kMaxClasses = 256;      // buckets per level incl. equality ones
-constexpr int kMaxSortSample = 4096;  // sample elements sorted in one CTA
+// sample keys sorted in one CTA: 16384, at most 128 KiB of keys
+template <class K>
+constexpr uint32_t max_sort_sample() {
+    return (128u * 1024 / sizeof(K)) < 16384u ? (uint32_t)(128u * 1024 / sizeof(K)) : 16384u;
+}
 constexpr uint32_t kRBias = 1u << 30; // bias of the read pointer field
 constexpr int kBaseSmemBytes = 184 * 1024;  // element buffer of the base case
 

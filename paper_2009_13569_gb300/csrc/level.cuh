@@ -26,7 +26,10 @@
 namespace ipsgpu {
 
 constexpr int kSampleThreads = 512;
-constexpr uint32_t kMinSamplesPerBucket = 16;
+// Samples per bucket: bucket sizes spread by about 1/sqrt of it, and every
+// child above the base-case size costs another partitioning pass, so the
+// sample is larger than the paper's alpha k on the GPU.
+constexpr uint32_t kMinSamplesPerBucket = 64;
 constexpr int kPermuteThreads = 256;
 constexpr int kAuxThreads = 256;
 
@@ -90,8 +93,9 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tree(LevelArgs a) {
     typedef typename T::K K;
     typedef typename T::E E;
     extern __shared__ __align__(16) unsigned char smem[];
-    K *smp = reinterpret_cast<K *>(smem);                       // kMaxSortSample
-    K *cand = smp + kMaxSortSample;                             // kMaxClasses
+    constexpr uint32_t kMaxSample = max_sort_sample<K>();
+    K *smp = reinterpret_cast<K *>(smem);                       // kMaxSample
+    K *cand = smp + kMaxSample;                                 // kMaxClasses
     uint32_t *flag = reinterpret_cast<uint32_t *>(cand + kMaxClasses);  // kMaxClasses
     uint32_t *pos = flag + kMaxClasses;                         // kMaxClasses
     uint32_t *wtmp = pos + kMaxClasses;                         // 34
@@ -140,7 +144,7 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tree(LevelArgs a) {
             uint32_t m = (uint32_t)(alpha * (float)C);
             if (m < kMinSamplesPerBucket * C) m = kMinSamplesPerBucket * C;
             if (m < C - 1) m = C - 1;
-            if (m > kMaxSortSample) m = kMaxSortSample;
+            if (m > kMaxSample) m = kMaxSample;
             uint32_t P = 1;
             while (P < m) P <<= 1;
             const uint64_t sseed = a.seed ^ (sd.addr * 0xD1B54A32D192ED03ull) ^ (sd.n << 17);

@@ -15,7 +15,8 @@ struct OpsImpl {
     typedef typename T::K K;
     static size_t classify_smem(const Sorter *s) { return ClsSmem<T>::bytes(s->b); }
     static size_t sample_smem() {
-        return (kMaxSortSample + kMaxClasses) * sizeof(K) + sizeof(uint32_t) * (2 * kMaxClasses + 34);
+        return (max_sort_sample<K>() + kMaxClasses) * sizeof(K) +
+               sizeof(uint32_t) * (2 * kMaxClasses + 34);
     }
 
     static cudaError_t init(Sorter *s) {
