@@ -36,8 +36,8 @@ template <class T>
 struct ClsCfg {
     static constexpr bool kSmall = T::D <= 16;
     static constexpr int NT = kSmall ? 1024 : 512;
-    // elements per thread and tile: a 32-48 KiB stage for 4..16-byte elements
-    static constexpr int EPT = T::D == 4 ? 8 : (T::D == 8 ? 6 : (T::D == 16 ? 3 : 1));
+    // elements per thread and tile: a 48-64 KiB stage for 4..16-byte elements
+    static constexpr int EPT = T::D == 4 ? 12 : (T::D == 8 ? 8 : (T::D == 16 ? 4 : 1));
     static constexpr int TILE = NT * EPT;
     static constexpr int UNIT = (T::D == 4 || T::D == 8 || T::D == 16) ? T::D : 4;
 };
@@ -307,8 +307,14 @@ __global__ void __launch_bounds__(ClsCfg<T>::NT, 1) k_classify(LevelArgs a) {
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     }
     uint32_t parity = 0;
+    // a balanced wave gives this CTA the stripes of its part; otherwise the
+    // stripes are taken round-robin
+    const bool parts = a.stripe_first && a.cnt && a.cnt->balanced;
     const uint32_t nstripe = lv_nstripe(a);
-    for (uint32_t sidx = blockIdx.x; sidx < nstripe; sidx += gridDim.x) {
+    const uint32_t s_begin = parts ? a.stripe_first[blockIdx.x] : blockIdx.x;
+    const uint32_t s_end = parts ? a.stripe_first[blockIdx.x + 1] : nstripe;
+    const uint32_t s_step = parts ? 1u : gridDim.x;
+    for (uint32_t sidx = s_begin; sidx < s_end; sidx += s_step) {
     __syncthreads();
     const StripeDesc sp = a.stripe[sidx];
     const SegDesc sd = a.seg[sp.seg];

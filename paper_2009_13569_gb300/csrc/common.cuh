@@ -142,6 +142,8 @@ struct SegDesc {
     uint32_t nsplit;     // given splitters (mode 1)
     uint32_t eq_given;
     uint32_t cnt0;       // first per-class count entry of the segment's stripes
+    uint32_t part0;      // balanced waves: classification part of its first stripe
+    uint64_t gblk0;      // balanced waves: first block in the wave's block order
 };
 
 // Per-stripe plan and outputs.
@@ -197,6 +199,8 @@ struct Move {
 // with cnt == nullptr the host-provided values in LevelArgs are used.
 struct LevelCounts {
     uint32_t nseg, nstripe, ncta, ncls;
+    uint32_t balanced;  // stripes are grouped into parts, one per classify CTA
+    uint32_t pad;
 };
 
 struct LevelArgs {
@@ -217,6 +221,7 @@ struct LevelArgs {
     uint32_t nseg, nstripe, ncta, ncls;
     const LevelCounts *cnt;
     const uint32_t *cta_seg;
+    const uint32_t *stripe_first;  // balanced waves: first stripe of each part
     uint32_t spin_limit;
     uint32_t pad;
     uint64_t seed;

@@ -62,6 +62,7 @@ struct GState {
     uint64_t elems;      // elements partitioned by the current wave
     uint64_t base_elems; // elements of the current wave's base list
     uint64_t last_elems, last_base_elems;  // the same of the wave that ended last
+    uint64_t part_q, part_blocks;  // balanced waves: blocks per part, blocks taken
 };
 
 // Fixed for a sorter: its scratch and capacities.
@@ -71,6 +72,9 @@ struct GraphArgs {
     GState *state;
     GList *ring;
     uint64_t *base_list;  // (address, n) pairs for the base case
+    uint32_t *stripe_first;  // nparts + 1 entries
+    uint32_t nparts;         // classification CTAs of a wave (one per SM)
+    uint32_t pad2;
     uint32_t ring_cap, base_cap, feed_cap, seg_cap, stripe_cap, cta_cap, cls_cap, cnt_cap;
     uint32_t smax, k, b, nsm, kbits, keybits, elem_bytes, elem_align;
     uint64_t arena_bytes, sarr_bytes, keys_bytes;
@@ -153,7 +157,9 @@ static __global__ void k_g_job(GraphArgs g, GJob j) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     *g.job = j;
     GState s;
-    s.counts = LevelCounts{0, 0, 0, 0};
+    s.counts = LevelCounts{0, 0, 0, 0, 0, 0};
+    s.part_q = 1;
+    s.part_blocks = 0;
     s.in_head = 0;
     s.head = 0;
     s.tail = 0;
@@ -210,27 +216,48 @@ static __global__ void __launch_bounds__(256) k_g_feed(GraphArgs g) {
 
 // Per-segment plan quantities.
 struct GPlanItem {
-    uint32_t C, p, nc;
+    uint32_t C, p, nc, part0;
     uint64_t arena, sarr, keys, cnt, moves;
 };
 
+// Stripe layout of a wave.  Balanced: the wave's blocks, in ring order, are
+// cut into parts of Q blocks, one part per classification CTA, and a
+// segment's stripes are its pieces of the parts it meets (so every CTA
+// classifies the same number of blocks).  Otherwise (a segment too large for
+// the arena when cut that way): stripes of about stripe_elems elements,
+// classified round-robin.
+struct GLayout {
+    bool balanced;
+    uint64_t Q;             // balanced: blocks per part
+    uint64_t stripe_elems;  // otherwise
+    uint64_t bpc;           // blocks per permutation CTA
+};
+
 template <class T>
-__device__ inline GPlanItem g_item(const GraphArgs &g, uint64_t n, uint64_t stripe_elems,
-                                   uint64_t bpc) {
+__device__ inline GPlanItem g_item(const GraphArgs &g, uint64_t n, uint64_t gblk0,
+                                   const GLayout &ly) {
     GPlanItem it;
     it.C = g.algo == 1 ? (1u << g.kbits) : g_class_budget(g, n);
     const uint64_t nb = (n + g.b - 1) / g.b;
-    uint64_t p = (n + stripe_elems - 1) / stripe_elems;
-    // one segment alone always fits the arena and the counters (the sorter
-    // checks at creation that one stripe of k classes does)
     const uint64_t stage = g_stage_bytes<T>(it.C, g.b), left = g_left_bytes<T>(it.C, g.b);
-    const uint64_t pfit = g.arena_bytes > stage ? (g.arena_bytes - stage) / left : 1;
-    if (p > pfit) p = pfit;
-    if (p > g.cnt_cap / it.C) p = g.cnt_cap / it.C;
-    if (p > g.stripe_cap) p = g.stripe_cap;
-    if (p > nb) p = nb;
-    if (p < 1) p = 1;
-    uint64_t nc = (nb + bpc - 1) / bpc;
+    uint64_t p;
+    it.part0 = 0;
+    if (ly.balanced) {
+        const uint64_t f = gblk0 / ly.Q, l = (gblk0 + nb - 1) / ly.Q;
+        it.part0 = (uint32_t)f;
+        p = l - f + 1;
+    } else {
+        p = (n + ly.stripe_elems - 1) / ly.stripe_elems;
+        // one segment alone always fits the arena and the counters (the
+        // sorter checks at creation that one stripe of k classes does)
+        const uint64_t pfit = g.arena_bytes > stage ? (g.arena_bytes - stage) / left : 1;
+        if (p > pfit) p = pfit;
+        if (p > g.cnt_cap / it.C) p = g.cnt_cap / it.C;
+        if (p > g.stripe_cap) p = g.stripe_cap;
+        if (p > nb) p = nb;
+        if (p < 1) p = 1;
+    }
+    uint64_t nc = (nb + ly.bpc - 1) / ly.bpc;
     if (nc > g.cta_cap) nc = g.cta_cap;
     if (nc < 1) nc = 1;
     it.p = (uint32_t)p;
@@ -245,10 +272,10 @@ __device__ inline GPlanItem g_item(const GraphArgs &g, uint64_t n, uint64_t stri
 
 // Plans the wave: the longest prefix of the ring (at most seg_cap entries)
 // whose summed needs fit every capacity.  Stripe and CTA sizes follow the
-// host planner's rule over the elements waiting in the ring window.
+// elements waiting in the ring window; the balanced layout is tried first.
 template <class T>
 __global__ void __launch_bounds__(kPlanThreads) k_g_plan(GraphArgs g) {
-    constexpr int NV = 8;  // stripes, ctas, classes, arena, sarr, keys, counts, moves
+    constexpr int NV = 9;  // stripes, ctas, classes, arena, sarr, keys, counts, moves, blocks
     __shared__ unsigned long long red[2][32];
     __shared__ unsigned long long wsum[NV][32];
     __shared__ uint32_t sh_cut;
@@ -260,7 +287,6 @@ __global__ void __launch_bounds__(kPlanThreads) k_g_plan(GraphArgs g) {
     uint32_t nin = (uint32_t)(avail < g.seg_cap ? avail : g.seg_cap);
     if (*(volatile int *)g.lv.status != 0) nin = 0;  // an error: stop partitioning
     if (tid == 0) {
-        sh_cut = nin;
         sh_elems = 0;
         *g.lv.nmoves = 0;  // the fix-up moves of this wave start at 0
     }
@@ -286,73 +312,108 @@ __global__ void __launch_bounds__(kPlanThreads) k_g_plan(GraphArgs g) {
         te += red[0][w];
         tb += red[1][w];
     }
-    uint64_t stripe_elems = te / (2 * (uint64_t)g.nsm);
-    if (stripe_elems < kMinStripeElems) stripe_elems = kMinStripeElems;
-    stripe_elems = (stripe_elems + g.b - 1) / g.b * g.b;
-    uint64_t bpc = tb / (8 * (uint64_t)g.nsm);
-    if (bpc < 32) bpc = 32;
-    // pass 2: each thread owns a contiguous range of the window
+    GLayout ly;
+    ly.Q = tb / g.nparts + (tb % g.nparts ? 1 : 0);
+    if (ly.Q < 1) ly.Q = 1;
+    ly.stripe_elems = te / (2 * (uint64_t)g.nsm);
+    if (ly.stripe_elems < kMinStripeElems) ly.stripe_elems = kMinStripeElems;
+    ly.stripe_elems = (ly.stripe_elems + g.b - 1) / g.b * g.b;
+    ly.bpc = tb / (8 * (uint64_t)g.nsm);
+    if (ly.bpc < 32) ly.bpc = 32;
     const uint32_t per = (nin + kPlanThreads - 1) / kPlanThreads;
     const uint32_t r0 = min(nin, tid * per), r1 = min(nin, r0 + per);
-    unsigned long long loc[NV] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (uint32_t i = r0; i < r1; i++) {
-        const GPlanItem it = g_item<T>(g, g.ring[(head + i) % g.ring_cap].n, stripe_elems, bpc);
-        loc[0] += it.p;
-        loc[1] += it.nc;
-        loc[2] += it.C;
-        loc[3] += it.arena;
-        loc[4] += it.sarr;
-        loc[5] += it.keys;
-        loc[6] += it.cnt;
-        loc[7] += it.moves;
-    }
-    // exclusive scan of the sums over threads
+    const unsigned long long cap[NV] = {g.stripe_cap,  g.cta_cap,    g.cls_cap,
+                                        g.arena_bytes, g.sarr_bytes, g.keys_bytes,
+                                        g.cnt_cap,     g.lv.move_cap, ~0ull};
     unsigned long long excl[NV];
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-        unsigned long long x = loc[v];
+    uint32_t cut = 0;
+    for (int mode = 0; mode < 2; mode++) {
+        ly.balanced = mode == 0;
+        // block prefix of each thread's range (blocks do not depend on the layout)
+        unsigned long long myblk = 0;
+        for (uint32_t i = r0; i < r1; i++) myblk += (g.ring[(head + i) % g.ring_cap].n + g.b - 1) / g.b;
+        unsigned long long x = myblk;
         for (int o = 1; o < 32; o <<= 1) {
             unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        excl[v] = x - loc[v];
-        if (lane == 31) wsum[v][warp] = x;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int v = 0; v < NV; v++) {
-        unsigned long long before = 0;
-        for (int w = 0; w < warp; w++) before += wsum[v][w];
-        excl[v] += before;
-    }
-    const unsigned long long cap[NV] = {g.stripe_cap, g.cta_cap,    g.cls_cap,    g.arena_bytes,
-                                        g.sarr_bytes, g.keys_bytes, g.cnt_cap,    g.lv.move_cap};
-    // pass 3: the first entry whose running totals exceed a capacity
-    {
-        unsigned long long run[NV];
-#pragma unroll
-        for (int v = 0; v < NV; v++) run[v] = excl[v];
-        for (uint32_t i = r0; i < r1; i++) {
-            const GPlanItem it = g_item<T>(g, g.ring[(head + i) % g.ring_cap].n, stripe_elems, bpc);
-            run[0] += it.p;
-            run[1] += it.nc;
-            run[2] += it.C;
-            run[3] += it.arena;
-            run[4] += it.sarr;
-            run[5] += it.keys;
-            run[6] += it.cnt;
-            run[7] += it.moves;
-            bool over = false;
-#pragma unroll
-            for (int v = 0; v < NV; v++) over |= run[v] > cap[v];
-            if (over) {
-                atomicMin(&sh_cut, i);
-                break;
+        __syncthreads();
+        if (lane == 31) wsum[NV - 1][warp] = x;
+        __syncthreads();
+        unsigned long long gblk = x - myblk;
+        for (int w = 0; w < warp; w++) gblk += wsum[NV - 1][w];
+        // pass 2: each thread sums its contiguous range of the window
+        unsigned long long loc[NV] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        {
+            unsigned long long gb = gblk;
+            for (uint32_t i = r0; i < r1; i++) {
+                const uint64_t n = g.ring[(head + i) % g.ring_cap].n;
+                const GPlanItem it = g_item<T>(g, n, gb, ly);
+                loc[0] += it.p;
+                loc[1] += it.nc;
+                loc[2] += it.C;
+                loc[3] += it.arena;
+                loc[4] += it.sarr;
+                loc[5] += it.keys;
+                loc[6] += it.cnt;
+                loc[7] += it.moves;
+                gb += (n + g.b - 1) / g.b;
             }
         }
+        loc[8] = myblk;
+        __syncthreads();  // every warp has read the block prefix
+        // exclusive scan of the sums over threads
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            unsigned long long y = loc[v];
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long z = __shfl_up_sync(0xffffffffu, y, o);
+                if (lane >= o) y += z;
+            }
+            excl[v] = y - loc[v];
+            if (lane == 31) wsum[v][warp] = y;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            unsigned long long before = 0;
+            for (int w = 0; w < warp; w++) before += wsum[v][w];
+            excl[v] += before;
+        }
+        if (tid == 0) sh_cut = nin;
+        __syncthreads();
+        // pass 3: the first entry whose running totals exceed a capacity
+        {
+            unsigned long long run[NV];
+#pragma unroll
+            for (int v = 0; v < NV; v++) run[v] = excl[v];
+            for (uint32_t i = r0; i < r1; i++) {
+                const uint64_t n = g.ring[(head + i) % g.ring_cap].n;
+                const GPlanItem it = g_item<T>(g, n, run[8], ly);
+                run[0] += it.p;
+                run[1] += it.nc;
+                run[2] += it.C;
+                run[3] += it.arena;
+                run[4] += it.sarr;
+                run[5] += it.keys;
+                run[6] += it.cnt;
+                run[7] += it.moves;
+                run[8] += (n + g.b - 1) / g.b;
+                bool over = false;
+#pragma unroll
+                for (int v = 0; v < NV; v++) over |= run[v] > cap[v];
+                if (over) {
+                    atomicMin(&sh_cut, i);
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+        cut = sh_cut;
+        __syncthreads();
+        // a first segment that does not fit when cut into parts: per-segment stripes
+        if (cut > 0 || nin == 0) break;
     }
-    __syncthreads();
-    const uint32_t cut = sh_cut;
     // pass 4: descriptors of the taken prefix [0, cut)
     unsigned long long my_elems = 0;
     {
@@ -361,7 +422,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_g_plan(GraphArgs g) {
         for (int v = 0; v < NV; v++) run[v] = excl[v];
         for (uint32_t i = r0; i < r1 && i < cut; i++) {
             const GList e = g.ring[(head + i) % g.ring_cap];
-            const GPlanItem it = g_item<T>(g, e.n, stripe_elems, bpc);
+            const GPlanItem it = g_item<T>(g, e.n, run[8], ly);
             SegDesc d;
             d.addr = e.addr;
             d.n = e.n;
@@ -381,6 +442,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_g_plan(GraphArgs g) {
             d.radix_bits = g.kbits;
             d.nsplit = 0;
             d.eq_given = 0;
+            d.part0 = it.part0;
+            d.gblk0 = run[8];
             const_cast<SegDesc *>(g.lv.seg)[i] = d;
             my_elems += e.n;
             run[0] += it.p;
@@ -391,8 +454,12 @@ __global__ void __launch_bounds__(kPlanThreads) k_g_plan(GraphArgs g) {
             run[5] += it.keys;
             run[6] += it.cnt;
             run[7] += it.moves;
+            run[8] += (e.n + g.b - 1) / g.b;
             if (i + 1 == cut) {  // the last taken entry knows the totals
-                S->counts = LevelCounts{cut, (uint32_t)run[0], (uint32_t)run[1], (uint32_t)run[2]};
+                S->counts = LevelCounts{cut,           (uint32_t)run[0], (uint32_t)run[1],
+                                        (uint32_t)run[2], ly.balanced ? 1u : 0u, 0u};
+                S->part_q = ly.Q;
+                S->part_blocks = run[8];
             }
         }
     }
@@ -401,15 +468,17 @@ __global__ void __launch_bounds__(kPlanThreads) k_g_plan(GraphArgs g) {
     if (tid == 0) {
         S->elems = sh_elems;
         S->take = cut;
-        if (cut == 0) S->counts = LevelCounts{0, 0, 0, 0};
+        if (cut == 0) S->counts = LevelCounts{0, 0, 0, 0, 0, 0};
         if (cut == 0 && nin > 0) set_status(g.lv.status, IPSGPU_E_NOMEM);  // cannot happen
     }
 }
 
-// Stripe descriptors and the CTA -> segment map of the planned wave.
+// Stripe descriptors, the CTA -> segment map and, for a balanced wave, the
+// first stripe of every classification part.
 template <class T>
 __global__ void __launch_bounds__(256) k_g_fill_stripes(GraphArgs g) {
     const LevelCounts c = g.state->counts;
+    const uint64_t Q = g.state->part_q, tblk = g.state->part_blocks;
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
     for (uint32_t i = t0; i < c.nstripe; i += stride) {
@@ -426,12 +495,27 @@ __global__ void __launch_bounds__(256) k_g_fill_stripes(GraphArgs g) {
         const uint32_t q = i - sd.stripe0, p = sd.nstripes;
         StripeDesc s;
         s.seg = lo;
-        s.blk0 = (uint32_t)(q * nb / p);
-        s.nblk = (uint32_t)((q + 1) * nb / p - q * nb / p);
+        if (c.balanced) {
+            const uint32_t part = sd.part0 + q;
+            const uint64_t gb0 = max(sd.gblk0, (uint64_t)part * Q);
+            const uint64_t gb1 = min(sd.gblk0 + nb, ((uint64_t)part + 1) * Q);
+            s.blk0 = (uint32_t)(gb0 - sd.gblk0);
+            s.nblk = (uint32_t)(gb1 - gb0);
+            // the first stripe of its part (stripes run in block order)
+            if (gb0 == (uint64_t)part * Q || i == 0) g.stripe_first[part] = i;
+        } else {
+            s.blk0 = (uint32_t)(q * nb / p);
+            s.nblk = (uint32_t)((q + 1) * nb / p - q * nb / p);
+        }
         s.cnt_off = sd.cnt0 + q * sd.C;
         s.left_off = sd.stage_off + g_stage_bytes<T>(sd.C, sd.b) +
                      (uint64_t)q * g_left_bytes<T>(sd.C, sd.b);
         const_cast<StripeDesc *>(g.lv.stripe)[i] = s;
+    }
+    if (c.balanced) {
+        // parts past the wave's blocks are empty; the end marker
+        for (uint32_t part = t0; part <= g.nparts; part += stride)
+            if ((uint64_t)part * Q >= tblk) g.stripe_first[part] = c.nstripe;
     }
     uint32_t *cta_seg = const_cast<uint32_t *>(g.lv.cta_seg);
     for (uint32_t i = t0; i < c.ncta; i += stride) {
@@ -503,7 +587,7 @@ static __global__ void k_g_advance(GraphArgs g, cudaGraphConditionalHandle h, in
     S->last_base_elems = S->base_elems;
     S->elems = 0;
     S->base_elems = 0;
-    S->counts = LevelCounts{0, 0, 0, 0};
+    S->counts = LevelCounts{0, 0, 0, 0, 0, 0};
     S->wave += 1;
     const bool work = S->in_head < j.nseg_in || S->head < S->tail;
     const int status = *(volatile int *)g.lv.status;

@@ -144,7 +144,7 @@ void free_all(Sorter &s) {
     void *dev[] = {s.d_seg,    s.d_st,     s.d_sarr,   s.d_keys,    s.d_stripe,
                    s.d_scount, s.d_sfull,  s.d_arena,  s.d_moves,   s.d_nmoves,
                    s.d_status, s.d_cta_seg, s.d_base,    s.d_flags,
-                   s.d_waitflag, s.d_ring, s.d_gjob, s.d_gstate};
+                   s.d_waitflag, s.d_ring, s.d_gjob, s.d_gstate, s.d_stripe_first};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (s.wave_exec) cudaGraphExecDestroy(s.wave_exec);
@@ -297,6 +297,8 @@ GraphArgs graph_args(Sorter &s) {
     ga.lv.cnt = &ga.state->counts;
     ga.ring = reinterpret_cast<GList *>(s.d_ring);
     ga.base_list = s.d_base;
+    ga.stripe_first = s.d_stripe_first;
+    ga.nparts = (uint32_t)s.nsm;
     ga.ring_cap = s.ring_cap;
     ga.base_cap = s.base_cap;
     ga.feed_cap = s.base_cap - s.cls_cap;
@@ -609,6 +611,7 @@ int ipsgpu_sorter_create(const ipsgpu_params *params, int dtype, ipsgpu_sorter *
     dm((void **)&s.d_flags, 64);
     dm((void **)&s.d_waitflag, 64);
     dm((void **)&s.d_ring, L.ring);
+    dm((void **)&s.d_stripe_first, sizeof(uint32_t) * 4096);
     dm((void **)&s.d_gjob, 256);
     dm((void **)&s.d_gstate, 256);
     hm((void **)&s.h_seg, L.seg);

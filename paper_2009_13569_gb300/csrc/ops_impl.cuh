@@ -126,9 +126,10 @@ struct OpsImpl {
         s->tend(st);
         LevelArgs a = ga.lv;
         a.cnt = &ga.state->counts;
+        a.stripe_first = ga.stripe_first;
         LevelGrids g;
         g.seg = (uint32_t)s->nsm * 4;
-        g.stripe = (uint32_t)s->nsm;
+        g.stripe = ga.nparts;  // one classification part per CTA
         g.cta = (uint32_t)s->nsm * 8;
         g.cls = big;
         cudaError_t e;

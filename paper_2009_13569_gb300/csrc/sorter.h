@@ -100,6 +100,7 @@ struct Sorter {
     int *d_flags = nullptr;
     uint32_t *d_waitflag = nullptr;
     unsigned char *d_ring = nullptr;   // device planner: segments waiting (GList)
+    uint32_t *d_stripe_first = nullptr;  // device planner: first stripe of each part
     unsigned char *d_gjob = nullptr;   // GJob of the current run
     unsigned char *d_gstate = nullptr; // GState of the current run
     unsigned char *h_gstate = nullptr; // pinned: GState read back by the host-driven loop
