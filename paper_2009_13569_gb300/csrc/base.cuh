@@ -19,7 +19,9 @@ constexpr int kDetectChunk = 8192;
 constexpr int kBaseThreads = 1024;
 constexpr int kBaseDigitBits = 14;       // at most 16384 sub-buckets per pass
 constexpr int kBaseInsertion = 24;       // sub-buckets up to this size: ranked directly
-constexpr int kBaseStack = 2048;         // pending ranges: >= 188416 B / 4 B / 25
+constexpr int kBaseStack = 256;          // pending large ranges: >= 188416 B / 4 B / 513
+constexpr int kBaseSmall = 512;          // ranges up to this size are finished by one warp
+constexpr int kBaseSmallStack = 2048;    // pending small ranges: >= 188416 B / 4 B / 25
 
 
 // second-level radix key: non-zero only for keys wider than 64 bits
@@ -107,7 +109,9 @@ __device__ __forceinline__ void store_unit(unsigned char *dst, const unsigned ch
 // one) into shared memory; afterwards the cursor of digit d is the end of
 // its sub-bucket.  Sub-buckets of at most kBaseInsertion elements are
 // finished by insertion sort in shared memory, one thread per sub-bucket;
-// larger ones get another pass (with their own min/max).  Every pass writes
+// those of at most kBaseSmall elements wait for one warp each once every
+// larger range is done (many of them hold equal keys only); larger ones get
+// another pass (with their own min/max).  Every pass writes
 // its range back to global memory (coalesced), so the global copy of a
 // pending range always matches the shared one.
 template <class T>
@@ -121,15 +125,18 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
     constexpr int U = (T::D == 4 || T::D == 8 || T::D == 16) ? T::D : 4;
     constexpr int DPT = ND / kBaseThreads;  // digits per thread in the scan
     extern __shared__ __align__(16) unsigned char smem[];
-    // layout: buf | stk | cur (ND/2 words, two 16-bit counters each) | wtmp.
-    // Ranges are < 2^16 elements, so 16-bit counters and cursors suffice.
+    // layout: buf | stk | sstk | cur (ND/2 words, two 16-bit counters each)
+    // | wtmp.  Ranges are < 2^16 elements, so 16-bit counters and cursors
+    // suffice.
     // Digits 2w and 2w + 1 share word w.
     E *buf = reinterpret_cast<E *>(smem);
     uint32_t *stk = reinterpret_cast<uint32_t *>(smem + kBaseSmemBytes);   // (a0 << 16) | len
-    uint32_t *cur = stk + kBaseStack;                                      // ND / 2
+    uint32_t *sstk = stk + kBaseStack;                                     // small ranges
+    uint32_t *cur = sstk + kBaseSmallStack;                                // ND / 2
     uint32_t *wtmp = cur + ND / 2;                                         // 34
     __shared__ unsigned long long red[2][32];
-    __shared__ uint32_t sp;
+    __shared__ uint32_t sp, ssp, sh_top;
+    constexpr uint32_t kNoRange = 0xFFFFFFFFu;  // no range has a0 = len = 65535
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = kBaseThreads / 32;
 
@@ -216,14 +223,23 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
         }
         if (tid == 0) {
             sp = 1;
+            ssp = 0;
             stk[0] = (uint32_t)n;
         }
-        __syncthreads();
         bool first = true;
-        while (sp > 0) {
-            const uint32_t top = stk[sp - 1];
+        while (true) {
+            // thread 0 pops the next pending range and publishes it between
+            // two barriers, so every thread sees the same range (or the end)
+            // whichever way the previous pass ended
             __syncthreads();
-            if (tid == 0) sp--;
+            if (tid == 0) {
+                if (sp > kBaseStack) sp = kBaseStack;  // pushes past the stack were dropped
+                sh_top = sp ? stk[sp - 1] : kNoRange;
+                if (sp) sp--;
+            }
+            __syncthreads();
+            const uint32_t top = sh_top;
+            if (top == kNoRange) break;
             // a range is packed as (a0 << 16) | len; both are < 2^16 because
             // a segment holds at most kBaseSmemBytes / 4 < 2^16 elements
             const uint32_t a0 = top >> 16, len = top & 0xFFFFu;
@@ -259,7 +275,11 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
             const uint32_t dbits = min(nbits, want);
             const uint32_t shift = nbits - dbits;
             const uint32_t nd = 1u << dbits;
-            for (uint32_t w = tid; w < ND / 2; w += kBaseThreads) cur[w] = 0;
+            const uint32_t nw = (nd + 1) >> 1;  // counter words in use
+            // with shift 0 a digit is the whole key (key word): each
+            // sub-bucket holds one key, so it is final
+            const bool exact = shift == 0 && (sizeof(typename T::K) <= 8 || mode == 1);
+            for (uint32_t w = tid; w < nw; w += kBaseThreads) cur[w] = 0;
             __syncthreads();
             for (uint32_t i = tid; i < len; i += kBaseThreads) {
                 const uint64_t v = mode == 0 ? T::rkey(buf[a0 + i]) : rk_lo<T>(buf[a0 + i]);
@@ -268,13 +288,16 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
             }
             __syncthreads();
             {
-                // exclusive scan of the 16-bit counts; each thread owns DPT
-                // consecutive digits and rewrites them as cursors
+                // exclusive scan of the 16-bit counts; each thread owns a
+                // run of at most DPT consecutive digits of the nd in use and
+                // rewrites them as cursors
+                const uint32_t wpt = (nw + kBaseThreads - 1) / kBaseThreads;  // <= DPT / 2
+                const uint32_t w0 = min(nw, tid * wpt), w1 = min(nw, w0 + wpt);
                 uint32_t cnt[DPT];
                 uint32_t sum = 0;
 #pragma unroll
                 for (int q = 0; q < DPT / 2; q++) {
-                    const uint32_t w = cur[tid * (DPT / 2) + q];
+                    const uint32_t w = w0 + q < w1 ? cur[w0 + q] : 0u;
                     cnt[2 * q] = w & 0xFFFFu;
                     cnt[2 * q + 1] = w >> 16;
                     sum += cnt[2 * q] + cnt[2 * q + 1];
@@ -300,7 +323,7 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
                 for (int q = 0; q < DPT / 2; q++) {
                     const uint32_t o0 = run, o1 = run + cnt[2 * q];
                     run = o1 + cnt[2 * q + 1];
-                    cur[tid * (DPT / 2) + q] = o0 | (o1 << 16);
+                    if (w0 + q < w1) cur[w0 + q] = o0 | (o1 << 16);
                 }
             }
             __syncthreads();
@@ -329,12 +352,18 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
             // per sub-bucket (one thread each): a large one gets another
             // pass; a small one is finished by insertion sort in shared
             // memory (its elements are in arbitrary order after the scatter)
-            for (uint32_t d = tid; d < nd; d += kBaseThreads) {
+            for (uint32_t d = tid; d < nd && !exact; d += kBaseThreads) {
                 const uint32_t lo = d ? dend(d - 1) : 0u, c = dend(d) - lo;
-                if (c > kBaseInsertion) {
+                if (c > kBaseSmall) {
                     uint32_t q = atomicAdd(&sp, 1u);
                     if (q < kBaseStack)
                         stk[q] = ((a0 + lo) << 16) | c;
+                    else
+                        set_status(status, IPSGPU_E_INTERNAL);
+                } else if (c > kBaseInsertion) {
+                    uint32_t q = atomicAdd(&ssp, 1u);
+                    if (q < kBaseSmallStack)
+                        sstk[q] = ((a0 + lo) << 16) | c;
                     else
                         set_status(status, IPSGPU_E_INTERNAL);
                 } else if (c > 1) {
@@ -361,10 +390,39 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
                 for (uint32_t u = tid; u < units; u += kBaseThreads)
                     store_unit<U>(dst + (size_t)u * U, src + (size_t)u * U);
             }
-            __syncthreads();
-            if (sp > kBaseStack) {
-                if (tid == 0) sp = kBaseStack;
-                __syncthreads();
+        }
+        // the small ranges, one warp each: a range of equal keys is final;
+        // otherwise each element goes to its rank within the range (ties by
+        // position), straight to global memory.  Shared memory holds the
+        // range as the last pass grouped it, like its global copy.
+        const uint32_t nsmall = min(ssp, (uint32_t)kBaseSmallStack);
+        for (uint32_t r = warp; r < nsmall; r += NW) {
+            const uint32_t top = sstk[r];
+            const uint32_t a0 = top >> 16, c = top & 0xFFFFu;
+            unsigned long long mn0 = ~0ull, mx0 = 0, mn1 = ~0ull, mx1 = 0;
+            for (uint32_t p = lane; p < c; p += 32) {
+                const unsigned long long v0 = T::rkey(buf[a0 + p]), v1 = rk_lo<T>(buf[a0 + p]);
+                mn0 = min(mn0, v0);
+                mx0 = max(mx0, v0);
+                mn1 = min(mn1, v1);
+                mx1 = max(mx1, v1);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                mn0 = min(mn0, __shfl_xor_sync(0xffffffffu, mn0, o));
+                mx0 = max(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
+                mn1 = min(mn1, __shfl_xor_sync(0xffffffffu, mn1, o));
+                mx1 = max(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
+            }
+            if (mn0 == mx0 && mn1 == mx1) continue;  // all keys equal
+            for (uint32_t p = lane; p < c; p += 32) {
+                const E x = buf[a0 + p];
+                const K kx = T::key(x);
+                uint32_t rank = 0;
+                for (uint32_t q = 0; q < c; q++) {
+                    const K kq = T::key(buf[a0 + q]);
+                    rank += (kq < kx || (!(kx < kq) && q < p)) ? 1u : 0u;
+                }
+                g[a0 + rank] = x;
             }
         }
         __syncthreads();
@@ -372,7 +430,7 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
 }
 
 inline size_t base_smem_bytes() {
-    return kBaseSmemBytes + sizeof(uint32_t) * kBaseStack +
+    return kBaseSmemBytes + sizeof(uint32_t) * (kBaseStack + kBaseSmallStack) +
            sizeof(uint32_t) * ((1 << kBaseDigitBits) / 2 + 34) + 16;
 }
 

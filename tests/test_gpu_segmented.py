@@ -237,3 +237,34 @@ def test_small_arena_forces_many_waves(timing):
 def test_arena_too_small_rejected():
     with pytest.raises(ipsgpu.IpsgpuError):
         ipsgpu.Sorter("u64", arena_bytes=64 << 10)
+
+
+def test_segmented_constant_and_two_valued_arrays():
+    # base-case segments whose keys are all equal (the first pass finds a zero
+    # key range) or take two values, next to ordinary ones
+    lengths = [100, 5000, 23_552, 33, 17_000, 64, 20_000, 9_999]
+    parts = []
+    for i, m in enumerate(lengths):
+        if i % 3 == 0:
+            parts.append(torch.full((m,), 7 + i, dtype=torch.int64))
+        elif i % 3 == 1:
+            parts.append((torch.arange(m, dtype=torch.int64) % 2) * (1 << 40))
+        else:
+            parts.append(inputs.generate("uniform", "u64", m, seed=i))
+    host = torch.cat(parts)
+    offsets = np.zeros(len(lengths) + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(lengths)
+    got = _run("u64", host, offsets)
+    _check_segments(got, inputs.to_numpy(host, "u64"), offsets, "u64")
+
+
+@pytest.mark.parametrize("dist", ["exponential", "zipf", "eightdup"])
+def test_sort_skewed_large(dist):
+    # 2^23 keys: several partitioning waves with equality buckets, base-case
+    # segments of few distinct values
+    host = inputs.generate(dist, "u64", 1 << 23, seed=91)
+    d = to_dev(host)
+    with ipsgpu.Sorter("u64") as s:
+        s.sort(d.data_ptr(), 1 << 23, stream())
+        assert s.status(stream()) == ipsgpu.OK
+    assert_sorted_parity(inputs.to_numpy(d.cpu(), "u64"), inputs.to_numpy(host, "u64"), "u64")
