@@ -5,7 +5,8 @@
 // is read tile by tile; the next tile streams into shared memory with
 // cp.async while the current one is processed:
 //   [B] every thread classifies its elements and takes a rank inside its
-//       class with one shared-memory atomic;
+//       class with a shared-memory atomic (one per warp when all its lanes
+//       share a class);
 //   [C] per class, the buffer blocks that fill up in this tile get slots at
 //       the front of the stripe (an atomic on the stripe's block counter:
 //       the order of full blocks in a stripe is free);
@@ -132,16 +133,62 @@ __device__ __forceinline__ uint64_t rk_of_key<TRec100>(const Key80 &k) {
     return k.hi;
 }
 
-// Cell geometry of the start-node table: cell(rk) = clamp((rk - base) >>
-// shift, 0, kCells - 1); with one distinct splitter (range 0) every key maps
-// to cell 0, whose entry then is the root.
+// Cell geometry of the start-node table, over x = rk - base (0 below base).
+// Linear: cell = min(x >> shift, kCells - 1); with one distinct splitter
+// (range 0) every key maps to cell 0, whose entry then is the root.
+// Log-scale (for splitters spread over many orders of magnitude): cell =
+// 64 e + m, e the position of the leading one of x and m the 6 bits below
+// it, so every octave of x gets 64 cells; x = 0 and 1 share cell 0.
+constexpr uint32_t kLogMant = 6;
 struct CellMap {
     uint64_t base;
     uint32_t shift;
+    uint32_t logscale;
     __device__ __forceinline__ uint32_t cell(uint64_t rk) const {
         if (rk < base) return 0;
-        const uint64_t x = (rk - base) >> shift;
-        return x >= (uint64_t)kCells ? (uint32_t)kCells - 1 : (uint32_t)x;
+        const uint64_t x = rk - base;
+        if (logscale) {
+            if (x < 2) return 0;
+            const uint32_t e = 63 - __clzll((long long)x);
+            const uint32_t m = e >= kLogMant ? (uint32_t)(x >> (e - kLogMant)) & 63u
+                                             : (uint32_t)(x << (kLogMant - e)) & 63u;
+            return (e << kLogMant) | m;
+        }
+        const uint64_t y = x >> shift;
+        return y >= (uint64_t)kCells ? (uint32_t)kCells - 1 : (uint32_t)y;
+    }
+    // rk range [clo, chi] of cell c; false if no rk maps to c
+    __device__ bool range(uint32_t c, bool single, uint64_t &clo, uint64_t &chi) const {
+        if (!logscale) {
+            if (single) {
+                clo = 0;
+                chi = ~0ull;
+                return true;
+            }
+            clo = c == 0 ? 0 : base + ((uint64_t)c << shift);
+            const uint64_t top = base + (((uint64_t)c + 1) << shift) - 1;
+            chi = (c == (uint32_t)kCells - 1 || top < base) ? ~0ull : top;
+            return c == 0 || clo >= base;  // cells past 2^64 are empty
+        }
+        const uint32_t e = c >> kLogMant, m = c & 63u;
+        uint64_t lo, hi;
+        if (c == 0) {
+            lo = 0;
+            hi = 1;
+        } else if (e == 0) {
+            return false;
+        } else if (e < kLogMant) {
+            if (m & ((1u << (kLogMant - e)) - 1)) return false;
+            lo = hi = (1ull << e) + (m >> (kLogMant - e));
+        } else {
+            lo = (64ull + m) << (e - kLogMant);
+            hi = lo + (1ull << (e - kLogMant)) - 1;
+        }
+        const uint64_t room = ~0ull - base;  // largest x
+        if (lo > room) return false;
+        clo = c == 0 ? 0 : base + lo;
+        chi = base + (hi < room ? hi : room);
+        return true;
     }
 };
 
@@ -168,46 +215,65 @@ __device__ __forceinline__ uint32_t count_less(const typename T::K *spl, uint32_
 //   cnt <= kMaxCellCmp:  ja | cnt << 9            (i = ja + compares)
 //   otherwise:           1 << 31 | depth << 9 | node  (the deepest tree node
 //                        every key of the cell reaches; the walk goes on)
+// The map (linear or log-scale) is the one that leaves fewer splitter
+// intervals in cells that need the walk (judged at each interval's
+// midpoint; every interval holds about the same share of the keys).  All
+// threads of the CTA call it.
 constexpr uint32_t kMaxCellCmp = 3;
+template <class T>
+__device__ uint32_t cell_entry(const CellMap &cm, uint32_t c, bool single,
+                               const typename T::K *tree, const typename T::K *spl,
+                               uint32_t nleaves, uint32_t logK) {
+    typedef typename T::K K;
+    uint64_t clo, chi;
+    if (!cm.range(c, single, clo, chi)) return 0x80000000u | 1u;  // unused: walk from the root
+    const K klo = key_lo_of<T>(clo), khi = key_hi_of<T>(chi);
+    const uint32_t ja = count_less<T>(spl, nleaves, klo);
+    const uint32_t jc = count_less<T>(spl, nleaves, khi);
+    if (jc - ja <= kMaxCellCmp) return ja | ((jc - ja) << 9);
+    uint32_t i = 1, l = 0;
+    for (; l < logK; l++) {
+        const K a = tree[i];
+        if (a < klo)
+            i = 2 * i + 1;  // every key of the cell is larger: right
+        else if (!(a < khi))
+            i = 2 * i;      // no key of the cell is larger: left
+        else
+            break;
+    }
+    return 0x80000000u | (l << 9) | i;
+}
+
 template <class T>
 __device__ void build_start_table(uint32_t *tab, CellMap &cm, const typename T::K *tree,
                                   const typename T::K *spl, uint32_t nleaves, uint32_t logK) {
-    typedef typename T::K K;
     const uint64_t lo = rk_of_key<T>(spl[0]);
     const uint64_t hi = rk_of_key<T>(spl[nleaves - 1]);
     const uint64_t range = hi - lo;
     const uint32_t nbits = range ? 64 - __clzll((long long)range) : 0;
-    cm.base = lo;
-    cm.shift = nbits > (uint32_t)kCellBits ? nbits - kCellBits : 0;
-    for (uint32_t c = threadIdx.x; c < (uint32_t)kCells; c += blockDim.x) {
-        uint64_t clo, chi;
-        if (range == 0) {
-            clo = 0;
-            chi = ~0ull;
-        } else {
-            clo = c == 0 ? 0 : lo + ((uint64_t)c << cm.shift);
-            const uint64_t top = lo + (((uint64_t)c + 1) << cm.shift) - 1;
-            chi = (c == (uint32_t)kCells - 1 || top < lo) ? ~0ull : top;
+    const bool single = range == 0;
+    CellMap lin, lg;
+    lin.base = lg.base = lo;
+    lin.shift = nbits > (uint32_t)kCellBits ? nbits - kCellBits : 0;
+    lg.shift = 0;
+    lin.logscale = 0;
+    lg.logscale = 1;
+    // which map leaves fewer splitter intervals to the walk
+    bool walk_lin = false, walk_lg = false;
+    const uint32_t j = threadIdx.x;
+    if (!single && j + 1 < nleaves) {
+        const uint64_t a = rk_of_key<T>(spl[j]), b = rk_of_key<T>(spl[j + 1]);
+        if (b > a) {
+            const uint64_t mid = a + (b - a) / 2;
+            walk_lin = cell_entry<T>(lin, lin.cell(mid), false, tree, spl, nleaves, logK) >> 31;
+            walk_lg = cell_entry<T>(lg, lg.cell(mid), false, tree, spl, nleaves, logK) >> 31;
         }
-        const K klo = key_lo_of<T>(clo), khi = key_hi_of<T>(chi);
-        const uint32_t ja = count_less<T>(spl, nleaves, klo);
-        const uint32_t jc = count_less<T>(spl, nleaves, khi);
-        if (jc - ja <= kMaxCellCmp) {
-            tab[c] = ja | ((jc - ja) << 9);
-            continue;
-        }
-        uint32_t i = 1, l = 0;
-        for (; l < logK; l++) {
-            const K a = tree[i];
-            if (a < klo)
-                i = 2 * i + 1;  // every key of the cell is larger: right
-            else if (!(a < khi))
-                i = 2 * i;      // no key of the cell is larger: left
-            else
-                break;
-        }
-        tab[c] = 0x80000000u | (l << 9) | i;
     }
+    const int n_lin = __syncthreads_count(walk_lin);
+    const int n_lg = __syncthreads_count(walk_lg);
+    cm = (!single && n_lg < n_lin) ? lg : lin;
+    for (uint32_t c = threadIdx.x; c < (uint32_t)kCells; c += blockDim.x)
+        tab[c] = cell_entry<T>(cm, c, single, tree, spl, nleaves, logK);
 }
 
 // Classify EPT keys: the table gives the class index directly or after at
@@ -384,13 +450,21 @@ __global__ void __launch_bounds__(ClsCfg<T>::NT, 1) k_classify(LevelArgs a) {
         } else {
             classify_tab<T, EPT>(k, c, v, tab, sh_cm, s_tree, s_spl, cl.logK, cl.eq);
         }
+        // ranks: one shared-memory atomic per element, or one per warp when
+        // all its lanes hold the same class (runs of presorted input)
 #pragma unroll
         for (int e = 0; e < EPT; e++) {
+            const bool ok = (valid >> e) & 1u;
+            if (!ok) c[e] = 0xFFFFFFFFu;
+            const uint32_t c0 = __shfl_sync(0xffffffffu, c[e], 0);
             r[e] = 0;
-            if ((valid >> e) & 1u)
+            if (__all_sync(0xffffffffu, c[e] == c0) && c0 != 0xFFFFFFFFu) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(&cnt[c0], 32u);
+                r[e] = __shfl_sync(0xffffffffu, base, 0) + (uint32_t)lane;
+            } else if (ok) {
                 r[e] = atomicAdd(&cnt[c[e]], 1u);
-            else
-                c[e] = 0xFFFFFFFFu;
+            }
         }
         __syncthreads();
         // the stage buffer is free: stream in the next tile
