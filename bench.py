@@ -268,13 +268,36 @@ def run_segmented(torch, inputs, ipsgpu, dev, steps):
         st.synchronize()
         pms = e0.elapsed_time(e1)
         ok2 = sorter.status(st.cuda_stream) == ipsgpu.OK and _segments_sorted(torch, work, offsets)
+        # the autotuner's pick (k, block bytes, base case, alpha) for this batch
+        from paper_2009_13569_gb300 import autotune
+        best, table = autotune.tune_segmented(torch, src, offsets, "u64", reps=2)
+        ts_t = []
+        with ipsgpu.Sorter("u64", **best) as s2:
+            g2 = s2.segmented_graph(work.data_ptr(), N, offsets.data_ptr(), lengths.numel())
+            for i in range(2 + steps):
+                work.copy_(src)
+                torch.cuda.synchronize(dev)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                g2.launch(st.cuda_stream)
+                e1.record(st)
+                st.synchronize()
+                if i >= 2:
+                    ts_t.append(e0.elapsed_time(e1))
+            ok3 = s2.status(st.cuda_stream) == ipsgpu.OK and _segments_sorted(torch, work, offsets)
+            g2.close()
+        tms = sum(ts_t) / len(ts_t)
         out[name] = {"arrays": int(lengths.numel()), "elements": N,
                      "lengths": "log-uniform [2^%g, 2^%g]" % (lo, hi),
                      "dists": "Uniform/TwoDup/AlmostSorted by array",
                      "graph_ms": gms, "value": N / (gms * 1e-3) / 1e9, "unit": UNIT,
                      "plain_per_array_ms": pms, "plain_value": N / (pms * 1e-3) / 1e9,
                      "speedup_vs_plain": pms / gms, "graph_nodes": g.nodes(),
-                     "result_sorted": ok and ok2, "steps": steps,
+                     "autotuned": {"params": best, "graph_ms": tms,
+                                   "value": N / (tms * 1e-3) / 1e9,
+                                   "candidates": [[p, t] for p, t in table]},
+                     "result_sorted": ok and ok2 and ok3, "steps": steps,
                      "l2": "inputs larger than L2 (%.1f GiB)" % (N * 8 / 2 ** 30)}
         g.close()
         sorter.close()

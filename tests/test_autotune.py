@@ -1,0 +1,36 @@
+"""The autotuner's search (coordinate descent over (k, block bytes), the
+base-case size and alpha), on the CPU with a synthetic cost function."""
+from paper_2009_13569_gb300 import autotune
+
+
+def test_search_finds_the_separable_minimum():
+    # cost = f(kb) + g(base) + h(alpha): coordinate descent reaches the optimum
+    def cost(p):
+        kb = {(256, 512): 3.0, (128, 1024): 1.0, (64, 2048): 2.0}[(p["k"], p["block_bytes"])]
+        base = abs(p["base_case"] - autotune.base_cap("u64") // 2) / 1000.0
+        alpha = {0.2: 0.3, 0.5: 0.1, 1.0: 0.2}[p["alpha_scale"]]
+        return kb + base + alpha
+
+    best, table = autotune.search(cost, "u64")
+    assert (best["k"], best["block_bytes"]) == (128, 1024)
+    assert best["base_case"] == autotune.base_cap("u64") // 2
+    assert best["alpha_scale"] == 0.5
+    # every candidate timed once, the starting point not twice
+    keys = [tuple(sorted(p.items())) for p, _ in table]
+    assert len(keys) == len(set(keys)) == 3 + 2 + 2
+
+
+def test_search_skips_rejected_candidates():
+    def cost(p):
+        if p["k"] == 256:
+            return None  # e.g. refused by the library
+        return 1.0 if p["k"] == 64 else 2.0
+
+    best, table = autotune.search(cost, "u32")
+    assert best["k"] == 64
+    assert any(t is None for _, t in table)
+
+
+def test_base_cap_matches_the_library_limit():
+    assert autotune.base_cap("u64") == 184 * 1024 // 8
+    assert autotune.base_cap("rec100") == 184 * 1024 // 100
