@@ -305,7 +305,7 @@ int ipsgpu_server_usage(ipsgpu_server *srv, uint64_t *used, uint64_t *budget, ui
  * service that reserves all device memory up front.  The paper has no
  * counterpart; this is a property of the library, not of the method.
  *   - No sorter is needed and nothing is allocated: all scratch lives in a
- *     fixed device array inside the library (about 8.3 MiB, held by every GPU
+ *     fixed device array inside the library (about 8.2 MiB, held by every GPU
  *     that loads the library until the process exits).  The caller passes the
  *     data, the splitters and d_bucket_begin exactly as for
  *     ipsgpu_partition_level; dtype is an ipsgpu_dtype.

@@ -11,7 +11,7 @@
 //
 // The array holds one segment's state, at most kNaStripes stripes with their
 // leftover buffer blocks, and the fix-up and permutation bookkeeping:
-// kNaScratchBytes in total (about 8.3 MiB), present on every GPU that loads
+// kNaScratchBytes in total (about 8.2 MiB), present on every GPU that loads
 // the library until the process exits.  Its device address is obtained once
 // per device with cudaGetSymbolAddress on the first call made with that
 // device current (a host-side name of a __device__ array is not a device
