@@ -49,6 +49,7 @@ def _args():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-segmented", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-radix", action="store_true")
     p.add_argument("--instrumented", action="store_true",
                    help="run every sort from the host-driven wave loop (the same kernels, no "
                         "CUDA graph): the form the ncu captures in profiles/ use")
@@ -494,6 +495,24 @@ def run_serve(torch, inputs, ipsgpu, dev):
             "saturated": "every request available at once: elements / makespan"}
 
 
+PARTITION_KERNELS = ("sample_tree", "classify", "prep", "fixup", "permute", "stage", "fill", "plan")
+
+
+def level_roofline(stats, peak, D, n):
+    """The distribution levels as a whole: their algorithmic bytes (each
+    element read and written by classification and by the permutation,
+    4 D per element and level) over the time of every kernel of the
+    partitioning waves."""
+    by = stats.get("classify", (0, 0.0, 0.0))[2] + stats.get("permute", (0, 0.0, 0.0))[2]
+    ms = sum(stats.get(k, (0, 0.0, 0.0))[1] for k in PARTITION_KERNELS)
+    if not by or not ms:
+        return None
+    ach = by / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "levels": by / (4.0 * D * n), "ms": ms, "bytes": by,
+            "kernels": list(PARTITION_KERNELS)}
+
+
 def run_ours(args):
     import torch
     import __graft_entry__ as entry
@@ -589,6 +608,37 @@ def run_ours(args):
     per_kernel = {k: {"launches": v[0] // args.steps, "ms": v[1] / args.steps,
                       "GBps": (v[2] / v[1] / 1e6) if v[1] and v[2] else None}
                   for k, v in stats.items() if v[0]}
+    levels = level_roofline(stats, peak, 8, n * args.steps)
+
+    # the radix variant (IPS2Ra) on the same input, both timed forms
+    ips2ra = None
+    if not args.no_radix:
+        rs = ipsgpu.Sorter("u64", algo=ipsgpu.RADIX)
+        for mode in (False, True):
+            rs.set_timing(mode)
+            for _ in range(args.warmup):
+                work.copy_(src)
+                torch.cuda.synchronize(dev)
+                rs.sort(work.data_ptr(), n, stream.cuda_stream)
+                stream.synchronize()
+        rs.set_timing(False)
+        rs.kernel_stats()
+        sorter_saved = sorter
+        sorter = rs
+        rtimes = timed_steps(args.steps)
+        rs.set_timing(True)
+        ritimes = timed_steps(args.steps)
+        rs.set_timing(False)
+        sorter = sorter_saved
+        rstats = rs.kernel_stats()
+        rok = rs.status(stream.cuda_stream) == ipsgpu.OK and bool(
+            ((work[1:] ^ sgn) >= (work[:-1] ^ sgn)).all().item())
+        rms = sum(rtimes) / len(rtimes)
+        ips2ra = {"value": world * n / (rms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": rms,
+                  "instrumented_ms_per_step": sum(ritimes) / len(ritimes),
+                  "level_roofline": level_roofline(rstats, peak, 8, n * args.steps),
+                  "result_sorted": rok}
+        rs.close()
 
     e2e = None
     if not args.no_e2e:
@@ -647,6 +697,7 @@ def run_ours(args):
                 "gpu_launches": launches // args.steps * args.steps, "clocks": clk,
                 "timed_form": "CUDA graph" if graph_ms else "host-driven waves, kernel events",
                 "instrumented_ms_per_step": inst_ms,
+                "level_roofline": levels, "ips2ra": ips2ra,
                 "kernels": per_kernel, "segmented": seg, "serve": serve}
         print(json.dumps(line))
     if pg:

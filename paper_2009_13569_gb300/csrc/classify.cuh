@@ -154,6 +154,10 @@ struct CellMap {
                                              : (uint32_t)(x << (kLogMant - e)) & 63u;
             return (e << kLogMant) | m;
         }
+        if (shift >= 32) {  // the cell is in the high word
+            const uint32_t y = (uint32_t)(x >> 32) >> (shift - 32);
+            return y >= (uint32_t)kCells ? (uint32_t)kCells - 1 : y;
+        }
         const uint64_t y = x >> shift;
         return y >= (uint64_t)kCells ? (uint32_t)kCells - 1 : (uint32_t)y;
     }
@@ -321,9 +325,13 @@ __device__ __forceinline__ void classify_tab(const typename T::K (&k)[EPT], uint
         for (int e = 0; e < EPT; e++)
             if (l[e] != 0xFFu) i[e] -= 1u << logK;
     }
+    if (eq) {
 #pragma unroll
-    for (int e = 0; e < EPT; e++)
-        c[e] = eq ? 2 * i[e] + 1 - (k[e] < spl[i[e]] ? 1u : 0u) : i[e];
+        for (int e = 0; e < EPT; e++) c[e] = 2 * i[e] + 1 - (k[e] < spl[i[e]] ? 1u : 0u);
+    } else {
+#pragma unroll
+        for (int e = 0; e < EPT; e++) c[e] = i[e];
+    }
 }
 
 template <class T>
