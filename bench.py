@@ -50,6 +50,11 @@ def _args():
     p.add_argument("--no-segmented", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-radix", action="store_true")
+    p.add_argument("--sweep", action="store_true",
+                   help="instead of the headline line: one JSON line per run of the plain-sort "
+                        "configurations (u32/u64 x 10 distributions x IPS4o/IPS2Ra at 2^30; "
+                        "f64, Pair and 100-byte records at 2^28), with per-level rooflines and "
+                        "full-size property checks")
     p.add_argument("--instrumented", action="store_true",
                    help="run every sort from the host-driven wave loop (the same kernels, no "
                         "CUDA graph): the form the ncu captures in profiles/ use")
@@ -512,6 +517,139 @@ def level_roofline(stats, peak, D, n):
             "kernels": list(PARTITION_KERNELS)}
 
 
+def _multiset_sig(torch, t):
+    """Order-independent signature of a tensor's elements (count, sum, xor
+    and sum of squares of its words, each mod 2^64; 32-bit words for u32
+    and 100-byte records, 64-bit words otherwise)."""
+    if t.dtype == torch.uint8:
+        w = t.contiguous().view(torch.int32).reshape(-1).to(torch.int64)
+    elif t.element_size() == 4:
+        w = t.reshape(-1).view(torch.int32).to(torch.int64)
+    else:
+        w = t.reshape(-1).view(torch.int64)
+    acc = [w.numel(), 0, 0, 0]
+    for a in range(0, w.numel(), 1 << 27):
+        x = w[a:a + (1 << 27)]
+        acc[1] = (acc[1] + int(x.sum().item())) & ((1 << 64) - 1)
+        acc[2] ^= int(_xor_reduce(torch, x))
+        acc[3] = (acc[3] + int((x * x).sum().item())) & ((1 << 64) - 1)
+    return tuple(acc)
+
+
+def _xor_reduce(torch, x):
+    while x.numel() > 1:
+        if x.numel() % 2:
+            x = torch.cat([x, torch.zeros(1, dtype=x.dtype, device=x.device)])
+        x = x[0::2] ^ x[1::2]
+    return x[0].item() & ((1 << 64) - 1)
+
+
+def _keys_sorted(torch, t, dtype, chunk=1 << 27):
+    """Non-decreasing keys (as unsigned; f64 by its order map), chunked."""
+    n = t.shape[0]
+    ok = True
+    for a in range(0, max(n - 1, 0), chunk):
+        x = t[a:a + chunk + 1]
+        if dtype == "u32":
+            k = x.to(torch.int64) & 0xFFFFFFFF
+            ok &= bool((k[1:] >= k[:-1]).all().item())
+        elif dtype in ("u64", "pair"):
+            k = (x[:, 0] if dtype == "pair" else x) ^ (-(1 << 63))
+            ok &= bool((k[1:] >= k[:-1]).all().item())
+        elif dtype == "f64":
+            b = x.view(torch.int64)
+            k = torch.where(b < 0, ~b, b | (-(1 << 63))) ^ (-(1 << 63))
+            ok &= bool((k[1:] >= k[:-1]).all().item())
+        else:  # rec100: 10-byte big-endian unsigned keys, compared bytewise
+            kb = x[:, :10].to(torch.int64)
+            hi = torch.zeros(kb.shape[0], dtype=torch.int64, device=x.device)
+            for j in range(7):
+                hi = hi * 256 + kb[:, j]
+            lo = kb[:, 7] * 65536 + kb[:, 8] * 256 + kb[:, 9]
+            d_hi = hi[1:] - hi[:-1]
+            ok &= bool(((d_hi > 0) | ((d_hi == 0) & (lo[1:] >= lo[:-1]))).all().item())
+    return ok
+
+
+SWEEP_INT_DISTS = ("uniform", "exponential", "rootdup", "twodup", "eightdup", "almostsorted",
+                   "zipf", "sorted", "reversesorted", "zero")
+
+
+def run_sweep(args):
+    """Plain-sort configurations: every distribution for u32/u64 with both
+    algorithms at 2^30, and f64 / Pair / 100-byte records at 2^28 with
+    IPS4o; one JSON line each.  Every run is checked at full size by
+    properties: keys non-decreasing and the multiset of words unchanged."""
+    import torch
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2009_13569_gb300 import inputs, ipsgpu
+    dev = torch.device("cuda", 0)
+    peak, _ = _peak_hbm()
+    stream = torch.cuda.Stream(dev)
+    runs = []
+    for dtype in ("u64", "u32"):
+        for dist in SWEEP_INT_DISTS:
+            for algo in (ipsgpu.SAMPLESORT, ipsgpu.RADIX):
+                runs.append((dtype, dist, algo, 30))
+    for dtype, dists in (("f64", inputs.F64_DISTS), ("pair", ("uniform",)),
+                         ("rec100", inputs.REC_DISTS)):
+        for dist in dists:
+            runs.append((dtype, dist, ipsgpu.SAMPLESORT, 28))
+    cur = None
+    for dtype, dist, algo, lg in runs:
+        n = 1 << lg
+        if cur != (dtype, dist, lg):
+            src = None
+            torch.cuda.empty_cache()
+            if dtype in ("u32", "u64", "pair"):
+                shape = (n, 2) if dtype == "pair" else (n,)
+                src = torch.empty(shape, dtype=torch.int32 if dtype == "u32" else torch.int64,
+                                  device=dev)
+                inputs.generate_into(src, dist, dtype, seed=SEED)
+            else:
+                src = inputs.generate(dist, dtype, n, seed=SEED, device=dev)
+            work = torch.empty_like(src)
+            sig = _multiset_sig(torch, src)
+            cur = (dtype, dist, lg)
+        D = ipsgpu.ELEM_BYTES[dtype]
+        s = ipsgpu.Sorter(dtype, algo=algo)
+        s.prepare()
+        times = []
+        for rep_ in range(1 + max(args.steps, 5)):
+            work.copy_(src)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.sort(work.data_ptr(), n, stream.cuda_stream)
+            e1.record(stream)
+            stream.synchronize()
+            if rep_ > 0:
+                times.append(e0.elapsed_time(e1))
+        s.set_timing(True)
+        work.copy_(src)
+        torch.cuda.synchronize(dev)
+        s.sort(work.data_ptr(), n, stream.cuda_stream)
+        stream.synchronize()
+        st = s.status(stream.cuda_stream)
+        stats = s.kernel_stats()
+        s.close()
+        ok = st == ipsgpu.OK and _keys_sorted(torch, work, dtype) and _multiset_sig(torch, work) == sig
+        med = statistics.median(times)
+        lv = level_roofline(stats, peak, D, n)
+        line = {"sweep": True, "dtype": dtype, "dist": dist, "n": n,
+                "algo": "IPS2Ra" if algo == ipsgpu.RADIX else "IPS4o",
+                "value": n / (med * 1e-3) / 1e9, "unit": UNIT, "ms_median": med,
+                "ms_mean": statistics.mean(times), "runs": len(times),
+                "level_roofline": lv,
+                "level_roofline_lower_bound_2Dn": (
+                    {"frac": lv["frac"] / 2, "note": "single read+write per level"} if lv else None),
+                "kernels_ms": {k: round(v[1], 3) for k, v in stats.items() if v[0]},
+                "result_sorted_and_same_multiset": ok}
+        print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     import __graft_entry__ as entry
@@ -707,6 +845,8 @@ def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args)
 

@@ -32,24 +32,55 @@ __device__ __forceinline__ uint64_t rk_lo<TRec100>(const TRec100::E &e) {
     return TRec100::key(e).lo;
 }
 
+// One pass over the input (Sec. 5): flags[0] stays set iff it is
+// non-decreasing, flags[1] iff it is non-increasing.  Each block reduces its
+// chunk's verdict with barrier votes and clears a flag at most once (a store
+// per thread to one word would serialise on it); a block stops as soon as
+// both flags are clear (the decision is block-uniform).  With mm set (radix
+// sorts) the pass reads everything and also leaves the minimum and maximum
+// radix key in mm[0], mm[1] (preset to ~0 and 0), from which the first digit
+// is placed at the highest bit where they differ.
 template <class T>
 __global__ void __launch_bounds__(kDetectThreads) k_detect(const unsigned char *data, uint64_t n,
-                                                           int *flags) {
+                                                           int *flags, unsigned long long *mm) {
     typedef typename T::E E;
     const E *a = reinterpret_cast<const E *>(data);
     volatile int *vf = flags;
-    for (uint64_t c0 = (uint64_t)blockIdx.x * kDetectChunk; c0 + 1 < n;
+    unsigned long long lmin = ~0ull, lmax = 0;
+    for (uint64_t c0 = (uint64_t)blockIdx.x * kDetectChunk; c0 < n;
          c0 += (uint64_t)gridDim.x * kDetectChunk) {
-        if (vf[0] == 0 && vf[1] == 0) return;
+        if (!mm && __syncthreads_or(vf[0] == 0 && vf[1] == 0)) return;
         bool inc = true, dec = true;
-        const uint64_t c1 = min(c0 + kDetectChunk, n - 1);
+        const uint64_t c1 = min(c0 + kDetectChunk, n);
         for (uint64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
-            typename T::K k0 = T::key(a[i]), k1 = T::key(a[i + 1]);
-            if (k1 < k0) inc = false;
-            if (k0 < k1) dec = false;
+            const E x = a[i];
+            if (mm) {
+                const unsigned long long r = T::rkey(x);
+                lmin = min(lmin, r);
+                lmax = max(lmax, r);
+            }
+            if (i + 1 < n) {
+                typename T::K k0 = T::key(x), k1 = T::key(a[i + 1]);
+                if (k1 < k0) inc = false;
+                if (k0 < k1) dec = false;
+            }
         }
-        if (!inc) flags[0] = 0;
-        if (!dec) flags[1] = 0;
+        const int not_inc = __syncthreads_or(!inc);
+        const int not_dec = __syncthreads_or(!dec);
+        if (threadIdx.x == 0) {
+            if (not_inc && vf[0]) flags[0] = 0;
+            if (not_dec && vf[1]) flags[1] = 0;
+        }
+    }
+    if (mm) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lmin = min(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+            lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&mm[0], lmin);
+            atomicMax(&mm[1], lmax);
+        }
     }
 }
 

@@ -42,6 +42,7 @@ struct GJob {
     const uint64_t *offsets;  // nseg_in + 1 element offsets into data, or null
     const uint64_t *segs;     // nseg_in (address, n) pairs, or null
     const int *skip_flags;    // if non-null and flags[0] or flags[1]: skip the input
+    const unsigned long long *radix_mm;  // single array, radix: key min and max (or null)
     uint64_t nseg_in;         // input arrays (1 in single-array mode)
     uint64_t n_total;         // elements of data (offsets and single-array mode)
     uint32_t max_waves;
@@ -207,10 +208,19 @@ static __global__ void __launch_bounds__(256) k_g_feed(GraphArgs g) {
             n = j.n_total;
         }
         if (n <= 1) continue;
+        // radix: the first digit ends at the top key bit, or, when the key
+        // range is known, at the highest bit where the smallest and the
+        // largest key differ (the bits above are common to every key)
+        uint32_t shift = g.keybits > g.kbits ? g.keybits - g.kbits : 0u;
+        if (j.radix_mm && g.algo == 1) {
+            const unsigned long long x = j.radix_mm[0] ^ j.radix_mm[1];
+            const uint32_t hb = x ? 63u - (uint32_t)__clzll((long long)x) : 0u;
+            shift = hb + 1 > g.kbits ? hb + 1 - g.kbits : 0u;
+        }
         if (n <= g.smax)
             g_push_base(g, addr, n);
         else
-            g_push_ring(g, floor, GList{addr, n, g.keybits > g.kbits ? g.keybits - g.kbits : 0u, 0u});
+            g_push_ring(g, floor, GList{addr, n, shift, 0u});
     }
 }
 

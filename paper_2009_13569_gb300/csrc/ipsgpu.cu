@@ -436,13 +436,14 @@ int graph_run(Sorter &s, const GJob &job, cudaStream_t st) {
 }
 
 GJob make_job(unsigned char *data, uint64_t n_total, const uint64_t *offsets, const uint64_t *segs,
-              uint64_t nseg, const int *skip_flags) {
+              uint64_t nseg, const int *skip_flags, const unsigned long long *radix_mm = nullptr) {
     GJob j;
     memset(&j, 0, sizeof j);
     j.data = data;
     j.offsets = offsets;
     j.segs = segs;
     j.skip_flags = skip_flags;
+    j.radix_mm = radix_mm;
     j.nseg_in = nseg;
     j.n_total = n_total;
     j.max_waves = kMaxWaves;
@@ -457,13 +458,18 @@ int sort_impl(Sorter &s, unsigned char *data, uint64_t n, cudaStream_t st) {
     if (n < 2) return IPSGPU_OK;
     if (n > (1ull << 40)) return IPSGPU_E_INVAL;
     s.data = data;
-    // both flags start non-zero ("still possible")
+    // both flags start non-zero ("still possible"); for radix the key
+    // min / max words follow them (d_flags + 2: ~0, then 0)
+    const bool radix = s.algo == IPSGPU_RADIX;
+    unsigned long long *mm = reinterpret_cast<unsigned long long *>(s.d_flags + 2);
     cudaError_t e = cudaMemsetAsync(s.d_flags, 1, 2 * sizeof(int), st);
-    if (e == cudaSuccess) e = s.ops->detect(&s, data, n, st);
+    if (e == cudaSuccess && radix) e = cudaMemsetAsync(mm, 0xFF, sizeof(unsigned long long), st);
+    if (e == cudaSuccess && radix) e = cudaMemsetAsync(mm + 1, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = s.ops->detect(&s, data, n, radix ? mm : nullptr, st);
     if (e == cudaSuccess) e = s.ops->reverse(&s, data, n, st);
     if (e != cudaSuccess) return IPSGPU_E_CUDA;
     s.level_elems = n;
-    return graph_run(s, make_job(data, n, nullptr, nullptr, 1, s.d_flags), st);
+    return graph_run(s, make_job(data, n, nullptr, nullptr, 1, s.d_flags, radix ? mm : nullptr), st);
 }
 
 int single_level(Sorter &s, unsigned char *data, uint64_t n, uint32_t mode, uint32_t nsplit,

@@ -75,12 +75,13 @@ struct OpsImpl {
         return cudaGetLastError();
     }
 
-    static cudaError_t detect(Sorter *s, const unsigned char *data, uint64_t n, cudaStream_t st) {
+    static cudaError_t detect(Sorter *s, const unsigned char *data, uint64_t n,
+                              unsigned long long *mm, cudaStream_t st) {
         uint64_t chunks = (n + kDetectChunk - 1) / kDetectChunk;
         uint32_t grid = (uint32_t)(chunks < (uint64_t)s->nsm * 8 ? chunks : (uint64_t)s->nsm * 8);
         if (grid == 0) grid = 1;
         s->tbegin(KK_DETECT, (double)n * T::D, st);  // one read pass
-        k_detect<T><<<grid, kDetectThreads, 0, st>>>(data, n, s->d_flags);
+        k_detect<T><<<grid, kDetectThreads, 0, st>>>(data, n, s->d_flags, mm);
         s->tend(st);
         return cudaGetLastError();
     }

@@ -45,7 +45,8 @@ struct TypeOps {
     cudaError_t (*level)(Sorter *, const LevelArgs &, const LevelGrids &, cudaStream_t);
     cudaError_t (*base)(Sorter *, const uint64_t *d_segs, uint32_t nsegs,
                         const uint32_t *nsegs_dev, uint32_t grid, cudaStream_t);
-    cudaError_t (*detect)(Sorter *, const unsigned char *data, uint64_t n, cudaStream_t);
+    cudaError_t (*detect)(Sorter *, const unsigned char *data, uint64_t n,
+                          unsigned long long *mm, cudaStream_t);
     cudaError_t (*reverse)(Sorter *, unsigned char *data, uint64_t n, cudaStream_t);
     cudaError_t (*classify_ids)(Sorter *, const LevelArgs &, uint32_t *out, cudaStream_t);
     cudaError_t (*wave)(Sorter *, const GraphArgs &, cudaStream_t, int in_graph,

@@ -75,3 +75,46 @@ def run_sort(dtype, host, **params):
         st = s.status(stream())
     assert st == ipsgpu.OK, ipsgpu.strerror(st)
     return inputs.to_numpy(d.cpu(), dtype)
+
+
+def multiset_sig(t):
+    """Order-independent signature of a device tensor's words (count, sum,
+    xor, sum of squares, each mod 2^64): equal for any permutation, and
+    changed by a lost, duplicated or altered word with overwhelming odds."""
+    if t.dtype == torch.uint8:
+        w = t.contiguous().view(torch.int32).reshape(-1).to(torch.int64)
+    elif t.element_size() == 4:
+        w = t.reshape(-1).view(torch.int32).to(torch.int64)
+    else:
+        w = t.reshape(-1).view(torch.int64)
+    acc = [w.numel(), 0, 0, 0]
+    for a in range(0, w.numel(), 1 << 27):
+        x = w[a:a + (1 << 27)]
+        acc[1] = (acc[1] + int(x.sum().item())) & ((1 << 64) - 1)
+        while x.numel() > 1:
+            if x.numel() % 2:
+                x = torch.cat([x, torch.zeros(1, dtype=x.dtype, device=x.device)])
+            x = x[0::2] ^ x[1::2]
+        acc[2] ^= int(x[0].item()) & ((1 << 64) - 1)
+        y = w[a:a + (1 << 27)]
+        acc[3] = (acc[3] + int((y * y).sum().item())) & ((1 << 64) - 1)
+    return tuple(acc)
+
+
+def keys_nondecreasing(t, dtype, chunk=1 << 27):
+    """Keys in non-decreasing order (unsigned; f64 by its order map)."""
+    n = t.shape[0]
+    for a in range(0, max(n - 1, 0), chunk):
+        x = t[a:a + chunk + 1]
+        if dtype == "u32":
+            k = x.to(torch.int64) & 0xFFFFFFFF
+        elif dtype in ("u64", "pair"):
+            k = (x[:, 0] if dtype == "pair" else x) ^ (-(1 << 63))
+        elif dtype == "f64":
+            b = x.view(torch.int64)
+            k = torch.where(b < 0, ~b, b | (-(1 << 63))) ^ (-(1 << 63))
+        else:
+            raise ValueError(dtype)
+        if not bool((k[1:] >= k[:-1]).all().item()):
+            return False
+    return True

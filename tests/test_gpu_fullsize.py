@@ -1,0 +1,31 @@
+"""Parity at the full sizes of the plain-sort configurations, in the form
+the bench times them (ipsgpu_sort through the sorter's CUDA graph): keys
+non-decreasing and the multiset of words unchanged.  For u32 / u64 / f64
+these two properties determine the output (the sorted permutation of a
+multiset is unique), so the result equals the oracle's."""
+import pytest
+import torch
+
+from paper_2009_13569_gb300 import inputs, ipsgpu
+from _util import DEV, keys_nondecreasing, multiset_sig, stream
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dtype,dist,log2n,algo", [
+    ("u64", "uniform", 30, ipsgpu.SAMPLESORT),
+    ("u64", "uniform", 30, ipsgpu.RADIX),
+    ("u32", "exponential", 30, ipsgpu.SAMPLESORT),
+    ("pair", "zipf", 28, ipsgpu.SAMPLESORT),
+])
+def test_full_size_sort_properties(dtype, dist, log2n, algo):
+    n = 1 << log2n
+    shape = (n, 2) if dtype == "pair" else (n,)
+    d = torch.empty(shape, dtype=torch.int32 if dtype == "u32" else torch.int64, device=DEV)
+    inputs.generate_into(d, dist, dtype, seed=0x5EED)
+    before = multiset_sig(d)
+    with ipsgpu.Sorter(dtype, algo=algo) as s:
+        s.sort(d.data_ptr(), n, stream())
+        assert s.status(stream()) == ipsgpu.OK
+    assert keys_nondecreasing(d, dtype)
+    assert multiset_sig(d) == before
