@@ -14,6 +14,8 @@ Array conventions (shared with the GPU binding by convention only):
   'f64'    -> numpy float64, shape (n,)
   'pair'   -> numpy uint64, shape (n, 2): column 0 key, column 1 value
   'rec100' -> numpy uint8,  shape (n, 100): bytes 0..9 key, 10..99 payload
+  'quartet'-> numpy uint64, shape (n, 4): columns 0..2 key (compared
+              lexicographically), column 3 value
 """
 import ctypes
 import os
@@ -25,8 +27,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
-DTYPES = {"u32": 0, "u64": 1, "f64": 2, "pair": 3, "rec100": 4}
-ELEM_BYTES = {"u32": 4, "u64": 8, "f64": 8, "pair": 16, "rec100": 100}
+DTYPES = {"u32": 0, "u64": 1, "f64": 2, "pair": 3, "rec100": 4, "quartet": 5}
+ELEM_BYTES = {"u32": 4, "u64": 8, "f64": 8, "pair": 16, "rec100": 100, "quartet": 32}
 
 _lib = None
 
@@ -68,14 +70,14 @@ def _load():
 
 def _count(a, dtype):
     a = np.asarray(a)
-    if dtype in ("pair", "rec100"):
+    if dtype in ("pair", "rec100", "quartet"):
         return a.shape[0]
     return a.size
 
 
 def _check(a, dtype):
     want = {"u32": np.uint32, "u64": np.uint64, "f64": np.float64,
-            "pair": np.uint64, "rec100": np.uint8}[dtype]
+            "pair": np.uint64, "rec100": np.uint8, "quartet": np.uint64}[dtype]
     a = np.ascontiguousarray(a)
     if a.dtype != want:
         raise TypeError("oracle: %s array must be %s, got %s" % (dtype, want, a.dtype))
@@ -83,6 +85,8 @@ def _check(a, dtype):
         raise ValueError("oracle: pair array must have shape (n, 2)")
     if dtype == "rec100" and (a.ndim != 2 or a.shape[1] != 100):
         raise ValueError("oracle: rec100 array must have shape (n, 100)")
+    if dtype == "quartet" and (a.ndim != 2 or a.shape[1] != 4):
+        raise ValueError("oracle: quartet array must have shape (n, 4)")
     return a
 
 

@@ -32,7 +32,10 @@
  *          -0.0 sorts before +0.0,
  *   3 pair: 16 bytes, key = first little-endian u64, value = second u64,
  *   4 rec100: 100 bytes, key = first 10 bytes compared lexicographically as
- *          unsigned bytes (the byte comparison of Sec. 6 with unsigned chars).
+ *          unsigned bytes (the byte comparison of Sec. 6 with unsigned chars),
+ *   5 quartet: 32 bytes, key = three little-endian u64 words (a, b, c)
+ *          compared lexicographically: a first, b on a tie in a, c on a tie
+ *          in both (the Quartet comparison of Sec. 6); value = fourth u64.
  *
  * Random sample positions come from splitmix64 (Steele, Lea and Flood,
  * "Fast splittable pseudorandom number generators", OOPSLA 2014), written
@@ -43,7 +46,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { DT_U32 = 0, DT_U64 = 1, DT_F64 = 2, DT_PAIR = 3, DT_REC100 = 4 };
+enum { DT_U32 = 0, DT_U64 = 1, DT_F64 = 2, DT_PAIR = 3, DT_REC100 = 4, DT_QUARTET = 5 };
 
 static size_t elem_size(int dt) {
     switch (dt) {
@@ -52,6 +55,7 @@ static size_t elem_size(int dt) {
     case DT_F64: return 8;
     case DT_PAIR: return 16;
     case DT_REC100: return 100;
+    case DT_QUARTET: return 32;
     default: return 0;
     }
 }
@@ -86,6 +90,12 @@ static int key_less(int dt, const unsigned char *a, const unsigned char *b) {
         return f64_order_bits(load_u64(a)) < f64_order_bits(load_u64(b));
     case DT_REC100:
         return memcmp(a, b, 10) < 0;
+    case DT_QUARTET:
+        for (int w = 0; w < 3; w++) {
+            uint64_t x = load_u64(a + 8 * w), y = load_u64(b + 8 * w);
+            if (x != y) return x < y;
+        }
+        return 0;
     }
     return 0;
 }

@@ -17,6 +17,14 @@ Storage formats (what the GPU library and ``to_numpy`` see):
   f64 -> torch.float64 (n,)
   pair -> torch.int64 (n, 2): key, value
   rec100 -> torch.uint8 (n, 100): 10-byte key, 90-byte payload
+  quartet -> torch.int64 (n, 4): key words a, b, c (lexicographic), value
+
+Quartet keys: "uniform" draws a, b and c as three independent uniform 64-bit
+words (the Quartet workload of Sec. 6); every other integer distribution
+draws its 64-bit value v and stores it as a = v >> 40, b = (v >> 20) mod
+2^20, c = v mod 2^20, an order-preserving embedding (so the sorted key
+sequence is that of v); "lexdup" draws a and b from {0, 1, 2, 3} and c
+uniform, so that most comparisons are decided by the third word.
 """
 import math
 
@@ -32,7 +40,8 @@ INT_DISTS = ("uniform", "exponential", "rootdup", "twodup", "eightdup",
              "almostsorted", "zipf", "sorted", "reversesorted", "zero")
 F64_DISTS = ("uniform", "normal")
 REC_DISTS = ("uniform", "rootdup")
-ELEM_BYTES = {"u32": 4, "u64": 8, "f64": 8, "pair": 16, "rec100": 100}
+QUARTET_DISTS = INT_DISTS + ("lexdup",)
+ELEM_BYTES = {"u32": 4, "u64": 8, "f64": 8, "pair": 16, "rec100": 100, "quartet": 32}
 
 
 def _s64(x):
@@ -150,15 +159,33 @@ def _int_values(dist, n, width, seed, device, i=None):
     raise ValueError("unknown distribution %r" % dist)
 
 
+def _quartet_keys(dist, n, seed, device, i=None):
+    """Key words (a, b, c) of a quartet input at global positions i."""
+    if i is None:
+        i = torch.arange(n, dtype=torch.int64, device=device)
+    if dist == "uniform":
+        return _draw_at(i, seed, 40), _draw_at(i, seed, 41), _draw_at(i, seed, 42)
+    if dist == "lexdup":
+        return _draw_at(i, seed, 43) & 3, _draw_at(i, seed, 44) & 3, _draw_at(i, seed, 45)
+    v = _int_values(dist, n, 64, seed, device, i)
+    return _lsr(v, 40), _lsr(v, 20) & 0xFFFFF, v & 0xFFFFF
+
+
 def generate_into(out, dist, dtype, seed=DEFAULT_SEED, chunk=1 << 26):
     """Fill `out` (storage format above, any device) with the same values as
     generate(dist, dtype, len(out), seed), chunk by chunk, so that inputs of
-    many GiB need little temporary memory.  u32, u64 and pair only."""
+    many GiB need little temporary memory.  u32, u64, pair and quartet."""
     n = out.shape[0]
     width = 32 if dtype == "u32" else 64
     for i0 in range(0, n, chunk):
         i1 = min(n, i0 + chunk)
         i = torch.arange(i0, i1, dtype=torch.int64, device=out.device)
+        if dtype == "quartet":
+            for w, x in enumerate(_quartet_keys(dist, n, seed, out.device, i)):
+                out[i0:i1, w] = x
+            out[i0:i1, 3] = i
+            del i
+            continue
         v = _int_values(dist, n, width, seed, out.device, i)
         if dtype == "u64":
             out[i0:i1] = v
@@ -168,7 +195,7 @@ def generate_into(out, dist, dtype, seed=DEFAULT_SEED, chunk=1 << 26):
             out[i0:i1, 0] = v
             out[i0:i1, 1] = i
         else:
-            raise ValueError("generate_into: u32, u64 and pair only")
+            raise ValueError("generate_into: u32, u64, pair and quartet only")
         del i, v
     return out
 
@@ -193,6 +220,12 @@ def generate(dist, dtype, n, seed=DEFAULT_SEED, device="cpu"):
         k = _int_values(dist, n, 64, seed, device)
         v = torch.arange(n, dtype=torch.int64, device=device)
         return torch.stack([k, v], dim=1).contiguous()
+    if dtype == "quartet":
+        if dist not in QUARTET_DISTS:
+            raise ValueError("quartet distributions: %s" % (QUARTET_DISTS,))
+        a, b, c = _quartet_keys(dist, n, seed, device)
+        v = torch.arange(n, dtype=torch.int64, device=device)
+        return torch.stack([a, b, c, v], dim=1).contiguous()
     if dtype == "rec100":
         out = torch.empty((n, 100), dtype=torch.uint8, device=device)
         if dist == "uniform":
@@ -303,7 +336,7 @@ def to_numpy(t, dtype):
     a = t.detach().cpu().contiguous().numpy()
     if dtype == "u32":
         return a.view(np.uint32)
-    if dtype in ("u64", "pair"):
+    if dtype in ("u64", "pair", "quartet"):
         return a.view(np.uint64)
     return a
 
@@ -313,7 +346,7 @@ def from_numpy(a, dtype, device="cpu"):
     a = np.ascontiguousarray(a)
     if dtype == "u32":
         a = a.view(np.int32)
-    elif dtype in ("u64", "pair"):
+    elif dtype in ("u64", "pair", "quartet"):
         a = a.view(np.int64)
     return torch.from_numpy(a.copy()).to(device)
 

@@ -18,6 +18,16 @@ def test_generate_into_matches_generate(dtype, dist):
     assert torch.equal(out, ref)
 
 
+@pytest.mark.parametrize("dist", inputs.QUARTET_DISTS)
+def test_quartet_generate_into_matches_generate(dist):
+    n = 30_001
+    ref = inputs.generate(dist, "quartet", n, seed=9)
+    out = torch.empty_like(ref)
+    inputs.generate_into(out, dist, "quartet", seed=9, chunk=4096)
+    assert torch.equal(out, ref)
+    assert torch.equal(ref[:, 3], torch.arange(n))
+
+
 def test_segmented_batch_layout():
     lengths = inputs.segment_lengths(50, 0, 12, seed=9)
     assert int(lengths.min()) >= 1 and int(lengths.max()) <= 1 << 12

@@ -125,6 +125,76 @@ def test_rec100_lexicographic_unsigned_bytes(dist):
     assert _multiset_hash(got) == _multiset_hash(a)
 
 
+def _qkeys(a):
+    return [tuple(r) for r in a[:, :3].tolist()]
+
+
+def test_quartet_bruteforce_all_short_sequences():
+    # every sequence of length <= 5 over the 8 keys with words in {0, 1},
+    # through the partitioning path (k=4, n0=1), against Python's tuple
+    # order (lexicographic by definition); the value column keeps each
+    # record's identity
+    keys = list(itertools.product(range(2), repeat=3))
+    for length in range(0, 6):
+        for seq in itertools.product(range(8), repeat=length):
+            a = np.array([keys[x] + (i,) for i, x in enumerate(seq)], dtype=np.uint64).reshape(-1, 4)
+            got = oracle.sort(a, "quartet", k=4, n0=1, seed=length)
+            assert _qkeys(got) == sorted(_qkeys(a)), seq
+            assert sorted(map(tuple, got.tolist())) == sorted(map(tuple, a.tolist()))
+
+
+def test_quartet_word_order_by_hand():
+    a = np.array([[1, 0, 0, 0], [0, 9, 9, 1], [0, 9, 0, 2], [0, 0, 5, 3],
+                  [0, 9, 9, 4], [2**64 - 1, 0, 0, 5], [0, 2**63, 0, 6]], dtype=np.uint64)
+    got = oracle.sort(a, "quartet", k=4, n0=1)
+    assert _qkeys(got) == [(0, 0, 5), (0, 9, 0), (0, 9, 9), (0, 9, 9), (0, 2**63, 0),
+                           (1, 0, 0), (2**64 - 1, 0, 0)]
+    assert oracle.insertion_sort(a, "quartet")[:, :3].tolist() == [list(k) for k in _qkeys(got)]
+
+
+@pytest.mark.parametrize("dist", inputs.QUARTET_DISTS)
+def test_quartet_matches_numpy_lexsort(dist):
+    n = 20000
+    a = inputs.to_numpy(inputs.generate(dist, "quartet", n), "quartet")
+    got = oracle.sort(a, "quartet")
+    ref = a[np.lexsort((a[:, 2], a[:, 1], a[:, 0]))]
+    np.testing.assert_array_equal(got[:, :3], ref[:, :3])
+    assert _multiset_hash(got) == _multiset_hash(a)
+    assert oracle.is_sorted(got, "quartet")
+    if dist not in ("uniform", "lexdup"):
+        # the order-preserving embedding of the 64-bit value
+        v = (got[:, 0] << np.uint64(40)) | (got[:, 1] << np.uint64(20)) | got[:, 2]
+        u = inputs.to_numpy(inputs.generate(dist, "u64", n), "u64")
+        np.testing.assert_array_equal(v, np.sort(u))
+
+
+@pytest.mark.parametrize("eq", [False, True])
+def test_quartet_classify_is_the_u64_classify_of_dense_ranks(eq):
+    # a comparison-based classification depends on the key order only: map
+    # every key to its dense rank in the lexicographic order (numpy sorts
+    # rows lexicographically) and the classes must be the searchsorted /
+    # equality-bucket classes of the ranks
+    rng = _rng(11 + eq)
+    n, m = 6000, 37
+    a = np.stack([rng.integers(0, 3, n), rng.integers(0, 3, n), rng.integers(0, 50, n),
+                  np.arange(n)], axis=1).astype(np.uint64)
+    spl = a[rng.choice(n, m, replace=False)]
+    spl = spl[np.lexsort((spl[:, 2], spl[:, 1], spl[:, 0]))]
+    allk = np.concatenate([a[:, :3], spl[:, :3]])
+    _, inv = np.unique(allk, axis=0, return_inverse=True)
+    ra, rs = inv[:n].astype(np.uint64).ravel(), inv[n:].astype(np.uint64).ravel()
+    cls, B = oracle.classify(a, "quartet", spl, eq)
+    pad, K = _padded(rs, m)
+    i = np.searchsorted(pad[:K - 1], ra, side="left")
+    if not eq:
+        assert B == K
+        np.testing.assert_array_equal(cls, i)
+    else:
+        assert B == 2 * K
+        hit = pad[np.minimum(i, K - 1)] == ra
+        np.testing.assert_array_equal(cls, np.where(hit, 2 * i + 1, np.where(i == K - 1, 2 * K - 1, 2 * i)))
+
+
 # ------------------------------------------------------------- closed forms
 
 def _expect_from_hist(values, counts):
