@@ -16,8 +16,8 @@
  * Conventions for every entry point:
  *   - Pointers named d_* are DEVICE pointers of the current CUDA device; the
  *     caller owns them.  Data arrays must be aligned to their element size
- *     (4 bytes for rec100) and must not be accessed by other work while a
- *     call on them is in flight.
+ *     (4 bytes for rec100, 16 for quartet) and must not be accessed by other
+ *     work while a call on them is in flight.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls are asynchronous with respect to the host unless a
  *     function says it synchronizes.  The sorts (ipsgpu_sort,
@@ -45,13 +45,17 @@ extern "C" {
  *              unsigned; this is '<' on non-NaN values with -0.0 before +0.0
  *   PAIR_U64   16 bytes {u64 key, u64 value}; key only
  *   REC100     100 bytes; the first 10 bytes compared lexicographically as
- *              unsigned bytes; 90 bytes of payload                          */
+ *              unsigned bytes; 90 bytes of payload
+ *   QUARTET    32 bytes {u64 a, u64 b, u64 c, u64 value}; key (a, b, c)
+ *              compared lexicographically (the Quartet comparison of
+ *              Sec. 6); arrays 16-byte aligned                              */
 typedef enum {
     IPSGPU_U32 = 0,
     IPSGPU_U64 = 1,
     IPSGPU_F64 = 2,
     IPSGPU_PAIR_U64 = 3,
-    IPSGPU_REC100 = 4
+    IPSGPU_REC100 = 4,
+    IPSGPU_QUARTET = 5
 } ipsgpu_dtype;
 
 /* Classifier of the partitioning step: the branchless splitter tree of IPS4o
@@ -103,8 +107,8 @@ typedef struct ipsgpu_sorter ipsgpu_sorter;
  * amount depends on the parameters only, never on n (see
  * ipsgpu_scratch_bytes).  params may be NULL (all defaults).  The sorter is
  * bound to the CUDA device current at creation.
- * Errors: E_INVAL (bad params, out NULL), E_UNSUPPORTED (RADIX with F64 or
- * REC100), E_NOMEM, E_CUDA. */
+ * Errors: E_INVAL (bad params, out NULL), E_UNSUPPORTED (RADIX with F64,
+ * REC100 or QUARTET), E_NOMEM, E_CUDA. */
 int ipsgpu_sorter_create(const ipsgpu_params *params, int dtype, ipsgpu_sorter **out);
 
 /* Build now what a sorter otherwise builds on its first sort: the CUDA graph
@@ -125,8 +129,8 @@ uint64_t ipsgpu_scratch_bytes(const ipsgpu_params *params, int dtype);
  * inputs (left as they are) and non-increasing ones (reversed) first
  * (Sec. 5), on the device.  Asynchronous: never synchronizes, and can be
  * captured into a CUDA graph.
- * For U32/U64/F64 the result is the unique sorted sequence; for PAIR_U64
- * and REC100 records with equal keys may appear in any order.
+ * For U32/U64/F64 the result is the unique sorted sequence; for PAIR_U64,
+ * REC100 and QUARTET records with equal keys may appear in any order.
  * Errors: E_INVAL, E_CUDA; kernel-side errors via ipsgpu_status. */
 int ipsgpu_sort(ipsgpu_sorter *s, void *d_data, uint64_t n, void *stream);
 
@@ -141,7 +145,8 @@ int ipsgpu_sort(ipsgpu_sorter *s, void *d_data, uint64_t n, void *stream);
  *                       padded to K entries with the largest one (Sec. 2)
  * and B = K or 2K; d_bucket_begin receives B+1 values (u64, device memory).
  * Order inside a bucket is unspecified.  B must be <= the sorter's k.
- * Errors: E_INVAL (num_splitters == 0, B > k, NULL pointers). */
+ * Errors: E_INVAL (num_splitters == 0, B > k, NULL or misaligned data or
+ * splitter pointers). */
 int ipsgpu_partition_level(ipsgpu_sorter *s, void *d_data, uint64_t n,
                            const void *d_splitters, uint32_t num_splitters,
                            int equal_buckets, uint64_t *d_bucket_begin, void *stream);
@@ -249,8 +254,8 @@ int ipsgpu_debug_bounded_wait(ipsgpu_sorter *s, uint32_t spin_limit, void *strea
  *     free lane.  A request that cannot run yet does not hold back those
  *     behind it.
  *   - Each request's result is exactly what ipsgpu_sort gives for it alone
- *     (for PAIR_U64 and REC100: the same keys, records with equal keys in
- *     some order).
+ *     (for PAIR_U64, REC100 and QUARTET: the same keys, records with equal
+ *     keys in some order).
  * Thread safety: every server call may be made from any host thread. */
 typedef struct ipsgpu_server ipsgpu_server;
 typedef struct {

@@ -24,12 +24,19 @@ constexpr int kBaseSmall = 512;          // ranges up to this size are finished 
 constexpr int kBaseSmallStack = 2048;    // pending small ranges: >= 188416 B / 4 B / 25
 
 
-// second-level radix key: non-zero only for keys wider than 64 bits
+// Radix-key word w < T::kKeyWords of an element, most significant first
+// (word 0 is T::rkey): keys wider than 64 bits go on in later words.
 template <class T>
-__device__ __forceinline__ uint64_t rk_lo(const typename T::E &e) { return 0; }
+__device__ __forceinline__ uint64_t rk_word(const typename T::E &e, int w) {
+    return T::rkey(e);
+}
 template <>
-__device__ __forceinline__ uint64_t rk_lo<TRec100>(const TRec100::E &e) {
-    return TRec100::key(e).lo;
+__device__ __forceinline__ uint64_t rk_word<TRec100>(const TRec100::E &e, int w) {
+    return w == 0 ? TRec100::rkey(e) : (uint64_t)TRec100::key(e).lo;
+}
+template <>
+__device__ __forceinline__ uint64_t rk_word<TQuartet>(const TQuartet::E &e, int w) {
+    return w == 0 ? e.a : (w == 1 ? e.b : e.c);
 }
 
 // One pass over the input (Sec. 5): flags[0] stays set iff it is
@@ -110,6 +117,14 @@ __device__ __forceinline__ Key80 shfl_key<TRec100>(Key80 k, int src) {
     r.lo = __shfl_sync(0xffffffffu, k.lo, src);
     return r;
 }
+template <>
+__device__ __forceinline__ Key192 shfl_key<TQuartet>(Key192 k, int src) {
+    Key192 r;
+    r.a = __shfl_sync(0xffffffffu, k.a, src);
+    r.b = __shfl_sync(0xffffffffu, k.b, src);
+    r.c = __shfl_sync(0xffffffffu, k.c, src);
+    return r;
+}
 
 // Bulk prefetch of [addr, addr + bytes) into L2 (both multiples of 16).
 __device__ __forceinline__ void prefetch_l2(uint64_t addr, uint32_t bytes) {
@@ -152,8 +167,8 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
     typedef typename T::E E;
     typedef typename T::K K;
     constexpr int ND = 1 << kBaseDigitBits;
-    constexpr int NB = T::D <= 8 ? 8 : (T::D <= 16 ? 4 : 1);  // elements in flight per thread
-    constexpr int U = (T::D == 4 || T::D == 8 || T::D == 16) ? T::D : 4;
+    constexpr int NB = T::D <= 8 ? 8 : (T::D <= 16 ? 4 : (T::D <= 32 ? 2 : 1));  // in flight per thread
+    constexpr int U = T::D % 16 == 0 ? 16 : (T::D % 8 == 0 ? 8 : 4);  // copy-out unit
     constexpr int DPT = ND / kBaseThreads;  // digits per thread in the scan
     extern __shared__ __align__(16) unsigned char smem[];
     // layout: buf | stk | sstk | cur (ND/2 words, two 16-bit counters each)
@@ -274,11 +289,12 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
             // a range is packed as (a0 << 16) | len; both are < 2^16 because
             // a segment holds at most kBaseSmemBytes / 4 < 2^16 elements
             const uint32_t a0 = top >> 16, len = top & 0xFFFFu;
-            // min / max of the radix key over the range (a second key word
-            // for keys wider than 64 bits when the first one is constant)
-            int mode = 0;  // 0: high word, 1: low word
+            // min / max of the radix key over the range: of its leading
+            // word, or, for keys wider than 64 bits, of the first word that
+            // is not constant over the range
+            int mode = 0;  // the key word the pass sorts by
             uint64_t mn = 0, rng = 0;
-            for (int pass = 0; pass < 2; pass++) {
+            for (int pass = 0; pass < T::kKeyWords; pass++) {
                 uint64_t gmn, gmx;
                 if (first && pass == 0) {
                     gmn = seg_mn;
@@ -286,8 +302,7 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
                 } else {
                     unsigned long long lmin = ~0ull, lmax = 0;
                     for (uint32_t i = tid; i < len; i += kBaseThreads) {
-                        const uint64_t v =
-                            pass == 0 ? T::rkey(buf[a0 + i]) : rk_lo<T>(buf[a0 + i]);
+                        const uint64_t v = rk_word<T>(buf[a0 + i], pass);
                         lmin = min(lmin, (unsigned long long)v);
                         lmax = max(lmax, (unsigned long long)v);
                     }
@@ -296,7 +311,7 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
                 mode = pass;
                 mn = gmn;
                 rng = gmx - gmn;
-                if (rng != 0 || sizeof(typename T::K) <= 8) break;
+                if (rng != 0) break;
             }
             first = false;
             if (rng == 0) continue;  // all keys equal: the range is final
@@ -307,13 +322,14 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
             const uint32_t shift = nbits - dbits;
             const uint32_t nd = 1u << dbits;
             const uint32_t nw = (nd + 1) >> 1;  // counter words in use
-            // with shift 0 a digit is the whole key (key word): each
-            // sub-bucket holds one key, so it is final
-            const bool exact = shift == 0 && (sizeof(typename T::K) <= 8 || mode == 1);
+            // with shift 0 a digit is the whole key word; in the last word
+            // (the words before it are constant) each sub-bucket then holds
+            // one key, so it is final
+            const bool exact = shift == 0 && mode == T::kKeyWords - 1;
             for (uint32_t w = tid; w < nw; w += kBaseThreads) cur[w] = 0;
             __syncthreads();
             for (uint32_t i = tid; i < len; i += kBaseThreads) {
-                const uint64_t v = mode == 0 ? T::rkey(buf[a0 + i]) : rk_lo<T>(buf[a0 + i]);
+                const uint64_t v = rk_word<T>(buf[a0 + i], mode);
                 const uint32_t d = (uint32_t)((v - mn) >> shift);
                 atomicAdd(&cur[word(d)], 1u << (16 * (d & 1)));
             }
@@ -371,7 +387,7 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
                 for (int q = 0; q < NB; q++) {
                     const uint32_t i = i0 + q * kBaseThreads + tid;
                     if (i < len) {
-                        const uint64_t v = mode == 0 ? T::rkey(x[q]) : rk_lo<T>(x[q]);
+                        const uint64_t v = rk_word<T>(x[q], mode);
                         const uint32_t d = (uint32_t)((v - mn) >> shift);
                         const uint32_t h = 16 * (d & 1);
                         const uint32_t p = (atomicAdd(&cur[word(d)], 1u << h) >> h) & 0xFFFFu;
@@ -430,21 +446,30 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
         for (uint32_t r = warp; r < nsmall; r += NW) {
             const uint32_t top = sstk[r];
             const uint32_t a0 = top >> 16, c = top & 0xFFFFu;
-            unsigned long long mn0 = ~0ull, mx0 = 0, mn1 = ~0ull, mx1 = 0;
+            unsigned long long mn[T::kKeyWords], mx[T::kKeyWords];
+#pragma unroll
+            for (int w = 0; w < T::kKeyWords; w++) {
+                mn[w] = ~0ull;
+                mx[w] = 0;
+            }
             for (uint32_t p = lane; p < c; p += 32) {
-                const unsigned long long v0 = T::rkey(buf[a0 + p]), v1 = rk_lo<T>(buf[a0 + p]);
-                mn0 = min(mn0, v0);
-                mx0 = max(mx0, v0);
-                mn1 = min(mn1, v1);
-                mx1 = max(mx1, v1);
+#pragma unroll
+                for (int w = 0; w < T::kKeyWords; w++) {
+                    const unsigned long long v = rk_word<T>(buf[a0 + p], w);
+                    mn[w] = min(mn[w], v);
+                    mx[w] = max(mx[w], v);
+                }
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                mn0 = min(mn0, __shfl_xor_sync(0xffffffffu, mn0, o));
-                mx0 = max(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
-                mn1 = min(mn1, __shfl_xor_sync(0xffffffffu, mn1, o));
-                mx1 = max(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
+            bool all_equal = true;
+#pragma unroll
+            for (int w = 0; w < T::kKeyWords; w++) {
+                for (int o = 16; o > 0; o >>= 1) {
+                    mn[w] = min(mn[w], __shfl_xor_sync(0xffffffffu, mn[w], o));
+                    mx[w] = max(mx[w], __shfl_xor_sync(0xffffffffu, mx[w], o));
+                }
+                all_equal = all_equal && mn[w] == mx[w];
             }
-            if (mn0 == mx0 && mn1 == mx1) continue;  // all keys equal
+            if (all_equal) continue;  // all keys equal
             for (uint32_t p = lane; p < c; p += 32) {
                 const E x = buf[a0 + p];
                 const K kx = T::key(x);

@@ -35,12 +35,12 @@ constexpr int kCells = 1 << kCellBits;
 
 template <class T>
 struct ClsCfg {
-    static constexpr bool kSmall = T::D <= 16;
+    static constexpr bool kSmall = T::D <= 32;
     static constexpr int NT = kSmall ? 1024 : 512;
-    // elements per thread and tile: a 48-64 KiB stage for 4..16-byte elements
-    static constexpr int EPT = T::D == 4 ? 12 : (T::D == 8 ? 8 : (T::D == 16 ? 4 : 1));
+    // elements per thread and tile: a 48-64 KiB stage for 4..32-byte elements
+    static constexpr int EPT =
+        T::D == 4 ? 12 : (T::D == 8 ? 8 : (T::D == 16 ? 4 : (T::D == 32 ? 2 : 1)));
     static constexpr int TILE = NT * EPT;
-    static constexpr int UNIT = (T::D == 4 || T::D == 8 || T::D == 16) ? T::D : 4;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -124,6 +124,20 @@ __device__ __forceinline__ Key80 key_hi_of<TRec100>(uint64_t rk) {
     k.lo = 0xFFFFu;
     return k;
 }
+template <>
+__device__ __forceinline__ Key192 key_lo_of<TQuartet>(uint64_t rk) {
+    Key192 k;
+    k.a = rk;
+    k.b = k.c = 0;
+    return k;
+}
+template <>
+__device__ __forceinline__ Key192 key_hi_of<TQuartet>(uint64_t rk) {
+    Key192 k;
+    k.a = rk;
+    k.b = k.c = ~0ull;
+    return k;
+}
 template <class T>
 __device__ __forceinline__ uint64_t rk_of_key(const typename T::K &k) {
     return (uint64_t)k;
@@ -131,6 +145,10 @@ __device__ __forceinline__ uint64_t rk_of_key(const typename T::K &k) {
 template <>
 __device__ __forceinline__ uint64_t rk_of_key<TRec100>(const Key80 &k) {
     return k.hi;
+}
+template <>
+__device__ __forceinline__ uint64_t rk_of_key<TQuartet>(const Key192 &k) {
+    return k.a;
 }
 
 // Cell geometry of the start-node table, over x = rk - base (0 below base).

@@ -11,10 +11,13 @@ namespace ipsgpu {
 
 // ---------------------------------------------------------------- limits
 constexpr int kMaxClasses = 256;      // buckets per level incl. equality ones
-// sample keys sorted in one CTA: 16384, at most 128 KiB of keys
+// sample keys sorted in one CTA: the largest power of two <= 16384 whose
+// keys fit in 128 KiB (the bitonic sort pads the sample to a power of two)
 template <class K>
 constexpr uint32_t max_sort_sample() {
-    return (128u * 1024 / sizeof(K)) < 16384u ? (uint32_t)(128u * 1024 / sizeof(K)) : 16384u;
+    uint32_t m = 16384u;
+    while (m > 1 && (uint64_t)m * sizeof(K) > 128u * 1024) m >>= 1;
+    return m;
 }
 constexpr uint32_t kRBias = 1u << 30; // bias of the read pointer field
 constexpr int kBaseSmemBytes = 184 * 1024;  // element buffer of the base case
@@ -32,19 +35,41 @@ __host__ __device__ inline bool operator==(const Key80 &a, const Key80 &b) {
     return a.hi == b.hi && a.lo == b.lo;
 }
 
+// Quartet keys: three u64 words compared lexicographically (Sec. 6)
+struct Key192 {
+    uint64_t a, b, c;
+};
+__host__ __device__ inline bool operator<(const Key192 &x, const Key192 &y) {
+    return x.a != y.a ? x.a < y.a : (x.b != y.b ? x.b < y.b : x.c < y.c);
+}
+__host__ __device__ inline bool operator==(const Key192 &x, const Key192 &y) {
+    return x.a == y.a && x.b == y.b && x.c == y.c;
+}
+
 struct PairElem {
     uint64_t k, v;
+};
+// 16-byte aligned so that an element moves as two 16-byte accesses
+struct __align__(16) QuartetElem {
+    uint64_t a, b, c, v;
 };
 struct Rec100Elem {
     uint32_t w[25];
 };
 
-// Element traits.  E: element storage, K: key, D: bytes, key(): order key.
+// Element traits.  E: element storage, K: key, D: bytes, key(): order key,
+// rkey(): the key's leading 64-bit word (radix key of the base case and of
+// the start-node table), kKeyWords: 64-bit words the base case's radix
+// passes walk through (rk_word<T>(e, w), w < kKeyWords), kHeadLanes: lanes of a
+// warp-held block (16 bytes each) that hold its first element's key,
+// head(): that element from lane 0's (and lane 1's) 16 bytes.
 struct TU32 {
     typedef uint32_t E;
     typedef uint32_t K;
     static constexpr int D = 4;
     static constexpr bool kRadix = true;
+    static constexpr int kKeyWords = 1;
+    static constexpr int kHeadLanes = 1;
     __device__ static K key(const E &e) { return e; }
     __device__ static uint64_t rkey(const E &e) { return e; }
     __device__ static K max_key() { return 0xFFFFFFFFu; }
@@ -55,6 +80,8 @@ struct TU64 {
     typedef uint64_t K;
     static constexpr int D = 8;
     static constexpr bool kRadix = true;
+    static constexpr int kKeyWords = 1;
+    static constexpr int kHeadLanes = 1;
     __device__ static K key(const E &e) { return e; }
     __device__ static uint64_t rkey(const E &e) { return e; }
     __device__ static K max_key() { return ~0ull; }
@@ -66,6 +93,8 @@ struct TF64 {
     typedef uint64_t K;
     static constexpr int D = 8;
     static constexpr bool kRadix = false;
+    static constexpr int kKeyWords = 1;
+    static constexpr int kHeadLanes = 1;
     __device__ static K key(const E &e) {
         return (e >> 63) ? ~e : (e | 0x8000000000000000ull);
     }
@@ -78,6 +107,8 @@ struct TPair {
     typedef uint64_t K;
     static constexpr int D = 16;
     static constexpr bool kRadix = true;
+    static constexpr int kKeyWords = 1;
+    static constexpr int kHeadLanes = 1;
     __device__ static K key(const E &e) { return e.k; }
     __device__ static uint64_t rkey(const E &e) { return e.k; }
     __device__ static K max_key() { return ~0ull; }
@@ -93,6 +124,8 @@ struct TRec100 {
     typedef Key80 K;
     static constexpr int D = 100;
     static constexpr bool kRadix = false;
+    static constexpr int kKeyWords = 2;
+    static constexpr int kHeadLanes = 1;
     // bytes 0..3 of a record are w[0] little-endian, so byte-swapping w[0]
     // and w[1] gives bytes 0..7 in big-endian (lexicographic) order
     __device__ static K key_words(uint32_t w0, uint32_t w1, uint32_t w2) {
@@ -119,6 +152,53 @@ struct TRec100 {
         return e;
     }
 };
+
+struct TQuartet {
+    typedef QuartetElem E;
+    typedef Key192 K;
+    static constexpr int D = 32;
+    static constexpr bool kRadix = false;
+    static constexpr int kKeyWords = 3;
+    static constexpr int kHeadLanes = 2;
+    __device__ static K key(const E &e) {
+        K k;
+        k.a = e.a;
+        k.b = e.b;
+        k.c = e.c;
+        return k;
+    }
+    __device__ static uint64_t rkey(const E &e) { return e.a; }
+    __device__ static K max_key() {
+        K k;
+        k.a = k.b = k.c = ~0ull;
+        return k;
+    }
+    __device__ static E head2(uint4 h0, uint4 h1) {
+        E e;
+        e.a = (uint64_t)h0.x | ((uint64_t)h0.y << 32);
+        e.b = (uint64_t)h0.z | ((uint64_t)h0.w << 32);
+        e.c = (uint64_t)h1.x | ((uint64_t)h1.y << 32);
+        e.v = (uint64_t)h1.z | ((uint64_t)h1.w << 32);
+        return e;
+    }
+};
+
+// The first element of a block held by a warp, 16 bytes per lane (lane 0's
+// bytes, and lane 1's where the key reaches past them).  Every lane calls it;
+// lane 0's result is the element.
+template <class T>
+__device__ __forceinline__ typename T::E block_head(const uint4 &r) {
+    if constexpr (T::kHeadLanes == 2) {
+        uint4 r1;
+        r1.x = __shfl_sync(0xffffffffu, r.x, 1);
+        r1.y = __shfl_sync(0xffffffffu, r.y, 1);
+        r1.z = __shfl_sync(0xffffffffu, r.z, 1);
+        r1.w = __shfl_sync(0xffffffffu, r.w, 1);
+        return T::head2(r, r1);
+    } else {
+        return T::head(r);
+    }
+}
 
 // ------------------------------------------------------------ level layouts
 // Planned description of one segment partitioned in a level launch (written

@@ -37,6 +37,7 @@ const TypeOps *ops_for(int dtype) {
     case IPSGPU_F64: return &ops_f64;
     case IPSGPU_PAIR_U64: return &ops_pair;
     case IPSGPU_REC100: return &ops_rec100;
+    case IPSGPU_QUARTET: return &ops_quartet;
     default: return nullptr;
     }
 }
@@ -684,7 +685,7 @@ int ipsgpu_partition_level(ipsgpu_sorter *h, void *d_data, uint64_t n, const voi
     if (n == 0)
         return cuda_status(cudaMemsetAsync(d_bucket_begin, 0, sizeof(uint64_t) * (B + 1), st));
     int rc = check_data(s, d_data);
-    if (rc) return rc;
+    if (rc || (rc = check_data(s, d_splitters))) return rc;
     rc = single_level(s, (unsigned char *)d_data, n, 1, num_splitters, equal_buckets, 0, 0,
                       (const unsigned char *)d_splitters, st);
     if (rc) return rc;
@@ -798,7 +799,7 @@ int ipsgpu_classify(ipsgpu_sorter *h, const void *d_data, uint64_t n, const void
     if (B > s.k) return IPSGPU_E_INVAL;
     if (n == 0) return IPSGPU_OK;
     int rc = check_data(s, d_data);
-    if (rc) return rc;
+    if (rc || (rc = check_data(s, d_splitters))) return rc;
     if ((rc = wait_uploads(s))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     s.data = (unsigned char *)d_data;

@@ -460,6 +460,7 @@ __global__ void __launch_bounds__(kAuxThreads) k_fixup(LevelArgs a) {
 template <class T>
 __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a) {
     typedef typename T::K K;
+    typedef typename T::E E;
     __shared__ K s_tree[kMaxClasses];
     __shared__ K s_spl[kMaxClasses];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -534,7 +535,8 @@ __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a) {
                 if (!got) break;
                 scanned = 0;
                 uint32_t tt = 0;
-                if (lane == 0) tt = cl(T::head(A));
+                const E ha = block_head<T>(A);
+                if (lane == 0) tt = cl(ha);
                 t = __shfl_sync(0xffffffffu, tt, 0);
                 hold = true;
             }
@@ -559,7 +561,8 @@ __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a) {
             if (unproc) {
                 warp_load_block(Bk, base + (uint64_t)slot * BB, BB, lane, u);
                 uint32_t t2 = 0;
-                if (lane == 0) t2 = cl(T::head(Bk));
+                const E hb = block_head<T>(Bk);
+                if (lane == 0) t2 = cl(hb);
                 t2 = __shfl_sync(0xffffffffu, t2, 0);
                 if (t2 == t) continue;  // already in place: w moved past it
                 warp_store_block(A, base + (uint64_t)slot * BB, BB, lane, u);

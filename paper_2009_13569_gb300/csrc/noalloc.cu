@@ -39,6 +39,7 @@ constexpr uint32_t kNaMoves = 2 * (kNaStripes + kMaxClasses) + 4;
 constexpr uint64_t kNaSlot = (uint64_t)kMaxClasses * 512;  // leftover buffers of one stripe
 constexpr uint64_t kNaMaxN = 0xFFFFFFFFull;                // elements per call
 constexpr int kNaMaxDevices = 64;
+constexpr int kNaTypes = IPSGPU_QUARTET + 1;
 
 constexpr uint64_t al(uint64_t x) { return (x + 255) & ~(uint64_t)255; }
 // cleanup staging of C <= 256 blocks of <= 512 bytes, then the overflow block
@@ -47,7 +48,7 @@ constexpr uint64_t kOSeg = 0;
 constexpr uint64_t kOSt = al(kOSeg + sizeof(SegDesc));
 constexpr uint64_t kOSarr = al(kOSt + sizeof(SegState));   // SegArrays: bucket_begin first
 constexpr uint64_t kOKeys = al(kOSarr + 28 * kMaxClasses + 32);  // tree, splitters
-constexpr uint64_t kOStripe = al(kOKeys + 2 * kMaxClasses * 16);
+constexpr uint64_t kOStripe = al(kOKeys + 2 * kMaxClasses * sizeof(Key192));  // widest key
 constexpr uint64_t kOScount = al(kOStripe + kNaStripes * sizeof(StripeDesc));
 constexpr uint64_t kOSfull = al(kOScount + (uint64_t)kNaStripes * kMaxClasses * 4);
 constexpr uint64_t kOMoves = al(kOSfull + kNaStripes * 4);
@@ -64,7 +65,7 @@ struct DeviceSetup {
     bool done[kNaMaxDevices] = {};
     unsigned char *ptr[kNaMaxDevices] = {};
     int nsm[kNaMaxDevices] = {};
-    bool typed[kNaMaxDevices][5] = {};
+    bool typed[kNaMaxDevices][kNaTypes] = {};
 };
 DeviceSetup g_setup;
 
@@ -129,6 +130,7 @@ const TypeOps *na_ops(int dtype) {
     case IPSGPU_F64: return &ops_f64;
     case IPSGPU_PAIR_U64: return &ops_pair;
     case IPSGPU_REC100: return &ops_rec100;
+    case IPSGPU_QUARTET: return &ops_quartet;
     default: return nullptr;
     }
 }
@@ -151,7 +153,8 @@ extern "C" int ipsgpu_partition_level_noalloc(int dtype, void *d_data, uint64_t 
                    ? IPSGPU_OK
                    : IPSGPU_E_CUDA;
     const uintptr_t al_req = ops->D == 100 ? 4 : (uintptr_t)(ops->D < 16 ? ops->D : 16);
-    if (!d_data || ((uintptr_t)d_data % al_req)) return IPSGPU_E_INVAL;
+    if (!d_data || ((uintptr_t)d_data % al_req) || ((uintptr_t)d_splitters % al_req))
+        return IPSGPU_E_INVAL;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return IPSGPU_E_CUDA;

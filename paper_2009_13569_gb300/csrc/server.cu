@@ -46,7 +46,7 @@
 
 namespace {
 
-constexpr int kTypes = 5;
+constexpr int kTypes = 6;
 
 int elem_bytes(int dtype) {
     switch (dtype) {
@@ -55,6 +55,7 @@ int elem_bytes(int dtype) {
     case IPSGPU_F64: return 8;
     case IPSGPU_PAIR_U64: return 16;
     case IPSGPU_REC100: return 100;
+    case IPSGPU_QUARTET: return 32;
     default: return 0;
     }
 }

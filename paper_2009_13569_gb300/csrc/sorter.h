@@ -53,7 +53,7 @@ struct TypeOps {
                         cudaGraphConditionalHandle);
 };
 
-extern const TypeOps ops_u32, ops_u64, ops_f64, ops_pair, ops_rec100;
+extern const TypeOps ops_u32, ops_u64, ops_f64, ops_pair, ops_rec100, ops_quartet;
 
 struct TimedLaunch {
     int kind;

@@ -24,6 +24,8 @@ def keys_of(a, dtype):
         return a[:, 0]
     if dtype == "rec100":
         return a[:, :10]
+    if dtype == "quartet":
+        return a[:, :3]
     if dtype == "f64":
         b = a.view(np.uint64)
         return np.where(b >> np.uint64(63), ~b, b | np.uint64(1 << 63))
@@ -32,8 +34,9 @@ def keys_of(a, dtype):
 
 def rows(a, dtype):
     """Canonically ordered copy of the records, to compare multisets."""
-    if dtype in ("pair", "rec100"):
-        v = np.ascontiguousarray(a).view(np.uint8).reshape(len(a), -1)
+    if dtype in ("pair", "rec100", "quartet"):
+        a = np.ascontiguousarray(a)
+        v = a.view(np.uint8).reshape(len(a), a.itemsize * int(np.prod(a.shape[1:])))
         order = np.lexsort(v.T[::-1])
         return v[order]
     return np.sort(a.view(np.uint64) if dtype == "f64" else a)
@@ -113,6 +116,15 @@ def keys_nondecreasing(t, dtype, chunk=1 << 27):
         elif dtype == "f64":
             b = x.view(torch.int64)
             k = torch.where(b < 0, ~b, b | (-(1 << 63))) ^ (-(1 << 63))
+        elif dtype == "quartet":
+            # lexicographic on the three key words, each unsigned
+            w = [x[:, j] ^ (-(1 << 63)) for j in range(3)]
+            lt = w[2][1:] < w[2][:-1]
+            for j in (1, 0):
+                lt = (w[j][1:] < w[j][:-1]) | ((w[j][1:] == w[j][:-1]) & lt)
+            if bool(lt.any().item()):
+                return False
+            continue
         else:
             raise ValueError(dtype)
         if not bool((k[1:] >= k[:-1]).all().item()):

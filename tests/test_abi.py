@@ -43,6 +43,19 @@ def test_strerror_and_scratch_bytes(lib):
     # radix takes unsigned keys only
     assert ipsgpu.scratch_bytes("f64", algo=ipsgpu.RADIX) == 0
     assert ipsgpu.scratch_bytes("u64", k=3) == 0
+    assert ipsgpu.scratch_bytes("quartet") > 0
+    assert ipsgpu.scratch_bytes("quartet", algo=ipsgpu.RADIX) == 0
+    assert ipsgpu.scratch_bytes("rec100", algo=ipsgpu.RADIX) == 0
+
+
+def test_dtype_enum_matches_binding():
+    with open(os.path.join(ROOT, "include", "ipsgpu.h")) as f:
+        text = f.read()
+    enum = dict((k, int(v)) for k, v in re.findall(r"IPSGPU_(U32|U64|F64|PAIR_U64|REC100|QUARTET)"
+                                                   r"\s*=\s*(\d+)", text))
+    names = {"u32": "U32", "u64": "U64", "f64": "F64", "pair": "PAIR_U64", "rec100": "REC100",
+             "quartet": "QUARTET"}
+    assert {d: enum[names[d]] for d in names} == ipsgpu.DTYPES
 
 
 def test_params_struct_layout():

@@ -12,7 +12,7 @@ from _util import DEV, assert_level_parity, stream, to_dev
 
 pytestmark = pytest.mark.gpu
 
-DTYPES = ["u32", "u64", "f64", "pair", "rec100"]
+DTYPES = ["u32", "u64", "f64", "pair", "rec100", "quartet"]
 
 
 def _input(dtype, n, dist, seed=5):
@@ -20,6 +20,8 @@ def _input(dtype, n, dist, seed=5):
         dist = "uniform" if dist != "normal" else dist
     elif dtype == "rec100":
         dist = "rootdup" if dist in ("rootdup", "twodup") else "uniform"
+    elif dtype == "quartet" and dist == "twodup":
+        dist = "lexdup"  # ties in the first two words
     return inputs.generate(dist, dtype, n, seed=seed)
 
 

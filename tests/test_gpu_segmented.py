@@ -66,10 +66,14 @@ def test_segmented_u64_base_case_boundary():
     _check_segments(got, inputs.to_numpy(data, "u64"), offsets.numpy(), "u64")
 
 
-@pytest.mark.parametrize("dtype", ["u32", "f64", "pair", "rec100"])
+@pytest.mark.parametrize("dtype", ["u32", "f64", "pair", "rec100", "quartet"])
 def test_segmented_other_types(dtype):
     if dtype == "rec100":
         lengths, dists = [5000, 1, 30_000, 700, 9000, 12], inputs.REC_DISTS
+    elif dtype == "quartet":
+        # around the 5888-element base-case capacity, and several levels
+        lengths, dists = [5887, 5888, 5889, 3, 80_000, 0, 33, 150_001], \
+            ("uniform", "lexdup", "rootdup", "zipf")
     elif dtype == "f64":
         lengths, dists = [100_000, 3, 50_000, 20_000, 64, 130_000], inputs.F64_DISTS
     else:
@@ -207,6 +211,19 @@ def test_sort_batch_pairs_and_bad_entry():
         assert s.status(stream()) == ipsgpu.E_INVAL
     for h, t in zip(hosts, devs):
         assert_sorted_parity(inputs.to_numpy(t.cpu(), "pair"), inputs.to_numpy(h, "pair"), "pair")
+
+
+def test_sort_batch_quartets():
+    hosts = [inputs.generate(d, "quartet", m, seed=60 + m)
+             for d, m in (("lexdup", 40_000), ("uniform", 6000), ("rootdup", 70_001), ("zero", 500))]
+    devs = [to_dev(h) for h in hosts]
+    segs = torch.tensor([[t.data_ptr(), t.shape[0]] for t in devs], dtype=torch.int64).to(DEV)
+    with ipsgpu.Sorter("quartet") as s:
+        s.sort_batch(segs.data_ptr(), len(devs), stream())
+        assert s.status(stream()) == ipsgpu.OK
+    for h, t in zip(hosts, devs):
+        assert_sorted_parity(inputs.to_numpy(t.cpu(), "quartet"), inputs.to_numpy(h, "quartet"),
+                             "quartet")
 
 
 @pytest.mark.parametrize("timing", [False, True])

@@ -16,8 +16,8 @@ DISTS = ("uniform", "twodup", "zipf", "rootdup", "sorted", "reversesorted", "alm
 
 def _requests(count, lo, hi, seed):
     lengths = inputs.segment_lengths(count, lo, hi, seed=seed).tolist()
-    types = ("u32", "u64", "pair")
-    return [(types[i % 3], DISTS[i % len(DISTS)], int(m), seed * 1000 + i)
+    types = ("u32", "u64", "pair", "quartet")
+    return [(types[i % 4], DISTS[i % len(DISTS)], int(m), seed * 1000 + i)
             for i, m in enumerate(lengths)]
 
 
@@ -33,7 +33,8 @@ def _alone(dtype, host):
 def test_server_mix_matches_alone_and_oracle(batch_max_elems):
     reqs = _requests(48, 3, 20, seed=7 + batch_max_elems)
     side = torch.cuda.Stream(DEV)
-    with ipsgpu.Server(8 << 30, lanes=3, batch_max_elems=batch_max_elems) as srv:
+    with ipsgpu.Server(8 << 30, lanes=3, batch_max_elems=batch_max_elems,
+                       dtypes=("u32", "u64", "pair", "quartet")) as srv:
         live = []
         for i, (dtype, dist, m, seed) in enumerate(reqs):
             host = inputs.generate(dist, dtype, m, seed=seed)
@@ -60,7 +61,8 @@ def test_server_mix_matches_alone_and_oracle(batch_max_elems):
             if dtype in ("u32", "u64"):
                 np.testing.assert_array_equal(got, alone)
             else:
-                np.testing.assert_array_equal(got[:, 0], alone[:, 0])
+                k = 3 if dtype == "quartet" else 1  # key columns
+                np.testing.assert_array_equal(got[:, :k], alone[:, :k])
             srv.release(t)
         used, budget, scratch = srv.usage()
         assert used == scratch and budget == 8 << 30

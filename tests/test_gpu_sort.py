@@ -39,6 +39,49 @@ def test_sort_rec100(dist):
     assert_sorted_parity(run_sort("rec100", host), inputs.to_numpy(host, "rec100"), "rec100")
 
 
+@pytest.mark.parametrize("dist", inputs.QUARTET_DISTS)
+def test_sort_quartet(dist):
+    host = inputs.generate(dist, "quartet", N)
+    assert_sorted_parity(run_sort("quartet", host), inputs.to_numpy(host, "quartet"), "quartet")
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 5887, 5888, 5889, 2 ** 16 + 3])
+def test_sort_quartet_sizes(n):
+    # 5888 = 184 KiB / 32 B: the base-case capacity for quartets
+    host = inputs.generate("lexdup", "quartet", n, seed=n + 3)
+    assert_sorted_parity(run_sort("quartet", host), inputs.to_numpy(host, "quartet"), "quartet")
+
+
+def test_sort_quartet_deep_ties():
+    # long runs equal in the first word, then in the first two: the radix
+    # passes of the base case move on to the second and third words, and
+    # the splitters tie in their leading words
+    n = 250_000
+    host = inputs.generate("uniform", "quartet", n, seed=21)
+    a = inputs.to_numpy(host, "quartet")
+    a[:, 0] = np.uint64(7)
+    a[: n // 2, 1] = a[: n // 2, 1] % np.uint64(3)
+    a[n // 3: n // 2, 2] = a[n // 3: n // 2, 2] % np.uint64(5)
+    a[::11, 0] = np.uint64(2 ** 64 - 1)
+    a[5::13, :3] = np.uint64(0)
+    host = inputs.from_numpy(a, "quartet")
+    assert_sorted_parity(run_sort("quartet", host), a, "quartet")
+
+
+@pytest.mark.parametrize("base_case", [32, 700])
+@pytest.mark.parametrize("dist", ["uniform", "lexdup", "rootdup"])
+def test_sort_quartet_small_base_case(base_case, dist):
+    host = inputs.generate(dist, "quartet", 150_001, seed=base_case)
+    got = run_sort("quartet", host, base_case=base_case)
+    assert_sorted_parity(got, inputs.to_numpy(host, "quartet"), "quartet")
+
+
+def test_quartet_radix_unsupported():
+    with pytest.raises(ipsgpu.IpsgpuError) as e:
+        ipsgpu.Sorter("quartet", algo=ipsgpu.RADIX)
+    assert e.value.code == ipsgpu.E_UNSUPPORTED
+
+
 @pytest.mark.parametrize("dist", ["uniform", "twodup", "almostsorted", "exponential"])
 @pytest.mark.parametrize("dtype", ["u32", "u64", "pair"])
 def test_sort_radix_variant(dtype, dist):
