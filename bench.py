@@ -53,8 +53,10 @@ def _args():
     p.add_argument("--sweep", action="store_true",
                    help="instead of the headline line: one JSON line per run of the plain-sort "
                         "configurations (u32/u64 x 10 distributions x IPS4o/IPS2Ra at 2^30; "
-                        "f64, Pair and 100-byte records at 2^28), with per-level rooflines and "
-                        "full-size property checks")
+                        "f64, Pair, Quartet and 100-byte records at 2^28), with per-level "
+                        "rooflines and full-size property checks")
+    p.add_argument("--sweep-dtypes", default="u64,u32,f64,pair,quartet,rec100",
+                   help="comma-separated element types the sweep runs")
     p.add_argument("--instrumented", action="store_true",
                    help="run every sort from the host-driven wave loop (the same kernels, no "
                         "CUDA graph): the form the ncu captures in profiles/ use")
@@ -560,6 +562,12 @@ def _keys_sorted(torch, t, dtype, chunk=1 << 27):
             b = x.view(torch.int64)
             k = torch.where(b < 0, ~b, b | (-(1 << 63))) ^ (-(1 << 63))
             ok &= bool((k[1:] >= k[:-1]).all().item())
+        elif dtype == "quartet":  # three unsigned words, lexicographic
+            w = [x[:, j] ^ (-(1 << 63)) for j in range(3)]
+            lt = w[2][1:] < w[2][:-1]
+            for j in (1, 0):
+                lt = (w[j][1:] < w[j][:-1]) | ((w[j][1:] == w[j][:-1]) & lt)
+            ok &= not bool(lt.any().item())
         else:  # rec100: 10-byte big-endian unsigned keys, compared bytewise
             kb = x[:, :10].to(torch.int64)
             hi = torch.zeros(kb.shape[0], dtype=torch.int64, device=x.device)
@@ -577,8 +585,8 @@ SWEEP_INT_DISTS = ("uniform", "exponential", "rootdup", "twodup", "eightdup", "a
 
 def run_sweep(args):
     """Plain-sort configurations: every distribution for u32/u64 with both
-    algorithms at 2^30, and f64 / Pair / 100-byte records at 2^28 with
-    IPS4o; one JSON line each.  Every run is checked at full size by
+    algorithms at 2^30, and f64 / Pair / Quartet / 100-byte records at 2^28
+    with IPS4o; one JSON line each.  Every run is checked at full size by
     properties: keys non-decreasing and the multiset of words unchanged."""
     import torch
     import __graft_entry__ as entry
@@ -588,22 +596,24 @@ def run_sweep(args):
     peak, _ = _peak_hbm()
     stream = torch.cuda.Stream(dev)
     runs = []
+    want = set(args.sweep_dtypes.split(","))
     for dtype in ("u64", "u32"):
         for dist in SWEEP_INT_DISTS:
             for algo in (ipsgpu.SAMPLESORT, ipsgpu.RADIX):
                 runs.append((dtype, dist, algo, 30))
     for dtype, dists in (("f64", inputs.F64_DISTS), ("pair", ("uniform",)),
-                         ("rec100", inputs.REC_DISTS)):
+                         ("quartet", ("uniform", "lexdup")), ("rec100", inputs.REC_DISTS)):
         for dist in dists:
             runs.append((dtype, dist, ipsgpu.SAMPLESORT, 28))
+    runs = [r for r in runs if r[0] in want]
     cur = None
     for dtype, dist, algo, lg in runs:
         n = 1 << lg
         if cur != (dtype, dist, lg):
             src = None
             torch.cuda.empty_cache()
-            if dtype in ("u32", "u64", "pair"):
-                shape = (n, 2) if dtype == "pair" else (n,)
+            if dtype in ("u32", "u64", "pair", "quartet"):
+                shape = {"pair": (n, 2), "quartet": (n, 4)}.get(dtype, (n,))
                 src = torch.empty(shape, dtype=torch.int32 if dtype == "u32" else torch.int64,
                                   device=dev)
                 inputs.generate_into(src, dist, dtype, seed=SEED)

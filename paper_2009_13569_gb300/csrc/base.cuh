@@ -149,27 +149,33 @@ __device__ __forceinline__ void store_unit(unsigned char *dst, const unsigned ch
 //
 // The segment is staged into shared memory through registers, taking the
 // min/max of its radix key on the way.  A pass over a range [a0, a0+len)
-// then counts an MSD radix digit of (key - min) (up to 2^kBaseDigitBits
-// digits, packed 16-bit counters), turns the counts into cursors, and
-// scatters the range by digit from its global copy (which equals the shared
-// one) into shared memory; afterwards the cursor of digit d is the end of
-// its sub-bucket.  Sub-buckets of at most kBaseInsertion elements are
-// finished by insertion sort in shared memory, one thread per sub-bucket;
-// those of at most kBaseSmall elements wait for one warp each once every
-// larger range is done (many of them hold equal keys only); larger ones get
-// another pass (with their own min/max).  Every pass writes
-// its range back to global memory (coalesced), so the global copy of a
-// pending range always matches the shared one.
+// then counts an MSD radix digit of (key - min) (up to 2^DBITS digits,
+// packed 16-bit counters), turns the counts into cursors, and scatters the
+// range by digit from its global copy (which equals the shared one) into
+// shared memory; afterwards the cursor of digit d is the end of its
+// sub-bucket.  Sub-buckets of at most kBaseInsertion elements are finished
+// by insertion sort in shared memory, one thread per sub-bucket; those of at
+// most kBaseSmall elements wait for one warp each once every larger range is
+// done (many of them hold equal keys only); larger ones get another pass
+// (with their own min/max).  Every pass writes its range back to global
+// memory (coalesced), so the global copy of a pending range always matches
+// the shared one.
 template <class T>
 __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
                                                           uint32_t nsegs_host,
                                                           const uint32_t *nsegs_dev, int *status) {
     typedef typename T::E E;
     typedef typename T::K K;
+    // Digits per pass: about two elements per digit for keys up to 8 bytes,
+    // one for wider records (whose insertion-sort moves cost more), at most
+    // 2^14 digits for 4-byte keys and 2^13 otherwise (measured optima) --
+    // unless one digit per key value fits in 2^kBaseDigitBits digits and at
+    // most twice that many: then the pass is final (no insertion sorts)
+    constexpr int DBITS = T::D <= 4 ? kBaseDigitBits : kBaseDigitBits - 1;
+    constexpr uint32_t kPerDigitLog = T::D <= 8 ? 1u : 0u;
     constexpr int ND = 1 << kBaseDigitBits;
     constexpr int NB = T::D <= 8 ? 8 : (T::D <= 16 ? 4 : (T::D <= 32 ? 2 : 1));  // in flight per thread
     constexpr int U = T::D % 16 == 0 ? 16 : (T::D % 8 == 0 ? 8 : 4);  // copy-out unit
-    constexpr int DPT = ND / kBaseThreads;  // digits per thread in the scan
     extern __shared__ __align__(16) unsigned char smem[];
     // layout: buf | stk | sstk | cur (ND/2 words, two 16-bit counters each)
     // | wtmp.  Ranges are < 2^16 elements, so 16-bit counters and cursors
@@ -317,8 +323,9 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
             if (rng == 0) continue;  // all keys equal: the range is final
             const uint32_t nbits = 64 - __clzll((long long)rng);
             uint32_t want = 1;
-            while (want < kBaseDigitBits && (1u << want) < len) want++;
-            const uint32_t dbits = min(nbits, want);
+            while (want < (uint32_t)DBITS && ((1u << kPerDigitLog) << want) < len) want++;
+            const uint32_t dbits =
+                (nbits <= (uint32_t)kBaseDigitBits && nbits <= want + 1) ? nbits : min(nbits, want);
             const uint32_t shift = nbits - dbits;
             const uint32_t nd = 1u << dbits;
             const uint32_t nw = (nd + 1) >> 1;  // counter words in use
@@ -336,18 +343,14 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
             __syncthreads();
             {
                 // exclusive scan of the 16-bit counts; each thread owns a
-                // run of at most DPT consecutive digits of the nd in use and
-                // rewrites them as cursors
-                const uint32_t wpt = (nw + kBaseThreads - 1) / kBaseThreads;  // <= DPT / 2
+                // run of consecutive counter words of the nd digits in use,
+                // sums it, and after the CTA-wide scan rewrites it as cursors
+                const uint32_t wpt = (nw + kBaseThreads - 1) / kBaseThreads;
                 const uint32_t w0 = min(nw, tid * wpt), w1 = min(nw, w0 + wpt);
-                uint32_t cnt[DPT];
                 uint32_t sum = 0;
-#pragma unroll
-                for (int q = 0; q < DPT / 2; q++) {
-                    const uint32_t w = w0 + q < w1 ? cur[w0 + q] : 0u;
-                    cnt[2 * q] = w & 0xFFFFu;
-                    cnt[2 * q + 1] = w >> 16;
-                    sum += cnt[2 * q] + cnt[2 * q + 1];
+                for (uint32_t w = w0; w < w1; w++) {
+                    const uint32_t c2 = cur[w];
+                    sum += (c2 & 0xFFFFu) + (c2 >> 16);
                 }
                 uint32_t x = sum;
                 for (int o = 1; o < 32; o <<= 1) {
@@ -366,11 +369,11 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
                 }
                 __syncthreads();
                 uint32_t run = wtmp[warp] + x - sum;
-#pragma unroll
-                for (int q = 0; q < DPT / 2; q++) {
-                    const uint32_t o0 = run, o1 = run + cnt[2 * q];
-                    run = o1 + cnt[2 * q + 1];
-                    if (w0 + q < w1) cur[w0 + q] = o0 | (o1 << 16);
+                for (uint32_t w = w0; w < w1; w++) {
+                    const uint32_t c2 = cur[w];
+                    const uint32_t o0 = run, o1 = run + (c2 & 0xFFFFu);
+                    run = o1 + (c2 >> 16);
+                    cur[w] = o0 | (o1 << 16);
                 }
             }
             __syncthreads();

@@ -12,11 +12,12 @@ namespace ipsgpu {
 // ---------------------------------------------------------------- limits
 constexpr int kMaxClasses = 256;      // buckets per level incl. equality ones
 // sample keys sorted in one CTA: the largest power of two <= 16384 whose
-// keys fit in 128 KiB (the bitonic sort pads the sample to a power of two)
+// keys fit in 192 KiB (the bitonic sort pads the sample to a power of two):
+// 16384 keys of 4 or 8 bytes, 8192 of 16 or 24 bytes
 template <class K>
 constexpr uint32_t max_sort_sample() {
     uint32_t m = 16384u;
-    while (m > 1 && (uint64_t)m * sizeof(K) > 128u * 1024) m >>= 1;
+    while (m > 1 && (uint64_t)m * sizeof(K) > 192u * 1024) m >>= 1;
     return m;
 }
 constexpr uint32_t kRBias = 1u << 30; // bias of the read pointer field

@@ -17,10 +17,11 @@ pytestmark = pytest.mark.gpu
     ("u64", "uniform", 30, ipsgpu.RADIX),
     ("u32", "exponential", 30, ipsgpu.SAMPLESORT),
     ("pair", "zipf", 28, ipsgpu.SAMPLESORT),
+    ("quartet", "lexdup", 28, ipsgpu.SAMPLESORT),
 ])
 def test_full_size_sort_properties(dtype, dist, log2n, algo):
     n = 1 << log2n
-    shape = (n, 2) if dtype == "pair" else (n,)
+    shape = {"pair": (n, 2), "quartet": (n, 4)}.get(dtype, (n,))
     d = torch.empty(shape, dtype=torch.int32 if dtype == "u32" else torch.int64, device=DEV)
     inputs.generate_into(d, dist, dtype, seed=0x5EED)
     before = multiset_sig(d)
