@@ -185,20 +185,22 @@ struct TQuartet {
 };
 
 // The first element of a block held by a warp, 16 bytes per lane (lane 0's
-// bytes, and lane 1's where the key reaches past them).  Every lane calls it;
-// lane 0's result is the element.
+// bytes, and lane 1's where the key reaches past them), broadcast: every
+// lane calls it and gets the element.
+__device__ __forceinline__ uint4 shfl_uint4(const uint4 &r, int src) {
+    uint4 x;
+    x.x = __shfl_sync(0xffffffffu, r.x, src);
+    x.y = __shfl_sync(0xffffffffu, r.y, src);
+    x.z = __shfl_sync(0xffffffffu, r.z, src);
+    x.w = __shfl_sync(0xffffffffu, r.w, src);
+    return x;
+}
 template <class T>
 __device__ __forceinline__ typename T::E block_head(const uint4 &r) {
-    if constexpr (T::kHeadLanes == 2) {
-        uint4 r1;
-        r1.x = __shfl_sync(0xffffffffu, r.x, 1);
-        r1.y = __shfl_sync(0xffffffffu, r.y, 1);
-        r1.z = __shfl_sync(0xffffffffu, r.z, 1);
-        r1.w = __shfl_sync(0xffffffffu, r.w, 1);
-        return T::head2(r, r1);
-    } else {
-        return T::head(r);
-    }
+    if constexpr (T::kHeadLanes == 2)
+        return T::head2(shfl_uint4(r, 0), shfl_uint4(r, 1));
+    else
+        return T::head(shfl_uint4(r, 0));
 }
 
 // ------------------------------------------------------------ level layouts

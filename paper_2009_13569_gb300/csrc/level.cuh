@@ -48,6 +48,33 @@ struct LevelClassifier {
         if (radix) return (uint32_t)((T::rkey(e) >> shift) & mask);
         return classify_key<K>(T::key(e), tree, spl, logK, eq);
     }
+    // The same class computed by a whole warp (every lane passes the same
+    // element and gets the class), in two vote steps instead of logK
+    // dependent tree steps.  The class index is the number of padded
+    // splitters s_0..s_{K-2} below the key.  For K <= 32 those are exactly
+    // the tree nodes 1..K-1; for K > 32 the tree's top nodes 1..31 are the
+    // splitters s_{S m - 1} (m = 1..31, S = K / 32) that close each group of
+    // S consecutive splitters, so the first vote counts the groups entirely
+    // below the key and the second counts inside the next group.
+    __device__ __forceinline__ uint32_t warp_class(const E &e, int lane) const {
+        if (radix) return (uint32_t)((T::rkey(e) >> shift) & mask);
+        const K k = T::key(e);
+        const uint32_t nk = 1u << logK;
+        uint32_t i;
+        if (nk <= 32) {
+            const bool below = lane >= 1 && (uint32_t)lane < nk && tree[lane] < k;
+            i = __popc(__ballot_sync(0xffffffffu, below));
+        } else {
+            const uint32_t S = nk >> 5;
+            const bool below = lane >= 1 && tree[lane] < k;
+            const uint32_t q = __popc(__ballot_sync(0xffffffffu, below));
+            const uint32_t j = q * S + (uint32_t)lane;
+            const bool below2 = (uint32_t)lane < S && j < nk - 1 && spl[j] < k;
+            i = q * S + __popc(__ballot_sync(0xffffffffu, below2));
+        }
+        if (eq) i = 2 * i + 1 - (k < spl[i] ? 1u : 0u);
+        return i;
+    }
 };
 
 template <class T>
@@ -534,10 +561,7 @@ __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a) {
                 }
                 if (!got) break;
                 scanned = 0;
-                uint32_t tt = 0;
-                const E ha = block_head<T>(A);
-                if (lane == 0) tt = cl(ha);
-                t = __shfl_sync(0xffffffffu, tt, 0);
+                t = cl.warp_class(block_head<T>(A), lane);
                 hold = true;
             }
             // place the held block into bucket t
@@ -560,10 +584,7 @@ __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a) {
             }
             if (unproc) {
                 warp_load_block(Bk, base + (uint64_t)slot * BB, BB, lane, u);
-                uint32_t t2 = 0;
-                const E hb = block_head<T>(Bk);
-                if (lane == 0) t2 = cl(hb);
-                t2 = __shfl_sync(0xffffffffu, t2, 0);
+                const uint32_t t2 = cl.warp_class(block_head<T>(Bk), lane);
                 if (t2 == t) continue;  // already in place: w moved past it
                 warp_store_block(A, base + (uint64_t)slot * BB, BB, lane, u);
                 A = Bk;
