@@ -57,6 +57,10 @@ def _args():
                         "rooflines and full-size property checks")
     p.add_argument("--sweep-dtypes", default="u64,u32,f64,pair,quartet,rec100",
                    help="comma-separated element types the sweep runs")
+    p.add_argument("--sweep-algos", default="IPS4o,IPS2Ra",
+                   help="comma-separated algorithms the sweep runs: IPS4o, IPS2Ra (u32/u64 "
+                        "only) and IPS4o-tree (IPS4o walking every element from the tree's "
+                        "root, without the start-node table)")
     p.add_argument("--instrumented", action="store_true",
                    help="run every sort from the host-driven wave loop (the same kernels, no "
                         "CUDA graph): the form the ncu captures in profiles/ use")
@@ -579,6 +583,9 @@ def _keys_sorted(torch, t, dtype, chunk=1 << 27):
     return ok
 
 
+ALGO_CODES = {"IPS4o": 0, "IPS2Ra": 1, "IPS4o-tree": 2}  # ipsgpu_algo values
+ALGO_NAMES = {v: k for k, v in ALGO_CODES.items()}
+
 SWEEP_INT_DISTS = ("uniform", "exponential", "rootdup", "twodup", "eightdup", "almostsorted",
                    "zipf", "sorted", "reversesorted", "zero")
 
@@ -597,14 +604,17 @@ def run_sweep(args):
     stream = torch.cuda.Stream(dev)
     runs = []
     want = set(args.sweep_dtypes.split(","))
+    algos = [ALGO_CODES[a] for a in args.sweep_algos.split(",")]
     for dtype in ("u64", "u32"):
         for dist in SWEEP_INT_DISTS:
-            for algo in (ipsgpu.SAMPLESORT, ipsgpu.RADIX):
+            for algo in algos:
                 runs.append((dtype, dist, algo, 30))
     for dtype, dists in (("f64", inputs.F64_DISTS), ("pair", ("uniform",)),
                          ("quartet", ("uniform", "lexdup")), ("rec100", inputs.REC_DISTS)):
         for dist in dists:
-            runs.append((dtype, dist, ipsgpu.SAMPLESORT, 28))
+            for algo in algos:
+                if algo != ipsgpu.RADIX:
+                    runs.append((dtype, dist, algo, 28))
     runs = [r for r in runs if r[0] in want]
     cur = None
     for dtype, dist, algo, lg in runs:
@@ -649,7 +659,7 @@ def run_sweep(args):
         med = statistics.median(times)
         lv = level_roofline(stats, peak, D, n)
         line = {"sweep": True, "dtype": dtype, "dist": dist, "n": n,
-                "algo": "IPS2Ra" if algo == ipsgpu.RADIX else "IPS4o",
+                "algo": ALGO_NAMES[algo],
                 "value": n / (med * 1e-3) / 1e9, "unit": UNIT, "ms_median": med,
                 "ms_mean": statistics.mean(times), "runs": len(times),
                 "level_roofline": lv,

@@ -60,8 +60,16 @@ typedef enum {
 
 /* Classifier of the partitioning step: the branchless splitter tree of IPS4o
  * (Sec. 2, Algorithm 1) or the radix extractor of IPS2Ra (Sec. 5; U32, U64
- * and PAIR_U64 keys only). */
-typedef enum { IPSGPU_SAMPLESORT = 0, IPSGPU_RADIX = 1 } ipsgpu_algo;
+ * and PAIR_U64 keys only).  SAMPLESORT starts each element's tree walk from
+ * a lookup table of start nodes addressed by the key's leading bits (the
+ * table Sec. 8 proposes); SAMPLESORT_TREE walks every element from the root
+ * as Algorithm 1 does.  Both give identical classes and results;
+ * SAMPLESORT_TREE exists to measure the table. */
+typedef enum {
+    IPSGPU_SAMPLESORT = 0,
+    IPSGPU_RADIX = 1,
+    IPSGPU_SAMPLESORT_TREE = 2
+} ipsgpu_algo;
 
 enum {
     IPSGPU_OK = 0,

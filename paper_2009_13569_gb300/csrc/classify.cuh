@@ -268,7 +268,8 @@ __device__ uint32_t cell_entry(const CellMap &cm, uint32_t c, bool single,
 
 template <class T>
 __device__ void build_start_table(uint32_t *tab, CellMap &cm, const typename T::K *tree,
-                                  const typename T::K *spl, uint32_t nleaves, uint32_t logK) {
+                                  const typename T::K *spl, uint32_t nleaves, uint32_t logK,
+                                  bool tree_only) {
     const uint64_t lo = rk_of_key<T>(spl[0]);
     const uint64_t hi = rk_of_key<T>(spl[nleaves - 1]);
     const uint64_t range = hi - lo;
@@ -294,8 +295,10 @@ __device__ void build_start_table(uint32_t *tab, CellMap &cm, const typename T::
     const int n_lin = __syncthreads_count(walk_lin);
     const int n_lg = __syncthreads_count(walk_lg);
     cm = (!single && n_lg < n_lin) ? lg : lin;
+    // tree_only: every cell starts the walk at the root (Algorithm 1 as printed)
     for (uint32_t c = threadIdx.x; c < (uint32_t)kCells; c += blockDim.x)
-        tab[c] = cell_entry<T>(cm, c, single, tree, spl, nleaves, logK);
+        tab[c] = tree_only ? (0x80000000u | 1u)
+                           : cell_entry<T>(cm, c, single, tree, spl, nleaves, logK);
 }
 
 // Classify EPT keys: the table gives the class index directly or after at
@@ -438,7 +441,7 @@ __global__ void __launch_bounds__(ClsCfg<T>::NT, 1) k_classify(LevelArgs a) {
                   (uint32_t)min((uint64_t)TILE, e1 - e0) * T::D, &sh_bar);
     if (!cl.radix) {
         CellMap cm;
-        build_start_table<T>(tab, cm, s_tree, s_spl, st.K, st.logK);
+        build_start_table<T>(tab, cm, s_tree, s_spl, st.K, st.logK, a.tree_only != 0);
         if (tid == 0) sh_cm = cm;
     }
 

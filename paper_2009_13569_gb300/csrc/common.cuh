@@ -306,7 +306,7 @@ struct LevelArgs {
     const uint32_t *cta_seg;
     const uint32_t *stripe_first;  // balanced waves: first stripe of each part
     uint32_t spin_limit;
-    uint32_t pad;
+    uint32_t tree_only;       // classification walks every element from the tree's root
     uint64_t seed;
     float alpha_scale;
     uint32_t pad2;

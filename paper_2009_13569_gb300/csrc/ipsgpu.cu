@@ -86,7 +86,9 @@ int resolve(const ipsgpu_params *p, int dtype, Resolved *r) {
     if (b == 0 || (uint64_t)b * ops->D * r->k > 160u * 1024 || (b * ops->D) % 16) return IPSGPU_E_INVAL;
     // the arena holds at least one segment with one stripe of k classes
     if (r->arena_bytes < 2ull * r->k * b * ops->D + (uint64_t)b * ops->D + 1024) return IPSGPU_E_INVAL;
-    if (r->algo != IPSGPU_SAMPLESORT && r->algo != IPSGPU_RADIX) return IPSGPU_E_INVAL;
+    if (r->algo != IPSGPU_SAMPLESORT && r->algo != IPSGPU_RADIX &&
+        r->algo != IPSGPU_SAMPLESORT_TREE)
+        return IPSGPU_E_INVAL;
     if (r->algo == IPSGPU_RADIX &&
         !(dtype == IPSGPU_U32 || dtype == IPSGPU_U64 || dtype == IPSGPU_PAIR_U64))
         return IPSGPU_E_UNSUPPORTED;
@@ -522,6 +524,7 @@ LevelArgs Sorter::args(uint32_t nseg, uint32_t nstripe, uint32_t ncta, uint32_t 
     a.cnt = nullptr;
     a.cta_seg = d_cta_seg;
     a.spin_limit = spin_limit;
+    a.tree_only = algo == IPSGPU_SAMPLESORT_TREE ? 1u : 0u;
     a.seed = seed;
     a.alpha_scale = alpha_scale;
     return a;

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(_PKG, "libipsgpu.so")
 
 DTYPES = {"u32": 0, "u64": 1, "f64": 2, "pair": 3, "rec100": 4, "quartet": 5}
 ELEM_BYTES = {"u32": 4, "u64": 8, "f64": 8, "pair": 16, "rec100": 100, "quartet": 32}
-SAMPLESORT, RADIX = 0, 1
+SAMPLESORT, RADIX, SAMPLESORT_TREE = 0, 1, 2
 
 OK, E_INVAL, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY, E_INTERNAL = range(8)
 

@@ -44,6 +44,8 @@ def test_strerror_and_scratch_bytes(lib):
     assert ipsgpu.scratch_bytes("f64", algo=ipsgpu.RADIX) == 0
     assert ipsgpu.scratch_bytes("u64", k=3) == 0
     assert ipsgpu.scratch_bytes("quartet") > 0
+    assert ipsgpu.scratch_bytes("u64", algo=ipsgpu.SAMPLESORT_TREE) == b64
+    assert ipsgpu.scratch_bytes("u64", algo=3) == 0
     assert ipsgpu.scratch_bytes("quartet", algo=ipsgpu.RADIX) == 0
     assert ipsgpu.scratch_bytes("rec100", algo=ipsgpu.RADIX) == 0
 

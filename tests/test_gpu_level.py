@@ -32,7 +32,7 @@ def _splitters(host, dtype, m, seed):
     return oracle.sort(pick, dtype)
 
 
-def _run_level(dtype, host, spl, eq, offset=0):
+def _run_level(dtype, host, spl, eq, offset=0, **params):
     n = inputs.count(host, dtype) - offset
     d = to_dev(host)
     dv = d[offset:]
@@ -40,7 +40,7 @@ def _run_level(dtype, host, spl, eq, offset=0):
     K = 1 << int(np.ceil(np.log2(len(spl) + 1)))
     B = 2 * K if eq else K
     bb = torch.zeros(B + 1, dtype=torch.int64, device=DEV)
-    with ipsgpu.Sorter(dtype) as s:
+    with ipsgpu.Sorter(dtype, **params) as s:
         s.partition_level(dv.data_ptr(), n, sd.data_ptr(), len(spl), eq, bb.data_ptr(), stream())
         st = s.status(stream())
     assert st == ipsgpu.OK, ipsgpu.strerror(st)
@@ -62,6 +62,16 @@ def test_partition_level_parity(dtype, m, eq, dist):
     host = _input(dtype, n, dist)
     spl = _splitters(host, dtype, m, seed=m)
     _run_level(dtype, host, spl, eq)
+
+
+@pytest.mark.parametrize("dtype", ["u64", "f64", "quartet"])
+@pytest.mark.parametrize("m,eq", [(5, False), (255, False), (127, True)])
+def test_partition_level_tree_walk_classifier(dtype, m, eq):
+    # the classifier without the start-node table (every element walks from
+    # the root, as Algorithm 1) gives the same level
+    host = _input(dtype, 150_001, "twodup" if eq else "uniform", seed=m)
+    spl = _splitters(host, dtype, m, seed=3 * m)
+    _run_level(dtype, host, spl, eq, algo=ipsgpu.SAMPLESORT_TREE)
 
 
 @pytest.mark.parametrize("dtype", ["u32", "u64", "pair"])

@@ -76,6 +76,14 @@ def test_sort_quartet_small_base_case(base_case, dist):
     assert_sorted_parity(got, inputs.to_numpy(host, "quartet"), "quartet")
 
 
+@pytest.mark.parametrize("dtype,dist", [("u64", "uniform"), ("u64", "exponential"), ("u32", "twodup"),
+                                        ("f64", "normal"), ("pair", "zipf"), ("quartet", "lexdup")])
+def test_sort_tree_walk_classifier(dtype, dist):
+    host = inputs.generate(dist, dtype, N)
+    got = run_sort(dtype, host, algo=ipsgpu.SAMPLESORT_TREE)
+    assert_sorted_parity(got, inputs.to_numpy(host, dtype), dtype)
+
+
 def test_quartet_radix_unsupported():
     with pytest.raises(ipsgpu.IpsgpuError) as e:
         ipsgpu.Sorter("quartet", algo=ipsgpu.RADIX)
