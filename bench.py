@@ -164,9 +164,15 @@ class ClockSampler:
 # the kernel source it was measured on, identified by its sha256; otherwise
 # the bench reports traffic as null.
 NCU_TRAFFIC = {
-    "classify": {"bytes_per_elem": 15.157,
+    "classify": {"bytes_per_elem": 15.16,
                  "source": "paper_2009_13569_gb300/csrc/classify.cuh",
-                 "sha256": "ad3c4b3475278f8ca8b52f4b89060396c47f7c3572dc212f012b0fe0481a8f06"},
+                 "sha256": "217f874a56bbf29af09547ba7213c038d224373a19cf2c3dc7a115bbb5be36ef"},
+    "permute": {"bytes_per_elem": 14.79,
+                "source": "paper_2009_13569_gb300/csrc/level.cuh",
+                "sha256": "804a39a9b6b6a00b753f9db58c3ea9a51846fa7cc977fdf0222420958c96c93c"},
+    "base_case": {"bytes_per_elem": 15.10,
+                  "source": "paper_2009_13569_gb300/csrc/base.cuh",
+                  "sha256": "c3e034fc3bf68f743fe8b4fdd4d89f712152ff2f1af49a634bb2185f108073e6"},
 }
 
 def _traffic(kernel, elems_per_launch):
