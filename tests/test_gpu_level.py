@@ -151,6 +151,17 @@ def test_invalid_arguments_are_rejected():
         assert e.value.code == ipsgpu.E_INVAL  # 2 * 256 classes > k
         with pytest.raises(ipsgpu.IpsgpuError):
             s.partition_level(d.data_ptr() + 4, 8, d.data_ptr(), 3, False, bb.data_ptr())
+        with pytest.raises(ipsgpu.IpsgpuError) as e:
+            s.partition_level(d.data_ptr(), 8, d.data_ptr() + 4, 3, False, bb.data_ptr())
+        assert e.value.code == ipsgpu.E_INVAL  # misaligned splitters
+        out = torch.zeros(16, dtype=torch.int32, device=DEV)
+        with pytest.raises(ipsgpu.IpsgpuError) as e:
+            s.classify(d.data_ptr(), 8, d.data_ptr() + 4, 3, False, out.data_ptr())
+        assert e.value.code == ipsgpu.E_INVAL
+    with ipsgpu.Sorter("quartet") as s:
+        with pytest.raises(ipsgpu.IpsgpuError) as e:
+            s.partition_level(d.data_ptr() + 8, 2, d.data_ptr(), 1, False, bb.data_ptr())
+        assert e.value.code == ipsgpu.E_INVAL  # quartets need 16-byte alignment
     with pytest.raises(ipsgpu.IpsgpuError) as e:
         ipsgpu.Sorter("f64", algo=ipsgpu.RADIX)
     assert e.value.code == ipsgpu.E_UNSUPPORTED

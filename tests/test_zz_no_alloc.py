@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _rows(a, dtype):
-    if dtype in ("pair", "rec100"):
+    if dtype in ("pair", "rec100", "quartet"):
         v = np.ascontiguousarray(a).view(np.uint8).reshape(len(a), -1)
         return v[np.lexsort(v.T[::-1])]
     return np.sort(a)
@@ -31,6 +31,8 @@ def _rows(a, dtype):
     ("u64", 1_000_003, 255, False, "uniform"),
     ("u32", 300_001, 127, True, "twodup"),
     ("pair", 200_003, 63, False, "uniform"),
+    ("quartet", 150_001, 127, True, "lexdup"),
+    ("f64", 250_001, 100, False, "normal"),
 ])
 def test_noalloc_matches_sorter_level_twice(dtype, n, m, eq, dist):
     dev = torch.device("cuda:0")
@@ -63,6 +65,15 @@ def test_noalloc_matches_sorter_level_twice(dtype, n, m, eq, dist):
             lo, hi = int(bbn[j]), int(bbn[j + 1])
             if hi > lo:
                 np.testing.assert_array_equal(_rows(g[lo:hi], dtype), _rows(r[lo:hi], dtype))
+
+
+def test_noalloc_rejects_misaligned_splitters():
+    d = torch.zeros(64, dtype=torch.int64, device="cuda:0")
+    bb = torch.zeros(9, dtype=torch.int64, device="cuda:0")
+    with pytest.raises(ipsgpu.IpsgpuError) as e:
+        ipsgpu.partition_level_noalloc("quartet", d.data_ptr(), 8, d.data_ptr() + 8, 3, False,
+                                       bb.data_ptr())
+    assert e.value.code == ipsgpu.E_INVAL
 
 
 def test_noalloc_rejects_too_many_classes():
