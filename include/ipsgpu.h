@@ -142,6 +142,20 @@ uint64_t ipsgpu_scratch_bytes(const ipsgpu_params *params, int dtype);
  * Errors: E_INVAL, E_CUDA; kernel-side errors via ipsgpu_status. */
 int ipsgpu_sort(ipsgpu_sorter *s, void *d_data, uint64_t n, void *stream);
 
+/* Sort an array that lives in HOST memory: copy h_in[0..n) to the device
+ * buffer d_work (n elements, caller-owned, aligned like d_data above), sort
+ * it there as ipsgpu_sort does, and copy the result to h_out[0..n) (h_out
+ * may equal h_in).  All three steps are queued on `stream` and the call
+ * returns at once when the host buffers are page-locked (cudaHostAlloc /
+ * cudaHostRegister); with pageable buffers the CUDA runtime stages the
+ * copies and the call may block.  Independent sorts issued this way on two
+ * streams (each with its own sorter and d_work) overlap one sort's copies
+ * with the other's kernels.
+ * Errors: E_INVAL (NULL or misaligned pointers), E_CUDA; kernel-side errors
+ * via ipsgpu_status. */
+int ipsgpu_sort_host(ipsgpu_sorter *s, const void *h_in, void *h_out, uint64_t n, void *d_work,
+                     void *stream);
+
 /* One partitioning step with given splitters (Sec. 3.1.2 - 3.1.4): classify
  * every element with the branchless tree over the sorted splitters
  * d_splitters[0..num_splitters) (elements of the sorter's dtype, only their

@@ -676,6 +676,21 @@ int ipsgpu_sort(ipsgpu_sorter *h, void *d_data, uint64_t n, void *stream) {
     return sort_impl(h->s, (unsigned char *)d_data, n, (cudaStream_t)stream);
 }
 
+int ipsgpu_sort_host(ipsgpu_sorter *h, const void *h_in, void *h_out, uint64_t n, void *d_work,
+                     void *stream) {
+    if (!h || !h_in || !h_out) return IPSGPU_E_INVAL;
+    if (n == 0) return IPSGPU_OK;
+    Sorter &s = h->s;
+    int rc = check_data(s, d_work);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)n * s.ops->D;
+    if (cudaMemcpyAsync(d_work, h_in, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return IPSGPU_E_CUDA;
+    if ((rc = sort_impl(s, (unsigned char *)d_work, n, st))) return rc;
+    return cuda_status(cudaMemcpyAsync(h_out, d_work, bytes, cudaMemcpyDeviceToHost, st));
+}
+
 int ipsgpu_partition_level(ipsgpu_sorter *h, void *d_data, uint64_t n, const void *d_splitters,
                            uint32_t num_splitters, int equal_buckets, uint64_t *d_bucket_begin,
                            void *stream) {

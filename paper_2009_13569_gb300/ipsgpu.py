@@ -55,6 +55,7 @@ def load():
         "ipsgpu_sorter_destroy": (i32, [vp]),
         "ipsgpu_scratch_bytes": (u64, [ctypes.POINTER(Params), i32]),
         "ipsgpu_sort": (i32, [vp, vp, u64, vp]),
+        "ipsgpu_sort_host": (i32, [vp, vp, vp, u64, vp, vp]),
         "ipsgpu_partition_level": (i32, [vp, vp, u64, vp, u32, i32, vp, vp]),
         "ipsgpu_radix_level": (i32, [vp, vp, u64, u32, u32, vp, vp]),
         "ipsgpu_classify": (i32, [vp, vp, u64, vp, u32, i32, vp, vp]),
@@ -102,6 +103,7 @@ def exported_symbols():
     """Names of the C-ABI functions this binding declares."""
     return [
         "ipsgpu_sorter_create", "ipsgpu_sorter_destroy", "ipsgpu_scratch_bytes", "ipsgpu_sort",
+        "ipsgpu_sort_host",
         "ipsgpu_partition_level", "ipsgpu_radix_level", "ipsgpu_classify", "ipsgpu_status",
         "ipsgpu_strerror", "ipsgpu_set_timing", "ipsgpu_kernel_stats", "ipsgpu_kernel_name",
         "ipsgpu_debug_bounded_wait", "ipsgpu_partition_level_noalloc", "ipsgpu_sort_segmented",
@@ -178,6 +180,12 @@ class Sorter:
 
     def sort(self, ptr, n, stream=0):
         _check(load().ipsgpu_sort(self._h, ptr, n, stream), "ipsgpu_sort")
+
+    def sort_host(self, in_ptr, out_ptr, n, work_ptr, stream=0):
+        """Host array in (in_ptr), sorted result out (out_ptr, may equal
+        in_ptr), through the device buffer work_ptr; queued on stream."""
+        _check(load().ipsgpu_sort_host(self._h, in_ptr, out_ptr, n, work_ptr, stream),
+               "ipsgpu_sort_host")
 
     def sort_segmented(self, ptr, n, offsets_ptr, num_segments, stream=0):
         """Sort segments [offsets[i], offsets[i+1]) of the n-element array in

@@ -84,6 +84,53 @@ def test_sort_tree_walk_classifier(dtype, dist):
     assert_sorted_parity(got, inputs.to_numpy(host, dtype), dtype)
 
 
+@pytest.mark.parametrize("dtype", ["u64", "quartet"])
+def test_sort_host_pinned_and_pageable(dtype):
+    host = inputs.generate("uniform", dtype, 200_003, seed=8)
+    inp = inputs.to_numpy(host, dtype)
+    n = host.shape[0]
+    pinned = host.pin_memory()
+    out = torch.empty_like(host).pin_memory()
+    work = torch.empty_like(host, device=DEV)
+    with ipsgpu.Sorter(dtype) as s:
+        s.sort_host(pinned.data_ptr(), out.data_ptr(), n, work.data_ptr(), stream())
+        assert s.status(stream()) == ipsgpu.OK  # synchronizes the stream
+        assert_sorted_parity(inputs.to_numpy(out, dtype), inp, dtype)
+        assert torch.equal(pinned, host)  # the input is left as it was
+        pageable = host.clone()  # pageable, sorted in place
+        s.sort_host(pageable.data_ptr(), pageable.data_ptr(), n, work.data_ptr(), stream())
+        assert s.status(stream()) == ipsgpu.OK
+        assert_sorted_parity(inputs.to_numpy(pageable, dtype), inp, dtype)
+        with pytest.raises(ipsgpu.IpsgpuError):
+            s.sort_host(0, out.data_ptr(), n, work.data_ptr(), stream())
+        with pytest.raises(ipsgpu.IpsgpuError):
+            s.sort_host(pinned.data_ptr(), out.data_ptr(), n, work.data_ptr() + 4, stream())
+
+
+def test_sort_host_two_streams_overlapped():
+    # two sorters on two streams, each with its own device buffer, issued
+    # back to back: the results are each the oracle's
+    hosts = [inputs.generate(d, "u64", 1_000_003, seed=31 + i)
+             for i, d in enumerate(("uniform", "twodup", "zipf", "exponential"))]
+    pins = [h.pin_memory() for h in hosts]
+    outs = [torch.empty_like(h).pin_memory() for h in hosts]
+    works = [torch.empty_like(hosts[0], device=DEV) for _ in range(2)]
+    streams = [torch.cuda.Stream(DEV) for _ in range(2)]
+    sorters = [ipsgpu.Sorter("u64") for _ in range(2)]
+    try:
+        for i in range(len(hosts)):
+            j = i % 2
+            sorters[j].sort_host(pins[i].data_ptr(), outs[i].data_ptr(), hosts[i].shape[0],
+                                 works[j].data_ptr(), streams[j].cuda_stream)
+        for j in range(2):
+            assert sorters[j].status(streams[j].cuda_stream) == ipsgpu.OK
+    finally:
+        for s in sorters:
+            s.close()
+    for h, o in zip(hosts, outs):
+        assert_sorted_parity(inputs.to_numpy(o, "u64"), inputs.to_numpy(h, "u64"), "u64")
+
+
 def test_quartet_radix_unsupported():
     with pytest.raises(ipsgpu.IpsgpuError) as e:
         ipsgpu.Sorter("quartet", algo=ipsgpu.RADIX)
