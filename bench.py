@@ -589,6 +589,8 @@ def _keys_sorted(torch, t, dtype, chunk=1 << 27):
     return ok
 
 
+E2E_LANES = 3  # streams (each with a sorter and a device buffer) of the end-to-end run
+
 ALGO_CODES = {"IPS4o": 0, "IPS2Ra": 1, "IPS4o-tree": 2}  # ipsgpu_algo values
 ALGO_NAMES = {v: k for k, v in ALGO_CODES.items()}
 
@@ -808,40 +810,43 @@ def run_ours(args):
         # end to end through the public API (ipsgpu_sort_host): every step
         # copies its input from pinned host memory to the device, sorts it
         # and copies the result back to pinned host memory, all inside the
-        # timed region.  Steps alternate between two streams, each with its
-        # own sorter and device buffer, so one step's copies overlap the
-        # other's kernels (the host link is full duplex).  The same steps on
-        # one stream, one after another, are reported as `sequential`.
+        # timed region.  Steps go round-robin over E2E_LANES streams, each
+        # with its own sorter and device buffer, so the host->device copy of
+        # one step, the kernels of another and the device->host copy of a
+        # third run at once (the host link is full duplex).  The same steps
+        # on one stream, one after another, are reported as `sequential`.
         hsrc = src.cpu().pin_memory()
-        hdst = [torch.empty_like(hsrc).pin_memory() for _ in range(2)]
-        work2 = torch.empty_like(work)
-        sorter2 = ipsgpu.Sorter("u64")
-        sorter2.prepare()
-        streams = [stream, torch.cuda.Stream(dev)]
-        sorters, works = [sorter, sorter2], [work, work2]
+        hdst = [torch.empty_like(hsrc).pin_memory() for _ in range(E2E_LANES)]
+        works = [work] + [torch.empty_like(work) for _ in range(E2E_LANES - 1)]
+        sorters = [sorter] + [ipsgpu.Sorter("u64") for _ in range(E2E_LANES - 1)]
+        for s_ in sorters[1:]:
+            s_.prepare()
+        streams = [stream] + [torch.cuda.Stream(dev) for _ in range(E2E_LANES - 1)]
 
-        def e2e_steps(k, overlap):
+        def e2e_steps(k, lanes):
             barrier()
             t0 = torch.cuda.Event(enable_timing=True)
             t1 = torch.cuda.Event(enable_timing=True)
-            join = torch.cuda.Event()
             t0.record(streams[0])
-            streams[1].wait_event(t0)
+            for st_ in streams[1:]:
+                st_.wait_event(t0)
             for i in range(k):
-                j = i % 2 if overlap else 0
+                j = i % lanes
                 sorters[j].sort_host(hsrc.data_ptr(), hdst[j].data_ptr(), n, works[j].data_ptr(),
                                      streams[j].cuda_stream)
-            join.record(streams[1])
-            streams[0].wait_event(join)
+            for st_ in streams[1:]:
+                join = torch.cuda.Event()
+                join.record(st_)
+                streams[0].wait_event(join)
             t1.record(streams[0])
             streams[0].synchronize()
             return t0.elapsed_time(t1) / k
 
-        e2e_steps(2, True)  # warm-up of both sorters and the copy paths
-        ems = e2e_steps(args.steps, True)
-        sms = e2e_steps(args.steps, False)
+        e2e_steps(E2E_LANES, E2E_LANES)  # warm-up of every sorter and the copy paths
+        ems = e2e_steps(args.steps, E2E_LANES)
+        sms = e2e_steps(args.steps, 1)
         eok = all(s_.status(st_.cuda_stream) == ipsgpu.OK for s_, st_ in zip(sorters, streams))
-        for h in hdst:  # both result buffers checked on the device
+        for h in hdst:  # every result buffer checked on the device
             work.copy_(h)
             eok = eok and bool(((work[1:] ^ sgn) >= (work[:-1] ^ sgn)).all().item())
         if pg:
@@ -850,13 +855,14 @@ def run_ours(args):
             ems, sms = float(t[0]), float(t[1])
         e2e = {"value": world * n / (ems * 1e-3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8, "ms_per_step": ems,
-               "form": "ipsgpu_sort_host, pinned host buffers, steps alternating over two "
-                       "streams (copies of one step overlap the other's kernels)",
+               "form": "ipsgpu_sort_host, pinned host buffers, steps round-robin over %d "
+                       "streams (copies of some steps overlap the kernels of others)" % E2E_LANES,
                "sequential": {"value": world * n / (sms * 1e-3) / 1e9, "ms_per_step": sms,
                               "form": "the same steps on one stream, one after another"},
                "result_sorted": eok}
-        sorter2.close()
-        del hsrc, hdst, work2
+        for s_ in sorters[1:]:
+            s_.close()
+        del hsrc, hdst, works
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
