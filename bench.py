@@ -67,6 +67,25 @@ def _args():
     return p.parse_args()
 
 
+def reduce_max_over_ranks(pg, values, device="cpu"):
+    """Element-wise maximum over all ranks of a list of floats (the slowest
+    rank's time, any rank's failure flag); every rank gets the result.  With
+    no process group (one GPU) the values come back unchanged."""
+    vals = [float(v) for v in values]
+    if not pg:
+        return vals
+    import torch
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def replica_value(world, n, ms):
+    """Whole-job throughput (Gelem/s) of `world` replicas that each sort n
+    elements per step, the step taking the slowest rank's ms."""
+    return world * n / (ms * 1e-3) / 1e9
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -750,12 +769,9 @@ def run_ours(args):
     sgn = -(1 << 63)
     ok = bool(((work[1:] ^ sgn) >= (work[:-1] ^ sgn)).all().item()) and st == ipsgpu.OK
     ms = sum(times) / len(times)
-    if pg:
-        t = torch.tensor([ms, 0.0 if ok else 1.0], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms, bad = float(t[0]), float(t[1])
-        ok = bad == 0.0
-    value = world * n / (ms * 1e-3) / 1e9
+    ms, bad = reduce_max_over_ranks(pg, [ms, 0.0 if ok else 1.0], dev)
+    ok = bad == 0.0
+    value = replica_value(world, n, ms)
 
     # roofline of the dominant kernel (algorithmic bytes / mean launch time)
     peak, peak_kind = _peak_hbm()
@@ -798,8 +814,10 @@ def run_ours(args):
         rstats = rs.kernel_stats()
         rok = rs.status(stream.cuda_stream) == ipsgpu.OK and bool(
             ((work[1:] ^ sgn) >= (work[:-1] ^ sgn)).all().item())
-        rms = sum(rtimes) / len(rtimes)
-        ips2ra = {"value": world * n / (rms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": rms,
+        rms, rbad = reduce_max_over_ranks(pg, [sum(rtimes) / len(rtimes), 0.0 if rok else 1.0],
+                                          dev)
+        rok = rbad == 0.0
+        ips2ra = {"value": replica_value(world, n, rms), "unit": UNIT, "ms_per_step": rms,
                   "instrumented_ms_per_step": sum(ritimes) / len(ritimes),
                   "level_roofline": level_roofline(rstats, peak, 8, n * args.steps),
                   "result_sorted": rok}
@@ -849,15 +867,13 @@ def run_ours(args):
         for h in hdst:  # every result buffer checked on the device
             work.copy_(h)
             eok = eok and bool(((work[1:] ^ sgn) >= (work[:-1] ^ sgn)).all().item())
-        if pg:
-            t = torch.tensor([ems, sms], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ems, sms = float(t[0]), float(t[1])
-        e2e = {"value": world * n / (ems * 1e-3) / 1e9, "unit": UNIT,
+        ems, sms, ebad = reduce_max_over_ranks(pg, [ems, sms, 0.0 if eok else 1.0], dev)
+        eok = ebad == 0.0
+        e2e = {"value": replica_value(world, n, ems), "unit": UNIT,
                "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8, "ms_per_step": ems,
                "form": "ipsgpu_sort_host, pinned host buffers, steps round-robin over %d "
                        "streams (copies of some steps overlap the kernels of others)" % E2E_LANES,
-               "sequential": {"value": world * n / (sms * 1e-3) / 1e9, "ms_per_step": sms,
+               "sequential": {"value": replica_value(world, n, sms), "ms_per_step": sms,
                               "form": "the same steps on one stream, one after another"},
                "result_sorted": eok}
         for s_ in sorters[1:]:

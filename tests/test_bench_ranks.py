@@ -1,0 +1,82 @@
+"""Host logic of the benchmark's multi-GPU form (replicas: every rank sorts
+its own array, no collective on the data path) on world-size-2 gloo process
+groups on the CPU: the job's time is the slowest rank's, a failure on any
+rank fails the job, the value counts every rank's elements, and the
+reference arm runs on rank 0 only."""
+import io
+import json
+import os
+import socket
+import sys
+from contextlib import redirect_stdout
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    sys.path.insert(0, ROOT)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        ms = [10.0, 25.0][rank]
+        bad = [0.0, 1.0][rank]
+        seq = [40.0, 30.0][rank]
+        out = bench.reduce_max_over_ranks(dist, [ms, seq, bad], "cpu")
+        q.put((rank, out, bench.replica_value(world, 1 << 30, out[0])))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_replica_value_gloo():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    for rank, out, value in got:
+        assert out == [25.0, 40.0, 1.0], rank  # slowest time per field, any failure
+        assert value == pytest.approx(2 * (1 << 30) / 25e-3 / 1e9)
+
+
+def test_reduce_without_process_group_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reduce_max_over_ranks(None, [3, 1.5]) == [3.0, 1.5]
+    assert bench.replica_value(1, 1 << 30, 36.4) == pytest.approx((1 << 30) / 36.4e-3 / 1e9)
+
+
+def test_reference_arm_prints_on_rank_zero_only(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    args = bench.argparse.Namespace(gpus=2, steps=1, warmup=0)
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(args)
+    assert buf.getvalue() == ""  # rank 1: no work, no line
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setattr(bench, "CPU_SAMPLE_LOG2", 14)  # a small sample keeps the test fast
+    with redirect_stdout(buf):
+        bench.run_reference(args)
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle"
