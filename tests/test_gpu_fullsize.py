@@ -30,3 +30,20 @@ def test_full_size_sort_properties(dtype, dist, log2n, algo):
         assert s.status(stream()) == ipsgpu.OK
     assert keys_nondecreasing(d, dtype)
     assert multiset_sig(d) == before
+
+
+@pytest.mark.parametrize("dtype,n,algo", [
+    ("u32", (1 << 32) + 3, ipsgpu.SAMPLESORT),
+    ("u64", (1 << 32) + 1, ipsgpu.RADIX),
+])
+def test_more_than_2_32_elements(dtype, n, algo):
+    # element offsets past 2^32 (16 GiB of u32 keys, 32 GiB of u64 keys):
+    # no index in the path may wrap at 32 bits
+    d = torch.empty((n,), dtype=torch.int32 if dtype == "u32" else torch.int64, device=DEV)
+    inputs.generate_into(d, "uniform", dtype, seed=0xB16)
+    before = multiset_sig(d)
+    with ipsgpu.Sorter(dtype, algo=algo) as s:
+        s.sort(d.data_ptr(), n, stream())
+        assert s.status(stream()) == ipsgpu.OK
+    assert keys_nondecreasing(d, dtype)
+    assert multiset_sig(d) == before
