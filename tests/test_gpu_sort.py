@@ -27,6 +27,23 @@ def test_sort_f64(dist):
     assert_sorted_parity(run_sort("f64", host), inputs.to_numpy(host, "f64"), "f64")
 
 
+@pytest.mark.parametrize("algo", [ipsgpu.SAMPLESORT, ipsgpu.SAMPLESORT_TREE])
+def test_sort_f64_special_values(algo):
+    # NaNs of both signs and several payloads, infinities, signed zeros and
+    # subnormals among normal values: the GPU order must be the oracle's
+    # (IEEE 754 totalOrder), bit for bit
+    a = inputs.to_numpy(inputs.generate("normal", "f64", N, seed=4), "f64").copy()
+    special = np.array([0xFFF8000000000001, 0xFFF0000000000001, 0xFFF0000000000000,
+                        0x800FFFFFFFFFFFFF, 0x8000000000000001, 0x8000000000000000, 0,
+                        1, 0x000FFFFFFFFFFFFF, 0x7FF0000000000000, 0x7FF0000000000001,
+                        0x7FF8000000000000], dtype=np.uint64).view(np.float64)
+    rng = np.random.default_rng(5)
+    pos = rng.choice(N, size=20_000, replace=False)
+    a[pos] = special[rng.integers(0, len(special), size=pos.size)]
+    host = inputs.from_numpy(a, "f64")
+    assert_sorted_parity(run_sort("f64", host, algo=algo), a, "f64")
+
+
 @pytest.mark.parametrize("dist", ["uniform", "rootdup", "twodup", "zipf"])
 def test_sort_pair(dist):
     host = inputs.generate(dist, "pair", N)

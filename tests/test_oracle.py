@@ -102,6 +102,38 @@ def test_f64_order_is_total_and_refines_less_than():
     assert np.signbit(got[4]) and not np.signbit(got[5])
 
 
+def test_f64_order_is_ieee754_total_order():
+    # IEEE 754-2008 totalOrder: -NaN (larger payload first) < -inf < negative
+    # normals < negative subnormals < -0 < +0 < positive subnormals < normals
+    # < +inf < +NaN (larger payload last).  Written out by hand from that
+    # definition, as bit patterns.
+    expect = [
+        0xFFF8000000000001,  # -NaN, payload 0x8000000000001 (quiet)
+        0xFFF0000000000001,  # -NaN, payload 1 (signalling)
+        0xFFF0000000000000,  # -inf
+        0xFFEFFFFFFFFFFFFF,  # -max double
+        0xBFF0000000000000,  # -1.0
+        0x8010000000000000,  # -smallest normal
+        0x800FFFFFFFFFFFFF,  # -largest subnormal
+        0x8000000000000001,  # -smallest subnormal
+        0x8000000000000000,  # -0.0
+        0x0000000000000000,  # +0.0
+        0x0000000000000001,  # +smallest subnormal
+        0x000FFFFFFFFFFFFF,  # +largest subnormal
+        0x0010000000000000,  # +smallest normal
+        0x3FF0000000000000,  # 1.0
+        0x7FEFFFFFFFFFFFFF,  # max double
+        0x7FF0000000000000,  # +inf
+        0x7FF0000000000001,  # +NaN, payload 1
+        0x7FF8000000000000,  # +NaN (the default quiet NaN)
+    ]
+    bits = np.array(expect, dtype=np.uint64)
+    for seed in range(5):
+        shuffled = bits[np.random.default_rng(seed).permutation(len(bits))]
+        got = oracle.sort(shuffled.view(np.float64), "f64", k=4, n0=1, seed=seed)
+        assert got.view(np.uint64).tolist() == expect
+
+
 def test_pair_keys_sorted_and_records_kept():
     n = 5000
     a = inputs.to_numpy(inputs.generate("rootdup", "pair", n), "pair")
