@@ -57,6 +57,8 @@ def _args():
                         "rooflines and full-size property checks")
     p.add_argument("--sweep-dtypes", default="u64,u32,f64,pair,quartet,rec100",
                    help="comma-separated element types the sweep runs")
+    p.add_argument("--sweep-shift", type=int, default=0,
+                   help="divide every sweep size by 2^shift (small cases for ncu captures)")
     p.add_argument("--sweep-algos", default="IPS4o,IPS2Ra",
                    help="comma-separated algorithms the sweep runs: IPS4o, IPS2Ra (u32/u64 "
                         "only) and IPS4o-tree (IPS4o walking every element from the tree's "
@@ -645,6 +647,7 @@ def run_sweep(args):
     runs = [r for r in runs if r[0] in want]
     cur = None
     for dtype, dist, algo, lg in runs:
+        lg -= args.sweep_shift
         n = 1 << lg
         if cur != (dtype, dist, lg):
             src = None
