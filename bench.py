@@ -46,6 +46,8 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--log2n", type=int, default=LOG2N)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--clocks-log", default=None,
+                   help="file for the raw nvidia-smi clock samples of the timed region")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-segmented", action="store_true")
     p.add_argument("--no-serve", action="store_true")
@@ -133,10 +135,14 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, path=None):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # the raw samples: a file the caller names (--clocks-log), else a
+        # temporary file
+        self.path = path or os.path.join(tempfile.gettempdir(),
+                                         "ipsgpu_clocks_%d_%d.csv" % (os.getpid(), index))
 
     def start(self):
         try:
@@ -750,7 +756,7 @@ def run_ours(args):
     assert sorter.status(stream.cuda_stream) == ipsgpu.OK
     sorter.set_timing(False)
     sorter.kernel_stats()  # drop warm-up statistics
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_log)
     clocks.start()
     time.sleep(1.0)  # nvidia-smi is up before the first timed step
     # timed region 1 (the value): the production path, every wave of a sort
