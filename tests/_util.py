@@ -105,7 +105,10 @@ def multiset_sig(t):
 
 
 def keys_nondecreasing(t, dtype, chunk=1 << 27):
-    """Keys in non-decreasing order (unsigned; f64 by its order map)."""
+    """Keys in non-decreasing order (unsigned; f64 by its order map;
+    lexicographic for quartet and rec100 keys)."""
+    if dtype == "rec100":
+        chunk = min(chunk, 1 << 23)  # 10 int64 temporaries per record
     n = t.shape[0]
     for a in range(0, max(n - 1, 0), chunk):
         x = t[a:a + chunk + 1]
@@ -116,6 +119,18 @@ def keys_nondecreasing(t, dtype, chunk=1 << 27):
         elif dtype == "f64":
             b = x.view(torch.int64)
             k = torch.where(b < 0, ~b, b | (-(1 << 63))) ^ (-(1 << 63))
+        elif dtype == "rec100":
+            # 10-byte keys compared as unsigned bytes: bytes 0..6 big-endian
+            # in one int64 (56 bits, non-negative), bytes 7..9 in another
+            kb = x[:, :10].to(torch.int64)
+            hi = torch.zeros(kb.shape[0], dtype=torch.int64, device=x.device)
+            for j in range(7):
+                hi = hi * 256 + kb[:, j]
+            lo = kb[:, 7] * 65536 + kb[:, 8] * 256 + kb[:, 9]
+            dh = hi[1:] - hi[:-1]
+            if not bool(((dh > 0) | ((dh == 0) & (lo[1:] >= lo[:-1]))).all().item()):
+                return False
+            continue
         elif dtype == "quartet":
             # lexicographic on the three key words, each unsigned
             w = [x[:, j] ^ (-(1 << 63)) for j in range(3)]

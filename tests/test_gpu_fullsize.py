@@ -47,3 +47,17 @@ def test_more_than_2_32_elements(dtype, n, algo):
         assert s.status(stream()) == ipsgpu.OK
     assert keys_nondecreasing(d, dtype)
     assert multiset_sig(d) == before
+
+
+@pytest.mark.parametrize("dtype,dist", [("f64", "normal"), ("rec100", "uniform")])
+def test_wide_record_configuration_2e28(dtype, dist):
+    # the wider-record plain-sort configuration at its full size: 2^28
+    # doubles (2 GiB) or 100-byte records (25 GiB)
+    n = 1 << 28
+    d = inputs.generate(dist, dtype, n, seed=0x5EED, device=DEV)
+    before = multiset_sig(d)
+    with ipsgpu.Sorter(dtype) as s:
+        s.sort(d.data_ptr(), n, stream())
+        assert s.status(stream()) == ipsgpu.OK
+    assert keys_nondecreasing(d, dtype)
+    assert multiset_sig(d) == before

@@ -6,12 +6,26 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2009_13569_gb300 import inputs, ipsgpu
 from _util import DEV, assert_sorted_parity, run_sort, stream
 
 pytestmark = pytest.mark.gpu
 
 N = 300_007
+
+
+@pytest.mark.parametrize("algo", [ipsgpu.SAMPLESORT, ipsgpu.RADIX])
+def test_small_configuration_2e20_uniform_u64(algo):
+    # the small plain-sort configuration: 2^20 uint64 keys, Uniform [0, 2^64),
+    # default seed.  The oracle runs its parameters exactly (k = 256,
+    # alpha = 0.2 log2 n, base case 16); the GPU runs its own block size (512 B:
+    # 256 blocks of 2 KiB would need 512 KiB of shared memory).  The sorted
+    # sequence is unique, so the two must agree bit for bit.
+    host = inputs.generate("uniform", "u64", 1 << 20)
+    ref = oracle.sort(inputs.to_numpy(host, "u64"), "u64", k=256, n0=16, alpha=0.2)
+    got = run_sort("u64", host, algo=algo)
+    np.testing.assert_array_equal(got, ref)
 
 
 @pytest.mark.parametrize("dist", inputs.INT_DISTS)
