@@ -257,6 +257,15 @@ const char *ipsgpu_kernel_name(int kind);
  * IPSGPU_E_TIMEOUT in the status word (read it with ipsgpu_status). */
 int ipsgpu_debug_bounded_wait(ipsgpu_sorter *s, uint32_t spin_limit, void *stream);
 
+/* Out-of-bounds write detection without a sanitizer: every device buffer of
+ * a sorter lies between two 256-byte guard zones filled with 0xA5 at
+ * creation.  Synchronizes the device and checks every guard.  Returns
+ * IPSGPU_OK if all are intact; IPSGPU_E_INTERNAL if one changed (a kernel
+ * wrote past a buffer's end or before its start), with *first_bad (if not
+ * NULL) the index of the first such buffer in creation order (UINT64_MAX
+ * when none).  Errors: E_INVAL (s NULL), E_CUDA. */
+int ipsgpu_debug_check_guards(ipsgpu_sorter *s, uint64_t *first_bad);
+
 /* ------------------------------------------------------------------ serving
  * A server sorts requests that arrive at any time: it admits them by HBM
  * footprint and runs them on a few CUDA streams ("lanes") while others are

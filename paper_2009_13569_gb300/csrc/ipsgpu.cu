@@ -144,12 +144,8 @@ void apply(Sorter &s, const Resolved &r, int dtype) {
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? IPSGPU_OK : IPSGPU_E_CUDA; }
 
 void free_all(Sorter &s) {
-    void *dev[] = {s.d_seg,    s.d_st,     s.d_sarr,   s.d_keys,    s.d_stripe,
-                   s.d_scount, s.d_sfull,  s.d_arena,  s.d_moves,   s.d_nmoves,
-                   s.d_status, s.d_cta_seg, s.d_base,    s.d_flags,
-                   s.d_waitflag, s.d_ring, s.d_gjob, s.d_gstate, s.d_stripe_first};
-    for (void *p : dev)
-        if (p) cudaFree(p);
+    for (const auto &g : s.guarded) cudaFree(g.base);
+    s.guarded.clear();
     if (s.wave_exec) cudaGraphExecDestroy(s.wave_exec);
     if (s.wave_graph) cudaGraphDestroy(s.wave_graph);
     if (s.cap_stream) cudaStreamDestroy(s.cap_stream);
@@ -599,8 +595,20 @@ int ipsgpu_sorter_create(const ipsgpu_params *params, int dtype, ipsgpu_sorter *
     Layout L = layout(s, s.ops->key_bytes);
     s.scratch_bytes = L.total();
     bool ok = true;
+    // device buffers between guard zones (see Sorter::guarded)
     auto dm = [&](void **p, uint64_t bytes) {
-        if (ok && cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) ok = false;
+        if (!ok) return;
+        if (!bytes) bytes = 16;
+        unsigned char *base = nullptr;
+        if (cudaMalloc((void **)&base, bytes + 2 * kGuardBytes) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        s.guarded.push_back({base, bytes});
+        if (cudaMemset(base, kGuardByte, kGuardBytes) != cudaSuccess ||
+            cudaMemset(base + kGuardBytes + bytes, kGuardByte, kGuardBytes) != cudaSuccess)
+            ok = false;
+        *p = base + kGuardBytes;
     };
     auto hm = [&](void **p, uint64_t bytes) {
         if (ok && cudaMallocHost(p, bytes ? bytes : 16) != cudaSuccess) ok = false;
@@ -650,6 +658,28 @@ int ipsgpu_sorter_create(const ipsgpu_params *params, int dtype, ipsgpu_sorter *
         return IPSGPU_E_CUDA;
     }
     *out = h;
+    return IPSGPU_OK;
+}
+
+int ipsgpu_debug_check_guards(ipsgpu_sorter *h, uint64_t *first_bad) {
+    if (!h) return IPSGPU_E_INVAL;
+    Sorter &s = h->s;
+    if (cudaDeviceSynchronize() != cudaSuccess) return IPSGPU_E_CUDA;
+    std::vector<unsigned char> buf(2 * kGuardBytes);
+    for (size_t i = 0; i < s.guarded.size(); i++) {
+        const auto &g = s.guarded[i];
+        if (cudaMemcpy(buf.data(), g.base, kGuardBytes, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(buf.data() + kGuardBytes, g.base + kGuardBytes + g.bytes, kGuardBytes,
+                       cudaMemcpyDeviceToHost) != cudaSuccess)
+            return IPSGPU_E_CUDA;
+        for (unsigned char c : buf) {
+            if (c != kGuardByte) {
+                if (first_bad) *first_bad = (uint64_t)i;
+                return IPSGPU_E_INTERNAL;
+            }
+        }
+    }
+    if (first_bad) *first_bad = ~0ull;
     return IPSGPU_OK;
 }
 

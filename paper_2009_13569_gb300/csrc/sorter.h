@@ -61,6 +61,9 @@ struct TimedLaunch {
     cudaEvent_t ev0, ev1;
 };
 
+constexpr uint64_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+
 struct Sorter {
     int dtype = 0;
     int device = 0;
@@ -114,6 +117,14 @@ struct Sorter {
     uint32_t *h_cta_seg = nullptr;
     int *h_flags = nullptr;
     uint64_t scratch_bytes = 0;
+    // Every device buffer sits between two guard zones of kGuardBytes filled
+    // with kGuardByte at creation; a kernel writing past either end of its
+    // buffer changes a guard (ipsgpu_debug_check_guards).
+    struct Guarded {
+        unsigned char *base;  // the allocation: guard | buffer | guard
+        uint64_t bytes;       // the buffer
+    };
+    std::vector<Guarded> guarded;
     cudaEvent_t h2d_done = nullptr;  // last upload out of the pinned mirrors
     // the level currently being launched
     unsigned char *data = nullptr;

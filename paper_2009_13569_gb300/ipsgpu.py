@@ -66,6 +66,7 @@ def load():
                                       ctypes.POINTER(ctypes.c_double), i32]),
         "ipsgpu_kernel_name": (ctypes.c_char_p, [i32]),
         "ipsgpu_debug_bounded_wait": (i32, [vp, u32, vp]),
+        "ipsgpu_debug_check_guards": (i32, [vp, ctypes.POINTER(u64)]),
         "ipsgpu_partition_level_noalloc": (i32, [i32, vp, u64, vp, u32, i32, vp, vp]),
         "ipsgpu_sort_segmented": (i32, [vp, vp, u64, vp, u64, vp]),
         "ipsgpu_sort_batch": (i32, [vp, vp, u64, vp]),
@@ -106,7 +107,8 @@ def exported_symbols():
         "ipsgpu_sort_host",
         "ipsgpu_partition_level", "ipsgpu_radix_level", "ipsgpu_classify", "ipsgpu_status",
         "ipsgpu_strerror", "ipsgpu_set_timing", "ipsgpu_kernel_stats", "ipsgpu_kernel_name",
-        "ipsgpu_debug_bounded_wait", "ipsgpu_partition_level_noalloc", "ipsgpu_sort_segmented",
+        "ipsgpu_debug_bounded_wait", "ipsgpu_debug_check_guards",
+        "ipsgpu_partition_level_noalloc", "ipsgpu_sort_segmented",
         "ipsgpu_sort_batch", "ipsgpu_segmented_graph_create", "ipsgpu_graph_launch",
         "ipsgpu_graph_nodes", "ipsgpu_graph_destroy", "ipsgpu_sorter_prepare",
         "ipsgpu_server_create", "ipsgpu_server_destroy", "ipsgpu_server_reserve",
@@ -235,6 +237,18 @@ class Sorter:
             raise IpsgpuError(-nk, "ipsgpu_kernel_stats")
         return {load().ipsgpu_kernel_name(i).decode(): (int(la[i]), float(ms[i]), float(by[i]))
                 for i in range(nk)}
+
+    def check_guards(self):
+        """Synchronize and check the guard zones around every device buffer
+        of the sorter: None if intact, else the index of the first buffer
+        whose guard changed."""
+        bad = ctypes.c_uint64(0)
+        rc = load().ipsgpu_debug_check_guards(self._h, ctypes.byref(bad))
+        if rc == OK:
+            return None
+        if rc == E_INTERNAL:
+            return int(bad.value)
+        raise IpsgpuError(rc, "ipsgpu_debug_check_guards")
 
     def debug_bounded_wait(self, spin_limit, stream=0):
         _check(load().ipsgpu_debug_bounded_wait(self._h, spin_limit, stream),
