@@ -71,6 +71,25 @@ def _args():
     return p.parse_args()
 
 
+PARAM_KEYS = {"k": int, "block_bytes": int, "alpha_scale": float, "base_case": int,
+              "seed": int, "spin_limit": int, "arena_bytes": int}
+
+
+def env_params(text=None):
+    """Sorter parameters of the headline sort from IPSGPU_PARAMS, e.g.
+    "k=128,block_bytes=1024,alpha_scale=0.5" (empty: the library's
+    defaults).  Unknown keys are an error."""
+    text = os.environ.get("IPSGPU_PARAMS", "") if text is None else text
+    out = {}
+    for item in filter(None, (x.strip() for x in text.split(","))):
+        key, _, val = item.partition("=")
+        key = key.strip()
+        if key not in PARAM_KEYS or not val:
+            raise ValueError("IPSGPU_PARAMS: bad item %r (keys: %s)" % (item, sorted(PARAM_KEYS)))
+        out[key] = PARAM_KEYS[key](val.strip())
+    return out
+
+
 def reduce_max_over_ranks(pg, values, device="cpu"):
     """Element-wise maximum over all ranks of a list of floats (the slowest
     rank's time, any rank's failure flag); every rank gets the result.  With
@@ -730,7 +749,8 @@ def run_ours(args):
     src = inputs.generate("uniform", "u64", n, seed=SEED + rank, device=dev)
     work = torch.empty_like(src)
     stream = torch.cuda.Stream(dev)
-    sorter = ipsgpu.Sorter("u64")
+    params = env_params()
+    sorter = ipsgpu.Sorter("u64", **params)
     def timed_steps(count):
         ts = []
         for _ in range(count):
@@ -845,7 +865,7 @@ def run_ours(args):
         hsrc = src.cpu().pin_memory()
         hdst = [torch.empty_like(hsrc).pin_memory() for _ in range(E2E_LANES)]
         works = [work] + [torch.empty_like(work) for _ in range(E2E_LANES - 1)]
-        sorters = [sorter] + [ipsgpu.Sorter("u64") for _ in range(E2E_LANES - 1)]
+        sorters = [sorter] + [ipsgpu.Sorter("u64", **params) for _ in range(E2E_LANES - 1)]
         for s_ in sorters[1:]:
             s_.prepare()
         streams = [stream] + [torch.cuda.Stream(dev) for _ in range(E2E_LANES - 1)]
@@ -910,7 +930,9 @@ def run_ours(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n": n, "dist": "uniform", "seed": SEED,
-                           "k": 256, "block_bytes": 512, "alpha": "0.2*log2(n')",
+                           "k": params.get("k", 256), "block_bytes": params.get("block_bytes", 512),
+                           "alpha": "%g*log2(n')" % params.get("alpha_scale", 0.2),
+                           "params_override": params or None,
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "inputs larger than L2 (8 GiB per array)"},
                 "result_sorted": ok, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,

@@ -79,7 +79,8 @@ enum {
     IPSGPU_E_CUDA = 4,        /* a CUDA runtime call failed                   */
     IPSGPU_E_TIMEOUT = 5,     /* a bounded device wait gave up                */
     IPSGPU_E_BUSY = 6,        /* server: request cannot be admitted now       */
-    IPSGPU_E_INTERNAL = 7     /* a kernel found an inconsistent count         */
+    IPSGPU_E_INTERNAL = 7,    /* a kernel found an inconsistent count         */
+    IPSGPU_E_CANCELED = 8     /* server: the request was cancelled before it ran */
 };
 
 /* Tuning parameters; a zero field takes its default.
@@ -330,6 +331,12 @@ double ipsgpu_server_now_us(void);
 /* Return a request's footprint (reserved or done; E_BUSY while it runs) and
  * forget its ticket. */
 int ipsgpu_server_release(ipsgpu_server *srv, uint64_t ticket);
+/* Cancel a request that has not begun to run: a reserved one, or a started
+ * one still waiting in the queue.  It becomes done with status
+ * IPSGPU_E_CANCELED (poll / wait report it) and its data is left untouched;
+ * release it as usual.  Errors: E_INVAL (unknown or already done ticket),
+ * E_BUSY (already running: it will complete normally). */
+int ipsgpu_server_cancel(ipsgpu_server *srv, uint64_t ticket);
 /* Block until every started request is done. */
 int ipsgpu_server_drain(ipsgpu_server *srv);
 /* Bytes admitted now (scratch included), the budget, the scratch. */

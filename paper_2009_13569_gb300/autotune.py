@@ -10,7 +10,16 @@ log2 n).  Each candidate is timed `reps` times on fresh copies of the sample
 (the sort is in place) and scored by its median.  The search logic is
 independent of how a candidate is timed (search()), so it is testable on the
 CPU; tune_array() and tune_segmented() time candidates through the C ABI.
+
+Results can be kept in a JSON cache file (``cache=path``): the key is the
+element type and a coarse signature of the workload (the array size, or the
+number of arrays, total elements and a histogram of log2 array lengths), so
+a later run on a workload of the same shape takes the stored parameters
+without timing anything.
 """
+import json
+import math
+import os
 import statistics
 
 from . import ipsgpu
@@ -60,6 +69,38 @@ def search(time_fn, dtype, kb_pairs=KB_PAIRS, base_fracs=BASE_FRACTIONS, alphas=
     return best, table
 
 
+def cached(path, key, tune):
+    """Run tune() -> (best params, table) unless the JSON file at `path`
+    already holds parameters for `key`; store the result under `key`.
+    Returns (best params, table); the table is empty on a cache hit."""
+    if not path:
+        return tune()
+    store = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            store = json.load(f)
+    if key in store:
+        return dict(store[key]), []
+    best, table = tune()
+    store[key] = best
+    tmp = "%s.tmp%d" % (path, os.getpid())
+    with open(tmp, "w") as f:
+        json.dump(store, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+    return best, table
+
+
+def segmented_signature(lengths):
+    """Coarse shape of a batch: arrays, total elements, and the count of
+    arrays per log2 length class (0 for empty ones)."""
+    hist = {}
+    for m in lengths:
+        c = 0 if m <= 0 else int(math.floor(math.log2(m))) + 1
+        hist[c] = hist.get(c, 0) + 1
+    return "arrays=%d,n=%d,log2hist=%s" % (
+        len(lengths), sum(lengths), ",".join("%d:%d" % kv for kv in sorted(hist.items())))
+
+
 def _median_time(torch, run, reps):
     ts = []
     for _ in range(reps):
@@ -67,9 +108,15 @@ def _median_time(torch, run, reps):
     return statistics.median(ts)
 
 
-def tune_array(torch, sample, dtype, reps=3, **kw):
+def tune_array(torch, sample, dtype, reps=3, cache=None, **kw):
     """Tune for plain sorts of arrays like `sample` (a device tensor in the
     storage format of paper_2009_13569_gb300.inputs)."""
+    n = sample.shape[0]
+    return cached(cache, "array:%s:n=%d" % (dtype, n),
+                  lambda: _tune_array(torch, sample, dtype, reps, **kw))
+
+
+def _tune_array(torch, sample, dtype, reps, **kw):
     n = sample.shape[0]
     work = torch.empty_like(sample)
     stream = torch.cuda.Stream(sample.device)
@@ -102,10 +149,16 @@ def tune_array(torch, sample, dtype, reps=3, **kw):
     return search(time_fn, dtype, **kw)
 
 
-def tune_segmented(torch, data, offsets, dtype, reps=3, **kw):
+def tune_segmented(torch, data, offsets, dtype, reps=3, cache=None, **kw):
     """Tune for segmented sorts of batches like (data, offsets): each
     candidate sorter captures the batch into a CUDA graph and is timed on
     graph launches."""
+    lengths = (offsets[1:] - offsets[:-1]).cpu().tolist()
+    return cached(cache, "segmented:%s:%s" % (dtype, segmented_signature(lengths)),
+                  lambda: _tune_segmented(torch, data, offsets, dtype, reps, **kw))
+
+
+def _tune_segmented(torch, data, offsets, dtype, reps, **kw):
     n = data.shape[0]
     nseg = offsets.numel() - 1
     work = torch.empty_like(data)

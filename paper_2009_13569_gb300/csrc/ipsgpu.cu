@@ -414,6 +414,7 @@ int graph_run(Sorter &s, const GJob &job, cudaStream_t st) {
         return cuda_status(cudaGraphLaunch(s.wave_exec, st));
     }
     for (uint32_t w = 0; w < kMaxWaves; w++) {
+        NvtxRange nvtx_wave("ipsgpu wave");
         const size_t l0 = s.launches.size();
         cudaError_t e = s.ops->wave(&s, ga, st, 0, cudaGraphConditionalHandle());
         if (e == cudaSuccess)
@@ -578,6 +579,7 @@ uint64_t ipsgpu_scratch_bytes(const ipsgpu_params *params, int dtype) {
 }
 
 int ipsgpu_sorter_create(const ipsgpu_params *params, int dtype, ipsgpu_sorter **out) {
+    NvtxRange nvtx_range("ipsgpu_sorter_create");
     if (!out) return IPSGPU_E_INVAL;
     *out = nullptr;
     Resolved r;
@@ -684,6 +686,7 @@ int ipsgpu_debug_check_guards(ipsgpu_sorter *h, uint64_t *first_bad) {
 }
 
 int ipsgpu_sorter_prepare(ipsgpu_sorter *h) {
+    NvtxRange nvtx_range("ipsgpu_sorter_prepare");
     if (!h) return IPSGPU_E_INVAL;
     Sorter &s = h->s;
     if (s.wave_exec) return IPSGPU_OK;
@@ -699,6 +702,7 @@ int ipsgpu_sorter_destroy(ipsgpu_sorter *h) {
 }
 
 int ipsgpu_sort(ipsgpu_sorter *h, void *d_data, uint64_t n, void *stream) {
+    NvtxRange nvtx_range("ipsgpu_sort");
     if (!h) return IPSGPU_E_INVAL;
     if (n == 0) return IPSGPU_OK;
     int rc = check_data(h->s, d_data);
@@ -708,6 +712,7 @@ int ipsgpu_sort(ipsgpu_sorter *h, void *d_data, uint64_t n, void *stream) {
 
 int ipsgpu_sort_host(ipsgpu_sorter *h, const void *h_in, void *h_out, uint64_t n, void *d_work,
                      void *stream) {
+    NvtxRange nvtx_range("ipsgpu_sort_host");
     if (!h || !h_in || !h_out) return IPSGPU_E_INVAL;
     if (n == 0) return IPSGPU_OK;
     Sorter &s = h->s;
@@ -724,6 +729,7 @@ int ipsgpu_sort_host(ipsgpu_sorter *h, const void *h_in, void *h_out, uint64_t n
 int ipsgpu_partition_level(ipsgpu_sorter *h, void *d_data, uint64_t n, const void *d_splitters,
                            uint32_t num_splitters, int equal_buckets, uint64_t *d_bucket_begin,
                            void *stream) {
+    NvtxRange nvtx_range("ipsgpu_partition_level");
     if (!h || !d_bucket_begin || !d_splitters || num_splitters == 0) return IPSGPU_E_INVAL;
     Sorter &s = h->s;
     const uint64_t K = next_pow2((uint64_t)num_splitters + 1);
@@ -744,6 +750,7 @@ int ipsgpu_partition_level(ipsgpu_sorter *h, void *d_data, uint64_t n, const voi
 
 int ipsgpu_radix_level(ipsgpu_sorter *h, void *d_data, uint64_t n, uint32_t shift, uint32_t bits,
                        uint64_t *d_bucket_begin, void *stream) {
+    NvtxRange nvtx_range("ipsgpu_radix_level");
     if (!h || !d_bucket_begin) return IPSGPU_E_INVAL;
     Sorter &s = h->s;
     if (!(s.dtype == IPSGPU_U32 || s.dtype == IPSGPU_U64 || s.dtype == IPSGPU_PAIR_U64))
@@ -774,6 +781,7 @@ static int check_segmented(ipsgpu_sorter *h, void *d_data, uint64_t n, const uin
 
 int ipsgpu_sort_segmented(ipsgpu_sorter *h, void *d_data, uint64_t n, const uint64_t *d_offsets,
                           uint64_t num_segments, void *stream) {
+    NvtxRange nvtx_range("ipsgpu_sort_segmented");
     int rc = check_segmented(h, d_data, n, d_offsets, num_segments);
     if (rc) return rc;
     if (n < 2 || num_segments == 0) return IPSGPU_OK;
@@ -785,6 +793,7 @@ int ipsgpu_sort_segmented(ipsgpu_sorter *h, void *d_data, uint64_t n, const uint
 
 int ipsgpu_sort_batch(ipsgpu_sorter *h, const uint64_t *d_segs, uint64_t num_segments,
                       void *stream) {
+    NvtxRange nvtx_range("ipsgpu_sort_batch");
     if (!h || num_segments > 0xFFFFFFFFull) return IPSGPU_E_INVAL;
     if (num_segments == 0) return IPSGPU_OK;
     if (!d_segs || ((uintptr_t)d_segs % 8)) return IPSGPU_E_INVAL;
@@ -801,6 +810,7 @@ struct ipsgpu_graph {
 int ipsgpu_segmented_graph_create(ipsgpu_sorter *h, void *d_data, uint64_t n,
                                   const uint64_t *d_offsets, uint64_t num_segments,
                                   ipsgpu_graph **out) {
+    NvtxRange nvtx_range("ipsgpu_segmented_graph_create");
     if (!out) return IPSGPU_E_INVAL;
     *out = nullptr;
     int rc = check_segmented(h, d_data, n, d_offsets, num_segments);
@@ -818,6 +828,7 @@ int ipsgpu_segmented_graph_create(ipsgpu_sorter *h, void *d_data, uint64_t n,
 }
 
 int ipsgpu_graph_launch(ipsgpu_graph *g, void *stream) {
+    NvtxRange nvtx_range("ipsgpu_graph_launch");
     if (!g || !g->exec) return IPSGPU_E_INVAL;
     return cuda_status(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
 }
@@ -840,6 +851,7 @@ int ipsgpu_graph_destroy(ipsgpu_graph *g) {
 
 int ipsgpu_classify(ipsgpu_sorter *h, const void *d_data, uint64_t n, const void *d_splitters,
                     uint32_t num_splitters, int equal_buckets, uint32_t *d_class, void *stream) {
+    NvtxRange nvtx_range("ipsgpu_classify");
     if (!h || !d_class || !d_splitters || num_splitters == 0) return IPSGPU_E_INVAL;
     Sorter &s = h->s;
     const uint64_t K = next_pow2((uint64_t)num_splitters + 1);
@@ -891,6 +903,7 @@ const char *ipsgpu_strerror(int code) {
     case IPSGPU_E_TIMEOUT: return "a bounded device wait timed out";
     case IPSGPU_E_BUSY: return "request cannot be admitted now";
     case IPSGPU_E_INTERNAL: return "internal consistency check failed";
+    case IPSGPU_E_CANCELED: return "request cancelled before it ran";
     default: return "unknown status";
     }
 }

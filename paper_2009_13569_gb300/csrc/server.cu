@@ -501,6 +501,30 @@ int ipsgpu_server_release(ipsgpu_server *s, uint64_t ticket) {
     return IPSGPU_OK;
 }
 
+int ipsgpu_server_cancel(ipsgpu_server *s, uint64_t ticket) {
+    if (!s) return IPSGPU_E_INVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end() || it->second.state == RS_DONE) return IPSGPU_E_INVAL;
+    Req &r = it->second;
+    if (r.state == RS_RUNNING) return IPSGPU_E_BUSY;
+    if (r.state == RS_QUEUED) {
+        for (auto q = s->queue.begin(); q != s->queue.end(); ++q) {
+            if (*q == ticket) {
+                s->queue.erase(q);
+                break;
+            }
+        }
+    }
+    const double t = now_us();
+    if (r.state == RS_RESERVED) r.t_submit = r.t_launch = t;
+    r.state = RS_DONE;
+    r.status = IPSGPU_E_CANCELED;
+    r.t_done = t;
+    s->cv_done.notify_all();
+    return IPSGPU_OK;
+}
+
 int ipsgpu_server_drain(ipsgpu_server *s) {
     if (!s) return IPSGPU_E_INVAL;
     std::unique_lock<std::mutex> lk(s->mu);

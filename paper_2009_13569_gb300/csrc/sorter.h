@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <vector>
 
 #include "common.cuh"
@@ -59,6 +61,15 @@ struct TimedLaunch {
     int kind;
     double bytes;
     cudaEvent_t ev0, ev1;
+};
+
+// NVTX range over a host-side call, so that profilers show which library
+// call issued which kernels (no cost without an attached tool).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 constexpr uint64_t kGuardBytes = 256;

@@ -15,7 +15,7 @@ DTYPES = {"u32": 0, "u64": 1, "f64": 2, "pair": 3, "rec100": 4, "quartet": 5}
 ELEM_BYTES = {"u32": 4, "u64": 8, "f64": 8, "pair": 16, "rec100": 100, "quartet": 32}
 SAMPLESORT, RADIX, SAMPLESORT_TREE = 0, 1, 2
 
-OK, E_INVAL, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY, E_INTERNAL = range(8)
+OK, E_INVAL, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY, E_INTERNAL, E_CANCELED = range(9)
 
 
 class IpsgpuError(RuntimeError):
@@ -88,6 +88,7 @@ def load():
                                       ctypes.POINTER(ctypes.c_double)]),
         "ipsgpu_server_now_us": (ctypes.c_double, []),
         "ipsgpu_server_release": (i32, [vp, u64]),
+        "ipsgpu_server_cancel": (i32, [vp, u64]),
         "ipsgpu_server_drain": (i32, [vp]),
         "ipsgpu_server_usage": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                       ctypes.POINTER(u64)]),
@@ -114,7 +115,7 @@ def exported_symbols():
         "ipsgpu_server_create", "ipsgpu_server_destroy", "ipsgpu_server_reserve",
         "ipsgpu_server_start", "ipsgpu_server_submit", "ipsgpu_server_poll", "ipsgpu_server_wait",
         "ipsgpu_server_times", "ipsgpu_server_now_us", "ipsgpu_server_release",
-        "ipsgpu_server_drain", "ipsgpu_server_usage",
+        "ipsgpu_server_drain", "ipsgpu_server_usage", "ipsgpu_server_cancel",
     ]
 
 
@@ -351,6 +352,10 @@ class Server:
 
     def release(self, ticket):
         _check(load().ipsgpu_server_release(self._h, ticket), "ipsgpu_server_release")
+
+    def cancel(self, ticket):
+        """Cancel a reserved or queued request (E_BUSY if it already runs)."""
+        _check(load().ipsgpu_server_cancel(self._h, ticket), "ipsgpu_server_cancel")
 
     def drain(self):
         _check(load().ipsgpu_server_drain(self._h), "ipsgpu_server_drain")

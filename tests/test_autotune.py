@@ -34,3 +34,28 @@ def test_search_skips_rejected_candidates():
 def test_base_cap_matches_the_library_limit():
     assert autotune.base_cap("u64") == 184 * 1024 // 8
     assert autotune.base_cap("rec100") == 184 * 1024 // 100
+
+
+def test_cache_file_stores_and_reuses(tmp_path):
+    path = str(tmp_path / "tune.json")
+    calls = []
+
+    def tune():
+        calls.append(1)
+        return {"k": 128, "block_bytes": 1024, "alpha_scale": 0.5, "base_case": 100}, [("t", 1.0)]
+
+    best, table = autotune.cached(path, "array:u64:n=1024", tune)
+    assert len(calls) == 1 and table
+    again, table2 = autotune.cached(path, "array:u64:n=1024", tune)
+    assert again == best and table2 == [] and len(calls) == 1  # hit: nothing timed
+    other, _ = autotune.cached(path, "array:u64:n=2048", tune)
+    assert len(calls) == 2  # another workload shape is tuned again
+    assert autotune.cached(None, "x", tune)[1]  # no cache file: always tuned
+
+
+def test_segmented_signature_is_coarse():
+    a = autotune.segmented_signature([0, 1, 3, 1000, 1023])
+    b = autotune.segmented_signature([0, 1, 2, 600, 1020])
+    assert a.startswith("arrays=5,")
+    # same histogram of log2 lengths, different totals: different keys
+    assert a.split("log2hist=")[1] == b.split("log2hist=")[1] and a != b

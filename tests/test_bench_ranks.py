@@ -80,3 +80,14 @@ def test_reference_arm_prints_on_rank_zero_only(monkeypatch):
     line = json.loads(buf.getvalue().strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_env_params_parsing():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.env_params("") == {}
+    assert bench.env_params(" k=128, block_bytes=1024 ,alpha_scale=0.5") == {
+        "k": 128, "block_bytes": 1024, "alpha_scale": 0.5}
+    for bad in ("k", "kk=3", "k=", "base_case=12,foo=1"):
+        with pytest.raises(ValueError):
+            bench.env_params(bad)

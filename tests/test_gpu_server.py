@@ -135,3 +135,35 @@ def test_server_small_reserve_keeps_small_requests_admitted():
         for t in smalls + [big]:
             srv.release(t)
         assert srv.usage()[0] == scratch
+
+
+def test_server_cancel_reserved_and_queued_requests():
+    # one lane, held busy by a request whose ready stream first runs a
+    # bounded sleep kernel: requests started meanwhile stay queued
+    side = torch.cuda.Stream(DEV)
+    with ipsgpu.Server(8 << 30, lanes=1, dtypes=("u64",), batch_max_elems=1 << 10) as srv:
+        host1 = inputs.generate("uniform", "u64", 300_000, seed=1)
+        host2 = inputs.generate("uniform", "u64", 200_000, seed=2)
+        d1, d2 = to_dev(host1), to_dev(host2)
+        torch.cuda.synchronize()
+        t0 = srv.reserve(1000, "u64")
+        srv.cancel(t0)  # reserved, never started
+        assert srv.poll(t0) == (True, ipsgpu.E_CANCELED)
+        assert srv.wait(t0) == ipsgpu.E_CANCELED
+        t1 = srv.reserve(300_000, "u64")
+        with torch.cuda.stream(side):
+            torch.cuda._sleep(200_000_000)  # ~0.1 s on the side stream
+        srv.start(t1, d1.data_ptr(), side.cuda_stream)
+        t2 = srv.submit(d2.data_ptr(), 200_000, "u64")
+        srv.cancel(t2)  # still queued behind t1 on the only lane
+        assert srv.wait(t2) == ipsgpu.E_CANCELED
+        assert srv.wait(t1) == ipsgpu.OK
+        with pytest.raises(ipsgpu.IpsgpuError) as e:
+            srv.cancel(t1)  # already done
+        assert e.value.code == ipsgpu.E_INVAL
+        # the cancelled request's data is untouched, the other one sorted
+        assert torch.equal(d2.cpu(), host2)
+        assert_sorted_parity(inputs.to_numpy(d1.cpu(), "u64"), inputs.to_numpy(host1, "u64"), "u64")
+        for t in (t0, t1, t2):
+            srv.release(t)
+        assert srv.usage()[0] == srv.usage()[2]
