@@ -637,6 +637,27 @@ def _keys_sorted(torch, t, dtype, chunk=1 << 27):
 
 E2E_LANES = 3  # streams (each with a sorter and a device buffer) of the end-to-end run
 
+
+def e2e_lanes(array_bytes, ranks_per_node, mem_available=None):
+    """Lanes of the end-to-end run: E2E_LANES, fewer when the pinned host
+    buffers of every rank on the node (one input plus one output per lane)
+    would take more than half of the host's available memory."""
+    if mem_available is None:
+        mem_available = 0
+        try:
+            with open("/proc/meminfo") as f:
+                for line in f:
+                    if line.startswith("MemAvailable:"):
+                        mem_available = int(line.split()[1]) * 1024
+        except OSError:
+            pass
+    if not mem_available:
+        return 1
+    lanes = E2E_LANES
+    while lanes > 1 and (lanes + 1) * array_bytes * ranks_per_node > mem_available // 2:
+        lanes -= 1
+    return lanes
+
 ALGO_CODES = {"IPS4o": 0, "IPS2Ra": 1, "IPS4o-tree": 2}  # ipsgpu_algo values
 ALGO_NAMES = {v: k for k, v in ALGO_CODES.items()}
 
@@ -857,18 +878,19 @@ def run_ours(args):
         # end to end through the public API (ipsgpu_sort_host): every step
         # copies its input from pinned host memory to the device, sorts it
         # and copies the result back to pinned host memory, all inside the
-        # timed region.  Steps go round-robin over E2E_LANES streams, each
+        # timed region.  Steps go round-robin over the lanes (streams), each
         # with its own sorter and device buffer, so the host->device copy of
         # one step, the kernels of another and the device->host copy of a
         # third run at once (the host link is full duplex).  The same steps
         # on one stream, one after another, are reported as `sequential`.
+        lanes = e2e_lanes(n * 8, int(os.environ.get("LOCAL_WORLD_SIZE", "1")))
         hsrc = src.cpu().pin_memory()
-        hdst = [torch.empty_like(hsrc).pin_memory() for _ in range(E2E_LANES)]
-        works = [work] + [torch.empty_like(work) for _ in range(E2E_LANES - 1)]
-        sorters = [sorter] + [ipsgpu.Sorter("u64", **params) for _ in range(E2E_LANES - 1)]
+        hdst = [torch.empty_like(hsrc).pin_memory() for _ in range(lanes)]
+        works = [work] + [torch.empty_like(work) for _ in range(lanes - 1)]
+        sorters = [sorter] + [ipsgpu.Sorter("u64", **params) for _ in range(lanes - 1)]
         for s_ in sorters[1:]:
             s_.prepare()
-        streams = [stream] + [torch.cuda.Stream(dev) for _ in range(E2E_LANES - 1)]
+        streams = [stream] + [torch.cuda.Stream(dev) for _ in range(lanes - 1)]
 
         def e2e_steps(k, lanes):
             barrier()
@@ -889,8 +911,8 @@ def run_ours(args):
             streams[0].synchronize()
             return t0.elapsed_time(t1) / k
 
-        e2e_steps(E2E_LANES, E2E_LANES)  # warm-up of every sorter and the copy paths
-        ems = e2e_steps(args.steps, E2E_LANES)
+        e2e_steps(lanes, lanes)  # warm-up of every sorter and the copy paths
+        ems = e2e_steps(args.steps, lanes)
         sms = e2e_steps(args.steps, 1)
         eok = all(s_.status(st_.cuda_stream) == ipsgpu.OK for s_, st_ in zip(sorters, streams))
         for h in hdst:  # every result buffer checked on the device
@@ -901,7 +923,8 @@ def run_ours(args):
         e2e = {"value": replica_value(world, n, ems), "unit": UNIT,
                "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8, "ms_per_step": ems,
                "form": "ipsgpu_sort_host, pinned host buffers, steps round-robin over %d "
-                       "streams (copies of some steps overlap the kernels of others)" % E2E_LANES,
+                       "streams (copies of some steps overlap the kernels of others)" % lanes,
+               "lanes": lanes,
                "sequential": {"value": replica_value(world, n, sms), "ms_per_step": sms,
                               "form": "the same steps on one stream, one after another"},
                "result_sorted": eok}

@@ -91,3 +91,14 @@ def test_env_params_parsing():
     for bad in ("k", "kk=3", "k=", "base_case=12,foo=1"):
         with pytest.raises(ValueError):
             bench.env_params(bad)
+
+
+def test_e2e_lanes_fit_host_memory():
+    sys.path.insert(0, ROOT)
+    import bench
+    gib = 1 << 30
+    assert bench.e2e_lanes(8 * gib, 1, 400 * gib) == bench.E2E_LANES
+    # 8 ranks on one node: (lanes + 1) x 8 GiB x 8 must stay within half of 400 GiB
+    assert bench.e2e_lanes(8 * gib, 8, 400 * gib) == 2
+    assert bench.e2e_lanes(8 * gib, 8, 200 * gib) == 1
+    assert bench.e2e_lanes(8 * gib, 1, 0) == 1  # unknown: the sequential form only
