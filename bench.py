@@ -215,7 +215,7 @@ NCU_TRAFFIC = {
                  "sha256": "217f874a56bbf29af09547ba7213c038d224373a19cf2c3dc7a115bbb5be36ef"},
     "permute": {"bytes_per_elem": 14.79,
                 "source": "paper_2009_13569_gb300/csrc/level.cuh",
-                "sha256": "804a39a9b6b6a00b753f9db58c3ea9a51846fa7cc977fdf0222420958c96c93c"},
+                "sha256": "c07bc0cba7502d40a5d5be1d96b17cd64f7fa048aa644845d22c11768c68564f"},
     "base_case": {"bytes_per_elem": 15.10,
                   "source": "paper_2009_13569_gb300/csrc/base.cuh",
                   "sha256": "c3e034fc3bf68f743fe8b4fdd4d89f712152ff2f1af49a634bb2185f108073e6"},

@@ -483,7 +483,8 @@ __global__ void __launch_bounds__(kAuxThreads) k_fixup(LevelArgs a) {
 // in [w_i, r_i] unprocessed, the rest empty.  A CTA runs the virtual CTAs
 // blockIdx.x, blockIdx.x + gridDim.x, ... of the level; workers of a segment
 // never wait for one another except for the bounded reader wait, so they need
-// not run at the same time.
+// not run at the same time.  The bucket of a block is that of its first
+// element, classified by the whole warp (LevelClassifier::warp_class).
 template <class T>
 __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a) {
     typedef typename T::K K;
