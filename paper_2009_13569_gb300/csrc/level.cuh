@@ -521,25 +521,37 @@ __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a) {
             if (!hold) {
                 bool got = false;
                 while (scanned < B) {
+                    // probe the next min(32, B - scanned) buckets with one
+                    // read per lane and move to the first that still has
+                    // unprocessed blocks (the claim below decides)
+                    const uint32_t span = min(32u, B - scanned);
+                    bool cand = false;
+                    if ((uint32_t)lane < span) {
+                        uint32_t q = p + (uint32_t)lane;
+                        if (q >= B) q -= B;
+                        const unsigned long long vq = *(volatile unsigned long long *)&ar.ptr[q];
+                        cand = (int64_t)(uint32_t)vq - (int64_t)kRBias > (int64_t)(vq >> 32);
+                    }
+                    const uint32_t found = __ballot_sync(0xffffffffu, cand);
+                    const uint32_t f = found ? (uint32_t)(__ffs(found) - 1) : span;
+                    p += f;
+                    if (p >= B) p -= B;
+                    scanned += f;
+                    if (!found) continue;
                     int res = 0;
                     uint32_t blk = 0;
                     if (lane == 0) {
-                        unsigned long long vv = *(volatile unsigned long long *)&ar.ptr[p];
-                        int64_t w = (int64_t)(vv >> 32);
-                        int64_t re = (int64_t)(uint32_t)vv - (int64_t)kRBias;
+                        atomicAdd(&ar.readers[p], 1u);
+                        __threadfence();
+                        unsigned long long old = atomicAdd(&ar.ptr[p], ~0ull);  // r - 1
+                        const int64_t w = (int64_t)(old >> 32);
+                        const int64_t re = (int64_t)(uint32_t)old - (int64_t)kRBias;
                         if (re > w) {
-                            atomicAdd(&ar.readers[p], 1u);
+                            blk = (uint32_t)(re - 1);
+                            res = 1;
+                        } else {
                             __threadfence();
-                            unsigned long long old = atomicAdd(&ar.ptr[p], ~0ull);  // r - 1
-                            w = (int64_t)(old >> 32);
-                            re = (int64_t)(uint32_t)old - (int64_t)kRBias;
-                            if (re > w) {
-                                blk = (uint32_t)(re - 1);
-                                res = 1;
-                            } else {
-                                __threadfence();
-                                atomicSub(&ar.readers[p], 1u);
-                            }
+                            atomicSub(&ar.readers[p], 1u);
                         }
                     }
                     res = __shfl_sync(0xffffffffu, res, 0);
