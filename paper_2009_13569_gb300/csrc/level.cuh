@@ -25,7 +25,7 @@
 
 namespace ipsgpu {
 
-constexpr int kSampleThreads = 512;
+constexpr int kSampleThreads = 1024;
 // Samples per bucket: bucket sizes spread by about 1/sqrt of it, and every
 // child above the base-case size costs another partitioning pass, so the
 // sample is larger than the paper's alpha k on the GPU.
@@ -175,21 +175,31 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample_tree(LevelArgs a) {
             uint32_t P = 1;
             while (P < m) P <<= 1;
             const uint64_t sseed = a.seed ^ (sd.addr * 0xD1B54A32D192ED03ull) ^ (sd.n << 17);
-            for (uint32_t t = tid; t < P; t += blockDim.x) {
-                if (t < m) {
-                    uint64_t idx = splitmix64(sseed + t * 0x9E3779B97F4A7C15ull) % sd.n;
-                    smp[t] = T::key(base[idx]);
-                } else {
-                    smp[t] = T::max_key();
+            // random gather, four keys in flight per thread
+            for (uint32_t t0 = tid; t0 < P; t0 += 4 * blockDim.x) {
+                K kx[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t t = t0 + q * blockDim.x;
+                    if (t < m) {
+                        const uint64_t idx = splitmix64(sseed + t * 0x9E3779B97F4A7C15ull) % sd.n;
+                        kx[q] = T::key(base[idx]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t t = t0 + q * blockDim.x;
+                    if (t < P) smp[t] = t < m ? kx[q] : T::max_key();
                 }
             }
             __syncthreads();
-            // bitonic sort of smp[0..P)
+            // bitonic sort of smp[0..P); j is a power of two, so compare-
+            // exchange i pairs lo = 2 j (i / j) + i mod j with lo + j
             for (uint32_t k = 2; k <= P; k <<= 1) {
-                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t j = k >> 1, lj = ilog2_floor(k) - 1; j > 0; j >>= 1, lj--) {
                     for (uint32_t i = tid; i < P / 2; i += blockDim.x) {
-                        uint32_t lo = 2 * j * (i / j) + (i % j);
-                        uint32_t hi = lo + j;
+                        const uint32_t lo = ((i >> lj) << (lj + 1)) | (i & (j - 1));
+                        const uint32_t hi = lo + j;
                         bool up = (lo & k) == 0;
                         K x = smp[lo], y = smp[hi];
                         if ((y < x) == up) {
