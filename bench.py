@@ -215,8 +215,8 @@ NCU_TRAFFIC = {
                  "sha256": "217f874a56bbf29af09547ba7213c038d224373a19cf2c3dc7a115bbb5be36ef"},
     "permute": {"bytes_per_elem": 14.79,
                 "source": "paper_2009_13569_gb300/csrc/level.cuh",
-                "sha256": "c07bc0cba7502d40a5d5be1d96b17cd64f7fa048aa644845d22c11768c68564f"},
-    "base_case": {"bytes_per_elem": 15.10,
+                "sha256": "1ff600e02d09ef4a2376787df01db9966d6ee2b1ee140d57684ae59b2c5fd67d"},
+    "base_case": {"bytes_per_elem": 15.11,
                   "source": "paper_2009_13569_gb300/csrc/base.cuh",
                   "sha256": "c3e034fc3bf68f743fe8b4fdd4d89f712152ff2f1af49a634bb2185f108073e6"},
 }
