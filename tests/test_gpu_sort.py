@@ -83,6 +83,40 @@ def test_sort_quartet_sizes(n):
     assert_sorted_parity(run_sort("quartet", host), inputs.to_numpy(host, "quartet"), "quartet")
 
 
+CAPACITY = {d: 184 * 1024 // inputs.ELEM_BYTES[d] for d in inputs.ELEM_BYTES}
+BOUNDARY_DIST = {"u32": "uniform", "u64": "twodup", "f64": "normal", "pair": "rootdup",
+                 "quartet": "uniform", "rec100": "uniform"}
+
+
+@pytest.mark.parametrize("dtype", sorted(CAPACITY))
+@pytest.mark.parametrize("rel", [-1, 0, 1, "2x+1"])
+def test_sort_around_base_case_capacity(dtype, rel):
+    # the largest segment the shared-memory base case takes (184 KiB of
+    # records) and its neighbours: one base-case call, or one level first
+    cap = CAPACITY[dtype]
+    n = 2 * cap + 1 if rel == "2x+1" else cap + rel
+    host = inputs.generate(BOUNDARY_DIST[dtype], dtype, n, seed=cap % 97)
+    assert_sorted_parity(run_sort(dtype, host), inputs.to_numpy(host, dtype), dtype)
+
+
+@pytest.mark.parametrize("dtype", ["u64", "pair", "quartet", "rec100"])
+@pytest.mark.parametrize("k", [4, 32])
+def test_sort_small_k_every_type(dtype, k):
+    # few buckets per level: many levels, small class budgets
+    dist = "rootdup" if dtype == "rec100" else "uniform"
+    host = inputs.generate(dist, dtype, 60_001 if dtype == "rec100" else 200_003, seed=k)
+    assert_sorted_parity(run_sort(dtype, host, k=k), inputs.to_numpy(host, dtype), dtype)
+
+
+@pytest.mark.parametrize("seed,alpha", [(1, 0.2), (0xDEADBEEF, 0.5), (7, 1.0)])
+def test_sampling_choices_do_not_change_the_result(seed, alpha):
+    # other sample positions and sizes give other splitters and levels, but
+    # the sorted sequence is unique: identical to the oracle's bit for bit
+    host = inputs.generate("zipf", "u64", 400_003, seed=11)
+    got = run_sort("u64", host, seed=seed, alpha_scale=alpha, base_case=2048)
+    np.testing.assert_array_equal(got, oracle.sort(inputs.to_numpy(host, "u64"), "u64"))
+
+
 def test_sort_quartet_deep_ties():
     # long runs equal in the first word, then in the first two: the radix
     # passes of the base case move on to the second and third words, and
