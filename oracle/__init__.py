@@ -44,27 +44,31 @@ def build(force=False):
     return _LIB_PATH
 
 
+def _configure(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    u64, u32, i32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_void_p
+    lib.oracle_sort.argtypes = [i32, vp, u64, u32, u32, ctypes.c_double, u64]
+    lib.oracle_sort.restype = i32
+    lib.oracle_insertion_sort.argtypes = [i32, vp, u64]
+    lib.oracle_insertion_sort.restype = i32
+    lib.oracle_is_sorted.argtypes = [i32, vp, u64]
+    lib.oracle_is_sorted.restype = i32
+    lib.oracle_classify.argtypes = [i32, vp, u64, vp, u32, i32, vp]
+    lib.oracle_classify.restype = u32
+    lib.oracle_radix_classify.argtypes = [i32, vp, u64, u32, u32, vp]
+    lib.oracle_radix_classify.restype = u32
+    lib.oracle_partition.argtypes = [i32, vp, u64, vp, u32, vp, vp]
+    lib.oracle_partition.restype = None
+    lib.oracle_elem_size.argtypes = [i32]
+    lib.oracle_elem_size.restype = i32
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB_PATH)
-        u64, u32, i32, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_void_p
-        lib.oracle_sort.argtypes = [i32, vp, u64, u32, u32, ctypes.c_double, u64]
-        lib.oracle_sort.restype = i32
-        lib.oracle_insertion_sort.argtypes = [i32, vp, u64]
-        lib.oracle_insertion_sort.restype = i32
-        lib.oracle_is_sorted.argtypes = [i32, vp, u64]
-        lib.oracle_is_sorted.restype = i32
-        lib.oracle_classify.argtypes = [i32, vp, u64, vp, u32, i32, vp]
-        lib.oracle_classify.restype = u32
-        lib.oracle_radix_classify.argtypes = [i32, vp, u64, u32, u32, vp]
-        lib.oracle_radix_classify.restype = u32
-        lib.oracle_partition.argtypes = [i32, vp, u64, vp, u32, vp, vp]
-        lib.oracle_partition.restype = None
-        lib.oracle_elem_size.argtypes = [i32]
-        lib.oracle_elem_size.restype = i32
-        _lib = lib
+        _lib = _configure(ctypes.CDLL(_LIB_PATH))
     return _lib
 
 

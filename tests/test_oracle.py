@@ -148,9 +148,14 @@ def test_pair_keys_sorted_and_records_kept():
 @pytest.mark.parametrize("dist", inputs.REC_DISTS)
 def test_rec100_lexicographic_unsigned_bytes(dist):
     n = 3000
-    a = inputs.to_numpy(inputs.generate(dist, "rec100", n), "rec100")
-    # make some keys differ only in byte 9 and use bytes >= 0x80 (sign test)
-    a[::7, 9] = 0xF0
+    a = inputs.to_numpy(inputs.generate(dist, "rec100", n), "rec100").copy()
+    # pairs of records equal in bytes 0..8 that differ only in byte 9, on
+    # either side of 0x80, the larger one first (a 9-byte compare keeps
+    # their input order, a signed-char compare reverses them)
+    m = len(a[1::7])
+    a[1::7, :9] = a[0::7, :9][:m]
+    a[0::7, 9] = 0xF0
+    a[1::7, 9] = 0x10
     got = oracle.sort(a, "rec100", k=16, n0=4)
     keys = [bytes(r[:10]) for r in got]
     assert keys == sorted(bytes(r[:10]) for r in a)  # Python bytes: unsigned
