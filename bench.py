@@ -65,6 +65,9 @@ def _args():
                    help="comma-separated algorithms the sweep runs: IPS4o, IPS2Ra (u32/u64 "
                         "only) and IPS4o-tree (IPS4o walking every element from the tree's "
                         "root, without the start-node table)")
+    p.add_argument("--batched-only", action="store_true",
+                   help="only the batched form's graph launches (both workloads), one JSON "
+                        "line: the command of the batched launch-list profile")
     p.add_argument("--instrumented", action="store_true",
                    help="run every sort from the host-driven wave loop (the same kernels, no "
                         "CUDA graph): the form the ncu captures in profiles/ use")
@@ -283,10 +286,15 @@ SEG_WORKLOADS = (
 )
 
 
-def run_segmented(torch, inputs, ipsgpu, dev, steps):
+def run_segmented(torch, inputs, ipsgpu, dev, steps, graph_only=False, instrumented=False):
     """Batched form: many uint64 arrays of log-uniform lengths, mixed
     Uniform / TwoDup / AlmostSorted, sorted by one launch of a captured CUDA
-    graph, against one plain ipsgpu_sort call per array on the same GPU."""
+    graph, against one plain ipsgpu_sort call per array on the same GPU.
+    graph_only: the graph launches alone (no per-array baseline, no
+    autotuning); with instrumented, the same sorts run from the host-driven
+    wave loop (ipsgpu_sort_segmented with kernel timing), whose kernels a
+    profiler can take one by one: the form of the batched launch-list
+    profile."""
     out = {}
     st = torch.cuda.Stream(dev)
     for name, count, lo, hi, total in SEG_WORKLOADS:
@@ -301,6 +309,7 @@ def run_segmented(torch, inputs, ipsgpu, dev, steps):
         work = torch.empty_like(src)
         sorter = ipsgpu.Sorter("u64")
         g = sorter.segmented_graph(work.data_ptr(), N, offsets.data_ptr(), lengths.numel())
+        sorter.set_timing(instrumented)
         ts = []
         for i in range(2 + steps):
             work.copy_(src)
@@ -308,13 +317,30 @@ def run_segmented(torch, inputs, ipsgpu, dev, steps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            g.launch(st.cuda_stream)
+            if instrumented:
+                sorter.sort_segmented(work.data_ptr(), N, offsets.data_ptr(), lengths.numel(),
+                                      st.cuda_stream)
+            else:
+                g.launch(st.cuda_stream)
             e1.record(st)
             st.synchronize()
             if i >= 2:
                 ts.append(e0.elapsed_time(e1))
         ok = sorter.status(st.cuda_stream) == ipsgpu.OK and _segments_sorted(torch, work, offsets)
         gms = sum(ts) / len(ts)
+        if graph_only:
+            out[name] = {"arrays": int(lengths.numel()), "elements": N,
+                         "form": "host-driven waves" if instrumented else "CUDA graph",
+                         "ms": gms, "value": N / (gms * 1e-3) / 1e9, "unit": UNIT,
+                         "result_sorted": ok}
+            if instrumented:
+                out[name]["kernels_ms"] = {k: round(v[1] / (2 + steps), 3)
+                                           for k, v in sorter.kernel_stats().items() if v[0]}
+            g.close()
+            sorter.close()
+            del src, work
+            torch.cuda.empty_cache()
+            continue
         # one plain sort call per array (the per-array baseline), one pass
         work.copy_(src)
         torch.cuda.synchronize(dev)
@@ -969,12 +995,25 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+def run_batched_only(args):
+    import torch
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2009_13569_gb300 import inputs, ipsgpu
+    dev = torch.device("cuda", 0)
+    seg = run_segmented(torch, inputs, ipsgpu, dev, args.steps, graph_only=True,
+                        instrumented=args.instrumented)
+    print(json.dumps({"batched_only": True, "segmented": seg}))
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
     elif args.sweep:
         run_sweep(args)
+    elif args.batched_only:
+        run_batched_only(args)
     else:
         run_ours(args)
 

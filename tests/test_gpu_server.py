@@ -167,3 +167,44 @@ def test_server_cancel_reserved_and_queued_requests():
         for t in (t0, t1, t2):
             srv.release(t)
         assert srv.usage()[0] == srv.usage()[2]
+
+
+def test_server_many_client_threads():
+    # four host threads submit, wait for and release requests of mixed sizes
+    # and types at the same time; every result is the oracle's
+    import threading
+    import time
+    types = ("u32", "u64", "pair", "quartet")
+    errors = []
+    with ipsgpu.Server(16 << 30, lanes=3, dtypes=types, batch_max_elems=1 << 14) as srv:
+        def client(c):
+            try:
+                rng = np.random.default_rng(c)
+                for i in range(12):
+                    dtype = types[(c + i) % 4]
+                    n = int(2 ** rng.uniform(4, 18))
+                    host = inputs.generate(DISTS[i % len(DISTS)], dtype, n, seed=100 * c + i)
+                    d = host.to(DEV)
+                    torch.cuda.synchronize()
+                    t = None
+                    for _ in range(10_000):  # admitted once others release
+                        t = srv.reserve(n, dtype)
+                        if t is not None:
+                            break
+                        time.sleep(0.001)
+                    assert t is not None
+                    srv.start(t, d.data_ptr())
+                    assert srv.wait(t) == ipsgpu.OK
+                    assert_sorted_parity(inputs.to_numpy(d.cpu(), dtype),
+                                         inputs.to_numpy(host, dtype), dtype)
+                    srv.release(t)
+            except Exception as e:  # reported by the main thread
+                errors.append(e)
+
+        threads = [threading.Thread(target=client, args=(c,)) for c in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join(timeout=300)
+        assert not errors, errors[0]
+        assert srv.usage()[0] == srv.usage()[2]
