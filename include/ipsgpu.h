@@ -90,8 +90,9 @@ enum {
  *                     k buffer blocks fit in one SM's shared memory)
  *   alpha_scale       oversampling alpha = alpha_scale * log2(n') (0.2, Sec. 5)
  *   base_case         largest segment sorted by the shared-memory base case
- *                     (elements; default: as many as fit, 24576 for 8-byte
- *                     elements)
+ *                     (elements; at least 32; default and maximum: as many
+ *                     as fit in 184 KiB, 23552 for 8-byte elements, 5888
+ *                     Quartets, 1884 100-byte records)
  *   seed              seed of the sampling generator (splitmix64)
  *   algo              ipsgpu_algo
  *   spin_limit        iterations of a bounded device wait before it gives up
@@ -130,7 +131,9 @@ int ipsgpu_sorter_prepare(ipsgpu_sorter *s);
 int ipsgpu_sorter_destroy(ipsgpu_sorter *s);
 
 /* Device scratch bytes a sorter with these parameters allocates: a constant
- * times k * block_bytes per stripe/segment slot, independent of n. */
+ * times k * block_bytes per stripe/segment slot, independent of n (plus
+ * under 64 KiB of fixed-size state and guard zones).  0 if the parameters
+ * are invalid for the dtype. */
 uint64_t ipsgpu_scratch_bytes(const ipsgpu_params *params, int dtype);
 
 /* Sort d_data[0..n) in place, ascending in the key order of the sorter's
