@@ -1,8 +1,10 @@
-// ipsgpu.cu -- the C ABI (include/ipsgpu.h) and the host-side driver of the
-// recursion: detect easy inputs, partition large segments level by level
-// (batches of segments per launch), hand segments that fit shared memory to
-// the base case (Sec. 3.2 task structure, Sec. 5 parameters; the recursion
-// on a GPU is breadth-first over all segments of a level).
+// ipsgpu.cu -- the C ABI (include/ipsgpu.h) on the host side: parameter
+// resolution and scratch (with guard zones), easy-input detection, the CUDA
+// graph that runs the device-planned recursion (graph.cuh: waves over all
+// pending segments, Sec. 3.2 task structure breadth-first, Sec. 5
+// parameters) or its host-driven twin when kernels are timed, host-planned
+// single levels (partition_level, radix_level, classify), batched and
+// segmented runs, and the host-array call.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
