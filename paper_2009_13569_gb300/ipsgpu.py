@@ -19,12 +19,14 @@ OK, E_INVAL, E_UNSUPPORTED, E_NOMEM, E_CUDA, E_TIMEOUT, E_BUSY, E_INTERNAL, E_CA
 
 
 class IpsgpuError(RuntimeError):
+    """A non-zero status of a C-ABI call (`code` is the ipsgpu status)."""
     def __init__(self, code, what):
         self.code = code
         super().__init__("%s: %s (status %d)" % (what, strerror(code) if _lib else "?", code))
 
 
 class Params(ctypes.Structure):
+    """ipsgpu_params: zero fields take the library defaults."""
     _fields_ = [("k", ctypes.c_uint32), ("block_bytes", ctypes.c_uint32),
                 ("alpha_scale", ctypes.c_float), ("base_case", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("algo", ctypes.c_int32),
@@ -32,6 +34,7 @@ class Params(ctypes.Structure):
 
 
 class ServerConfig(ctypes.Structure):
+    """ipsgpu_server_config: zero fields take the library defaults."""
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("batch_max_elems", ctypes.c_uint64),
                 ("small_reserve_bytes", ctypes.c_uint64),
                 ("lanes", ctypes.c_uint32), ("dtype_mask", ctypes.c_uint32),
@@ -120,6 +123,7 @@ def exported_symbols():
 
 
 def strerror(code):
+    """Message of an ipsgpu status code (ipsgpu_strerror)."""
     return load().ipsgpu_strerror(code).decode()
 
 
@@ -139,10 +143,12 @@ def partition_level_noalloc(dtype, ptr, n, spl_ptr, num_splitters, equal_buckets
 
 def make_params(k=0, block_bytes=0, alpha_scale=0.0, base_case=0, seed=0, algo=SAMPLESORT,
                 spin_limit=0, arena_bytes=0):
+    """An ipsgpu_params structure (see include/ipsgpu.h for each field)."""
     return Params(k, block_bytes, alpha_scale, base_case, seed, algo, spin_limit, arena_bytes)
 
 
 def scratch_bytes(dtype, **params):
+    """Device scratch of a sorter with these parameters (0: invalid)."""
     p = make_params(**params)
     return int(load().ipsgpu_scratch_bytes(ctypes.byref(p), DTYPES[dtype]))
 
@@ -161,6 +167,7 @@ class Sorter:
         self._h = h
 
     def close(self):
+        """Free the underlying library object (also on leaving a with block)."""
         if self._h:
             load().ipsgpu_sorter_destroy(self._h)
             self._h = None
@@ -182,6 +189,7 @@ class Sorter:
         _check(load().ipsgpu_sorter_prepare(self._h), "ipsgpu_sorter_prepare")
 
     def sort(self, ptr, n, stream=0):
+        """Sort ptr[0..n) in place on the device (ipsgpu_sort), queued on stream."""
         _check(load().ipsgpu_sort(self._h, ptr, n, stream), "ipsgpu_sort")
 
     def sort_host(self, in_ptr, out_ptr, n, work_ptr, stream=0):
@@ -207,15 +215,20 @@ class Sorter:
         return SegmentedGraph(self, ptr, n, offsets_ptr, num_segments)
 
     def partition_level(self, ptr, n, spl_ptr, num_splitters, equal_buckets, bb_ptr, stream=0):
+        """One partitioning step with given sorted splitters; bucket begins
+        (u64, B + 1 of them) to bb_ptr (ipsgpu_partition_level)."""
         _check(load().ipsgpu_partition_level(self._h, ptr, n, spl_ptr, num_splitters,
                                              1 if equal_buckets else 0, bb_ptr, stream),
                "ipsgpu_partition_level")
 
     def radix_level(self, ptr, n, shift, bits, bb_ptr, stream=0):
+        """One IPS2Ra step on key bits [shift, shift + bits) (ipsgpu_radix_level)."""
         _check(load().ipsgpu_radix_level(self._h, ptr, n, shift, bits, bb_ptr, stream),
                "ipsgpu_radix_level")
 
     def classify(self, ptr, n, spl_ptr, num_splitters, equal_buckets, cls_ptr, stream=0):
+        """Class id of every element to cls_ptr (u32), data not moved
+        (ipsgpu_classify)."""
         _check(load().ipsgpu_classify(self._h, ptr, n, spl_ptr, num_splitters,
                                       1 if equal_buckets else 0, cls_ptr, stream),
                "ipsgpu_classify")
@@ -225,6 +238,8 @@ class Sorter:
         return load().ipsgpu_status(self._h, stream)
 
     def set_timing(self, enable=True):
+        """Per-kernel CUDA-event timing on or off (ipsgpu_set_timing); while
+        on, sorts run from the host-driven wave loop."""
         _check(load().ipsgpu_set_timing(self._h, 1 if enable else 0), "ipsgpu_set_timing")
 
     def kernel_stats(self):
@@ -252,6 +267,8 @@ class Sorter:
         raise IpsgpuError(rc, "ipsgpu_debug_check_guards")
 
     def debug_bounded_wait(self, spin_limit, stream=0):
+        """Run the permutation's bounded wait on a flag nothing sets; the
+        status then reads IPSGPU_E_TIMEOUT (ipsgpu_debug_bounded_wait)."""
         _check(load().ipsgpu_debug_bounded_wait(self._h, spin_limit, stream),
                "ipsgpu_debug_bounded_wait")
 
@@ -269,14 +286,17 @@ class SegmentedGraph:
         self._h = h
 
     def launch(self, stream=0):
+        """Launch the captured segmented sort (ipsgpu_graph_launch)."""
         _check(load().ipsgpu_graph_launch(self._h, stream), "ipsgpu_graph_launch")
 
     def nodes(self):
+        """Top-level nodes of the captured graph (ipsgpu_graph_nodes)."""
         v = ctypes.c_uint64()
         _check(load().ipsgpu_graph_nodes(self._h, ctypes.byref(v)), "ipsgpu_graph_nodes")
         return int(v.value)
 
     def close(self):
+        """Free the underlying library object (also on leaving a with block)."""
         if self._h:
             load().ipsgpu_graph_destroy(self._h)
             self._h = None
@@ -316,6 +336,8 @@ class Server:
         return int(t.value)
 
     def start(self, ticket, ptr, ready_stream=0):
+        """Queue a reserved request on data at ptr; the sort waits for the work
+        queued so far on ready_stream (ipsgpu_server_start)."""
         _check(load().ipsgpu_server_start(self._h, ticket, ptr, ready_stream),
                "ipsgpu_server_start")
 
@@ -348,9 +370,11 @@ class Server:
 
     @staticmethod
     def now_us():
+        """The server's clock in microseconds (ipsgpu_server_now_us)."""
         return load().ipsgpu_server_now_us()
 
     def release(self, ticket):
+        """Give a finished request's footprint back (ipsgpu_server_release)."""
         _check(load().ipsgpu_server_release(self._h, ticket), "ipsgpu_server_release")
 
     def cancel(self, ticket):
@@ -358,6 +382,7 @@ class Server:
         _check(load().ipsgpu_server_cancel(self._h, ticket), "ipsgpu_server_cancel")
 
     def drain(self):
+        """Wait until no request is queued or running (ipsgpu_server_drain)."""
         _check(load().ipsgpu_server_drain(self._h), "ipsgpu_server_drain")
 
     def usage(self):
@@ -368,6 +393,7 @@ class Server:
         return int(u.value), int(b.value), int(s.value)
 
     def close(self):
+        """Free the underlying library object (also on leaving a with block)."""
         if self._h:
             load().ipsgpu_server_destroy(self._h)
             self._h = None
