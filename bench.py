@@ -568,12 +568,14 @@ def run_serve(torch, inputs, ipsgpu, dev):
             "budget_gb": cfg["budget_gb"], "lanes": cfg["lanes"],
             "server": {"p50_ms": float(np.percentile(lat, 50)) * 1e-3,
                        "p99_ms": float(np.percentile(lat, 99)) * 1e-3,
+                       "latency_ms": latency_summary(lat),
                        "max_admission_wait_ms": wait_max * 1e-3,
                        "value_at_load": elems / span / 1e9,
                        "value_saturated": elems / sat_span / 1e9, "unit": UNIT,
                        "result_sorted": srv_ok and sat_ok},
             "plain_fifo": {"p50_ms": float(np.percentile(fifo_lat, 50)) * 1e-3,
                            "p99_ms": float(np.percentile(fifo_lat, 99)) * 1e-3,
+                           "latency_ms": latency_summary(fifo_lat),
                            "value_at_load": elems / fifo_span / 1e9,
                            "value_saturated": elems / (total_service * 1e-6) / 1e9, "unit": UNIT,
                            "result_sorted": fifo_ok},
@@ -581,6 +583,23 @@ def run_serve(torch, inputs, ipsgpu, dev):
                        "included; plain_fifo latencies follow from the measured service time of "
                        "each request sorted alone, one after another in arrival order",
             "saturated": "every request available at once: elements / makespan"}
+
+
+def latency_summary(lat_us):
+    """Percentiles, mean and a histogram over powers of two of request
+    latencies given in microseconds (all figures in milliseconds)."""
+    import numpy as np
+    a = np.asarray(lat_us, dtype=np.float64) * 1e-3
+    if a.size == 0:
+        return {"count": 0}
+    hist = {}
+    for x in a:
+        e = int(np.floor(np.log2(x))) if x > 0 else -30
+        hist[e] = hist.get(e, 0) + 1
+    return {"count": int(a.size), "p50_ms": float(np.percentile(a, 50)),
+            "p90_ms": float(np.percentile(a, 90)), "p99_ms": float(np.percentile(a, 99)),
+            "mean_ms": float(a.mean()), "max_ms": float(a.max()),
+            "histogram_ms": [[2.0 ** e, 2.0 ** (e + 1), c] for e, c in sorted(hist.items())]}
 
 
 PARTITION_KERNELS = ("sample_tree", "classify", "prep", "fixup", "permute", "stage", "fill", "plan")

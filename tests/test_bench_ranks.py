@@ -102,3 +102,14 @@ def test_e2e_lanes_fit_host_memory():
     assert bench.e2e_lanes(8 * gib, 8, 400 * gib) == 2
     assert bench.e2e_lanes(8 * gib, 8, 200 * gib) == 1
     assert bench.e2e_lanes(8 * gib, 1, 0) == 1  # unknown: the sequential form only
+
+
+def test_latency_summary():
+    sys.path.insert(0, ROOT)
+    import bench
+    s = bench.latency_summary([1000.0, 1500.0, 3000.0, 100_000.0])  # microseconds
+    assert s["count"] == 4 and s["max_ms"] == 100.0
+    assert s["p50_ms"] == pytest.approx(2.25)
+    # bins [1, 2) ms: 1.0 and 1.5; [2, 4): 3.0; [64, 128): 100
+    assert s["histogram_ms"] == [[1.0, 2.0, 2], [2.0, 4.0, 1], [64.0, 128.0, 1]]
+    assert bench.latency_summary([]) == {"count": 0}
