@@ -1,6 +1,5 @@
 """The autotuner on the GPU: the parameters it picks for a segmented batch
 and for plain arrays sort correctly (checked against the oracle)."""
-import numpy as np
 import pytest
 import torch
 
