@@ -160,20 +160,41 @@ __device__ __forceinline__ void store_unit(unsigned char *dst, const unsigned ch
 // (with their own min/max).  Every pass writes its range back to global
 // memory (coalesced), so the global copy of a pending range always matches
 // the shared one.
-template <class T>
-__global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
-                                                          uint32_t nsegs_host,
-                                                          const uint32_t *nsegs_dev, int *status) {
+//
+// Two shapes share the code (BaseShape): one 1024-thread CTA per SM with
+// 184 KiB of elements, and two 512-thread CTAs per SM with 88 KiB each, which
+// take the segments that fit so that one CTA's loads and stores overlap the
+// other's counting and scattering.  A launch sorts the listed segments with
+// n_lo < n <= n_hi.
+template <int NT_, int BUF_, int MAXB_, int SSTK_>
+struct BaseShape {
+    static constexpr int NT = NT_;          // threads of a CTA
+    static constexpr int BUF = BUF_;        // element buffer bytes
+    static constexpr int MAXB = MAXB_;      // digit bits of the counter array
+    static constexpr int SSTK = SSTK_;      // pending small ranges (>= BUF / 4 / 25)
+    static constexpr int CTAS = 1024 / NT_;  // CTAs per SM
+};
+typedef BaseShape<1024, kBaseSmemBytes, kBaseDigitBits, kBaseSmallStack> BaseLarge;
+typedef BaseShape<512, 88 * 1024, kBaseDigitBits - 1, 1024> BaseSmall;
+
+template <class T, class S>
+__global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
+                                                         uint32_t nsegs_host,
+                                                         const uint32_t *nsegs_dev, int *status,
+                                                         uint64_t n_lo, uint64_t n_hi) {
     typedef typename T::E E;
     typedef typename T::K K;
+    constexpr int kBaseThreads = S::NT;
     // Digits per pass: about two elements per digit for keys up to 8 bytes,
     // one for wider records (whose insertion-sort moves cost more), at most
-    // 2^14 digits for 4-byte keys and 2^13 otherwise (measured optima) --
-    // unless one digit per key value fits in 2^kBaseDigitBits digits and at
-    // most twice that many: then the pass is final (no insertion sorts)
-    constexpr int DBITS = T::D <= 4 ? kBaseDigitBits : kBaseDigitBits - 1;
+    // 2^14 digits for 4-byte keys and 2^13 otherwise (measured optima; 2^13
+    // in the small shape) -- unless one digit per key value fits in 2^MAXB
+    // digits and at most twice that many: then the pass is final (no
+    // insertion sorts)
+    constexpr int DBITS = T::D <= 4 ? S::MAXB
+                                    : (S::MAXB < kBaseDigitBits - 1 ? S::MAXB : kBaseDigitBits - 1);
     constexpr uint32_t kPerDigitLog = T::D <= 8 ? 1u : 0u;
-    constexpr int ND = 1 << kBaseDigitBits;
+    constexpr int ND = 1 << S::MAXB;
     constexpr int NB = T::D <= 8 ? 8 : (T::D <= 16 ? 4 : (T::D <= 32 ? 2 : 1));  // in flight per thread
     constexpr int U = T::D % 16 == 0 ? 16 : (T::D % 8 == 0 ? 8 : 4);  // copy-out unit
     extern __shared__ __align__(16) unsigned char smem[];
@@ -182,9 +203,9 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
     // suffice.
     // Digits 2w and 2w + 1 share word w.
     E *buf = reinterpret_cast<E *>(smem);
-    uint32_t *stk = reinterpret_cast<uint32_t *>(smem + kBaseSmemBytes);   // (a0 << 16) | len
-    uint32_t *sstk = stk + kBaseStack;                                     // small ranges
-    uint32_t *cur = sstk + kBaseSmallStack;                                // ND / 2
+    uint32_t *stk = reinterpret_cast<uint32_t *>(smem + S::BUF);  // (a0 << 16) | len
+    uint32_t *sstk = stk + kBaseStack;                            // small ranges
+    uint32_t *cur = sstk + S::SSTK;                               // ND / 2
     uint32_t *wtmp = cur + ND / 2;                                         // 34
     __shared__ unsigned long long red[2][32];
     __shared__ uint32_t sp, ssp, sh_top;
@@ -220,12 +241,13 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
     const uint32_t nsegs = nsegs_dev ? *nsegs_dev : nsegs_host;
     for (uint32_t si = blockIdx.x; si < nsegs; si += gridDim.x) {
         const uint64_t addr = segs[2 * si], n = segs[2 * si + 1];
+        if (n <= n_lo || n > n_hi) continue;  // the other shape's segment
         E *g = reinterpret_cast<E *>(addr);
         if (tid == 0 && si + gridDim.x < nsegs) {
             // the CTA's next segment streams into L2 while this one is sorted
             const uint64_t na = segs[2 * (si + gridDim.x)], nn = segs[2 * (si + gridDim.x) + 1];
             const uint64_t lo = (na + 15) & ~15ull, hi = (na + nn * T::D) & ~15ull;
-            if (hi > lo) prefetch_l2(lo, (uint32_t)(hi - lo));
+            if (nn > n_lo && nn <= n_hi && hi > lo) prefetch_l2(lo, (uint32_t)(hi - lo));
         }
         if (n <= 1) continue;
         if (n <= 32) {
@@ -325,7 +347,7 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
             uint32_t want = 1;
             while (want < (uint32_t)DBITS && ((1u << kPerDigitLog) << want) < len) want++;
             const uint32_t dbits =
-                (nbits <= (uint32_t)kBaseDigitBits && nbits <= want + 1) ? nbits : min(nbits, want);
+                (nbits <= (uint32_t)S::MAXB && nbits <= want + 1) ? nbits : min(nbits, want);
             const uint32_t shift = nbits - dbits;
             const uint32_t nd = 1u << dbits;
             const uint32_t nw = (nd + 1) >> 1;  // counter words in use
@@ -412,7 +434,7 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
                         set_status(status, IPSGPU_E_INTERNAL);
                 } else if (c > kBaseInsertion) {
                     uint32_t q = atomicAdd(&ssp, 1u);
-                    if (q < kBaseSmallStack)
+                    if (q < (uint32_t)S::SSTK)
                         sstk[q] = ((a0 + lo) << 16) | c;
                     else
                         set_status(status, IPSGPU_E_INTERNAL);
@@ -445,7 +467,7 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
         // otherwise each element goes to its rank within the range (ties by
         // position), straight to global memory.  Shared memory holds the
         // range as the last pass grouped it, like its global copy.
-        const uint32_t nsmall = min(ssp, (uint32_t)kBaseSmallStack);
+        const uint32_t nsmall = min(ssp, (uint32_t)S::SSTK);
         for (uint32_t r = warp; r < nsmall; r += NW) {
             const uint32_t top = sstk[r];
             const uint32_t a0 = top >> 16, c = top & 0xFFFFu;
@@ -488,9 +510,10 @@ __global__ void __launch_bounds__(kBaseThreads, 1) k_base(const uint64_t *segs,
     }
 }
 
+template <class S>
 inline size_t base_smem_bytes() {
-    return kBaseSmemBytes + sizeof(uint32_t) * (kBaseStack + kBaseSmallStack) +
-           sizeof(uint32_t) * ((1 << kBaseDigitBits) / 2 + 34) + 16;
+    return S::BUF + sizeof(uint32_t) * (kBaseStack + S::SSTK) +
+           sizeof(uint32_t) * ((1 << S::MAXB) / 2 + 34) + 16;
 }
 
 }  // namespace ipsgpu

@@ -27,8 +27,13 @@ struct OpsImpl {
         e = cudaFuncSetAttribute(k_sample_tree<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sample_smem());
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_base<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)base_smem_bytes());
+        e = cudaFuncSetAttribute(k_base<T, BaseLarge>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)base_smem_bytes<BaseLarge>());
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_base<T, BaseSmall>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)base_smem_bytes<BaseSmall>());
         return e;
     }
 
@@ -68,9 +73,13 @@ struct OpsImpl {
     static cudaError_t base(Sorter *s, const uint64_t *d_segs, uint32_t nsegs,
                             const uint32_t *nsegs_dev, uint32_t grid, cudaStream_t st) {
         if (grid == 0) return cudaSuccess;
+        // segments that fit the small shape: two CTAs per SM; the rest: one
+        const uint64_t small_cap = (uint64_t)BaseSmall::BUF / T::D;
         s->tbegin(KK_BASE, 2.0 * (double)s->level_elems * T::D, st);
-        k_base<T><<<grid, kBaseThreads, base_smem_bytes(), st>>>(d_segs, nsegs, nsegs_dev,
-                                                                 s->d_status);
+        k_base<T, BaseSmall><<<2 * grid, BaseSmall::NT, base_smem_bytes<BaseSmall>(), st>>>(
+            d_segs, nsegs, nsegs_dev, s->d_status, 0ull, small_cap);
+        k_base<T, BaseLarge><<<grid, BaseLarge::NT, base_smem_bytes<BaseLarge>(), st>>>(
+            d_segs, nsegs, nsegs_dev, s->d_status, small_cap, ~0ull);
         s->tend(st);
         return cudaGetLastError();
     }
