@@ -4,6 +4,7 @@ behave.  No kernel runs here."""
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -69,3 +70,38 @@ def test_server_config_struct_layout():
     assert ctypes.sizeof(ipsgpu.ServerConfig) == 40
     assert ipsgpu.ServerConfig.lanes.offset == 24
     assert ipsgpu.ServerConfig.batch_max_requests.offset == 32
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "ipsgpu.h"
+int main(void) {
+    ipsgpu_params p;
+    memset(&p, 0, sizeof p);
+    size_t a = ipsgpu_scratch_bytes(&p, IPSGPU_U64);
+    size_t b = ipsgpu_scratch_bytes(&p, IPSGPU_QUARTET);
+    printf("%s|%llu|%llu\n", ipsgpu_strerror(IPSGPU_E_TIMEOUT),
+           (unsigned long long)a, (unsigned long long)b);
+    return (a > 0 && b > 0) ? 0 : 1;
+}
+"""
+
+
+@pytest.mark.parametrize("compiler,std", [("gcc", "-std=c99"), ("g++", "-std=c++17")])
+def test_header_is_plain_c_and_links(lib, tmp_path, compiler, std):
+    # the boundary carries no C++ or torch types: the header compiles as
+    # strict C99 (and as C++), and a C program linked against the library
+    # calls its host-only entry points
+    src = tmp_path / ("t.c" if compiler == "gcc" else "t.cpp")
+    src.write_text(C_PROGRAM)
+    libdir = os.path.dirname(lib._name)
+    exe = tmp_path / "t"
+    subprocess.check_call([compiler, std, "-Wall", "-Wextra", "-Werror", "-pedantic",
+                           "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                           "-L", libdir, "-lipsgpu", "-Wl,-rpath," + libdir])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    msg, a, b = out.strip().split("|")
+    assert msg == ipsgpu.strerror(ipsgpu.E_TIMEOUT)
+    assert int(a) == ipsgpu.scratch_bytes("u64")
+    assert int(b) == ipsgpu.scratch_bytes("quartet")
