@@ -66,6 +66,26 @@ def test_segmented_u64_base_case_boundary():
     _check_segments(got, inputs.to_numpy(data, "u64"), offsets.numpy(), "u64")
 
 
+SHAPE_DISTS = {"f64": inputs.F64_DISTS, "rec100": inputs.REC_DISTS}
+
+
+def _shape_cut_lengths(dtype):
+    # segments of at most 88 KiB of records run on the 512-thread base-case
+    # shape (two CTAs per SM), larger ones up to the 184 KiB capacity on the
+    # 1024-thread shape, and larger still through a partitioning level
+    small = 88 * 1024 // inputs.ELEM_BYTES[dtype]
+    cap = 184 * 1024 // inputs.ELEM_BYTES[dtype]
+    return [small - 1, small, small + 1, 2, cap, small, cap + 1, small + 1, 33, cap - 1]
+
+
+@pytest.mark.parametrize("dtype", ["u32", "u64", "f64", "pair", "quartet", "rec100"])
+def test_segmented_around_the_base_case_shapes(dtype):
+    dists = SHAPE_DISTS.get(dtype, ("uniform", "twodup", "rootdup"))
+    host, offsets = _concat(dtype, _shape_cut_lengths(dtype), dists, seed=31)
+    got = _run(dtype, host, offsets)
+    _check_segments(got, inputs.to_numpy(host, dtype), offsets, dtype)
+
+
 @pytest.mark.parametrize("dtype", ["u32", "f64", "pair", "rec100", "quartet"])
 def test_segmented_other_types(dtype):
     if dtype == "rec100":

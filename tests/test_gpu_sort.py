@@ -89,12 +89,17 @@ BOUNDARY_DIST = {"u32": "uniform", "u64": "twodup", "f64": "normal", "pair": "ro
 
 
 @pytest.mark.parametrize("dtype", sorted(CAPACITY))
-@pytest.mark.parametrize("rel", [-1, 0, 1, "2x+1"])
+@pytest.mark.parametrize("rel", [-1, 0, 1, "2x+1", "small-1", "small", "small+1"])
 def test_sort_around_base_case_capacity(dtype, rel):
     # the largest segment the shared-memory base case takes (184 KiB of
-    # records) and its neighbours: one base-case call, or one level first
+    # records) and its neighbours: one base-case call, or one level first;
+    # and around 88 KiB, where the 512-thread base-case shape hands over to
+    # the 1024-thread one
     cap = CAPACITY[dtype]
-    n = 2 * cap + 1 if rel == "2x+1" else cap + rel
+    small = 88 * 1024 // inputs.ELEM_BYTES[dtype]
+    n = {"2x+1": 2 * cap + 1, "small-1": small - 1, "small": small,
+         "small+1": small + 1}.get(rel)
+    n = cap + rel if n is None else n
     host = inputs.generate(BOUNDARY_DIST[dtype], dtype, n, seed=cap % 97)
     assert_sorted_parity(run_sort(dtype, host), inputs.to_numpy(host, dtype), dtype)
 
