@@ -388,6 +388,21 @@ def test_radix_classify_against_numpy(dtype, shift, bits):
     np.testing.assert_array_equal(out, a[np.argsort(cls, kind="stable")])
 
 
+@pytest.mark.parametrize("shift,bits", [(28, 8), (30, 4), (32, 8)])
+def test_radix_u32_digits_above_the_key_width_read_zero(shift, bits):
+    # a 32-bit key has no bits above bit 31: a digit that reaches past them
+    # holds only the key's top bits, and one that starts at bit 32 is zero
+    a = inputs.to_numpy(inputs.generate("uniform", "u32", 5000), "u32")
+    cls, B = oracle.radix_classify(a, "u32", shift, bits)
+    assert B == 1 << bits
+    expect = (a.astype(np.uint64) >> np.uint64(shift)) & np.uint64((1 << bits) - 1)
+    np.testing.assert_array_equal(cls, expect.astype(np.uint32))
+    if shift >= 32:
+        assert not cls.any()
+    else:
+        assert cls.max() == (1 << (32 - shift)) - 1  # the top bits do vary
+
+
 def test_multiset_hash_detects_a_lost_element():
     a = _rng(3).integers(0, 1 << 62, size=1000, dtype=np.uint64)
     b = a.copy()

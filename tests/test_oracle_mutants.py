@@ -6,7 +6,11 @@ the pins of test_oracle.py must fail against every one of them (a crash
 counts as caught).  The mistakes live only in those temporary copies.  One
 mutant -- a comparison of record keys on 9 bytes -- survived the record pin
 as first written, which is why that pin now plants records equal in bytes
-0..8.  CPU only.
+0..8; another -- a u32 radix key read as 8 bytes -- is why a pin takes
+digits above bit 31.  Mistakes in the choice of splitters (an unsorted
+sample, other sample positions) are not planted: a samplesort's result does
+not depend on its splitters, only its recursion shape does, and the
+deduplication step keeps any kept splitters strictly increasing.  CPU only.
 """
 import ctypes
 import os
@@ -61,6 +65,36 @@ MUTANTS = [
      # still sorts correctly (only the recursion shape changes) unless the
      # partitioning path is exercised with tiny tasks: the brute force does
      [pins.test_bruteforce_all_short_sequences_partitioning_path]),
+    ("pair ordered by its value word",
+     "    case DT_U64:\n    case DT_PAIR:\n        return load_u64(a) < load_u64(b);",
+     "    case DT_U64:\n        return load_u64(a) < load_u64(b);\n"
+     "    case DT_PAIR:\n        return load_u64(a + 8) < load_u64(b + 8);",
+     [pins.test_pair_keys_sorted_and_records_kept]),
+    ("quartet third key word ignored", "for (int w = 0; w < 3; w++) {",
+     "for (int w = 0; w < 2; w++) {",
+     [pins.test_quartet_bruteforce_all_short_sequences, pins.test_quartet_word_order_by_hand]),
+    ("f64 positives without the sign bit", "return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);",
+     "return (b >> 63) ? ~b : b;",
+     [lambda: pins.test_sort_f64_matches_numpy("normal"),
+      pins.test_f64_order_is_ieee754_total_order]),
+    ("u32 radix key read as 8 bytes",
+     "    if (dt == DT_U32) {\n        uint32_t x;\n        memcpy(&x, a, 4);\n        return x;\n"
+     "    }\n    return load_u64(a);",
+     "    return load_u64(a);",
+     [lambda: pins.test_radix_u32_digits_above_the_key_width_read_zero(28, 8)]),
+    ("last bucket boundary not summed",
+     "for (uint32_t j = 0; j < B; j++) bucket_begin[j + 1] += bucket_begin[j];",
+     "for (uint32_t j = 0; j + 1 < B; j++) bucket_begin[j + 1] += bucket_begin[j];",
+     [lambda: pins.test_partition_level_boundaries_and_multisets(False)]),
+    ("tree size one power of two too large", "while (p < x) p <<= 1;", "while (p <= x) p <<= 1;",
+     [lambda: pins.test_classify_no_equality_is_searchsorted(7)]),
+    ("equality bucket and the bucket below it swapped",
+     "cls[e] = (uint32_t)(2 * i + 1 - (uint64_t)key_less",
+     "cls[e] = (uint32_t)(2 * i + (uint64_t)key_less",
+     [lambda: pins.test_classify_equality_buckets_semantics(7)]),
+    ("insertion sort leaves the first element", "for (uint64_t i = 1; i < n; i++) {\n        memcpy(c->swap",
+     "for (uint64_t i = 2; i < n; i++) {\n        memcpy(c->swap",
+     [pins.test_bruteforce_insertion_sort_all_short_sequences]),
 ]
 
 
