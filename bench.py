@@ -224,6 +224,7 @@ NCU_TRAFFIC = {
                   "sha256": "c3e034fc3bf68f743fe8b4fdd4d89f712152ff2f1af49a634bb2185f108073e6"},
 }
 
+
 def _traffic(kernel, elems_per_launch):
     import hashlib
     t = NCU_TRAFFIC.get(kernel)

@@ -90,7 +90,7 @@ __device__ inline uint32_t g_next_pow2(uint64_t x) {
 }
 
 // class budget of a segment: the adaptive k of Sec. 3.2, aimed at children
-// of about half the base-case size (same rule as the host planner)
+// of about half the base-case size
 __device__ inline uint32_t g_class_budget(const GraphArgs &g, uint64_t n) {
     const uint64_t half = g.smax / 2;
     uint64_t want = g_next_pow2((n + half - 1) / half);

@@ -168,16 +168,6 @@ struct Pending {
     uint32_t shift;    // radix: the digit to use is bits [shift, shift+bits)
 };
 
-// class budget of a segment (the adaptive k of Sec. 3.2, re-targeted so that
-// children fit the shared-memory base case); the device planner uses the
-// same rule
-uint32_t class_budget(const Sorter &s, uint64_t n) {
-    uint64_t want = next_pow2((n + s.smax / 2 - 1) / (s.smax / 2));
-    if (want < 4) want = 4;
-    if (want > s.k) want = s.k;
-    return (uint32_t)want;
-}
-
 struct BatchPlan {
     uint32_t nseg = 0, nstripe = 0, ncta = 0, nmoves = 0, ncls = 0, ncnt = 0;
     uint64_t arena = 0, elems = 0, sarr = 0, keys = 0;
