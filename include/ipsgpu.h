@@ -87,7 +87,11 @@ enum {
  *   k                 max buckets per level incl. equality buckets (256,
  *                     Sec. 5; power of two in [4, 256])
  *   block_bytes       bytes per block (512; the paper's 2 KiB shrinks so that
- *                     k buffer blocks fit in one SM's shared memory)
+ *                     k buffer blocks fit in one SM's shared memory).  A
+ *                     block holds b elements, b the largest power of two
+ *                     with b * element size <= block_bytes (at least 1);
+ *                     b * element size must be a multiple of 16 and
+ *                     k * b * element size at most 160 KiB
  *   alpha_scale       oversampling alpha = alpha_scale * log2(n') (0.2, Sec. 5)
  *   base_case         largest segment sorted by the shared-memory base case
  *                     (elements; at least 32; default and maximum: as many
@@ -98,7 +102,10 @@ enum {
  *   spin_limit        iterations of a bounded device wait before it gives up
  *                     with IPSGPU_E_TIMEOUT (default 1<<22, ~0.5 s)
  *   arena_bytes       device scratch for leftover buffer blocks and cleanup
- *                     staging (default 256 MiB)                            */
+ *                     staging (default 256 MiB; at least
+ *                     (2k + 1) * block + 1 KiB, block = b * element size)
+ * A parameter outside these ranges makes ipsgpu_sorter_create return
+ * IPSGPU_E_INVAL and ipsgpu_scratch_bytes return 0.                       */
 typedef struct {
     uint32_t k;
     uint32_t block_bytes;

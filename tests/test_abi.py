@@ -105,3 +105,50 @@ def test_header_is_plain_c_and_links(lib, tmp_path, compiler, std):
     assert msg == ipsgpu.strerror(ipsgpu.E_TIMEOUT)
     assert int(a) == ipsgpu.scratch_bytes("u64")
     assert int(b) == ipsgpu.scratch_bytes("quartet")
+
+
+def _block_elems(block_bytes, D):
+    b = 1
+    while b * 2 * D <= block_bytes:
+        b *= 2
+    return b
+
+
+@pytest.mark.parametrize("dtype", sorted(ipsgpu.ELEM_BYTES))
+def test_parameter_ranges_of_the_header(lib, dtype):
+    # every range the header states for ipsgpu_params, at its edges: inside,
+    # scratch_bytes is positive; outside, it is 0 and creating a sorter
+    # fails with E_INVAL before any CUDA call
+    D = ipsgpu.ELEM_BYTES[dtype]
+    cap = 184 * 1024 // D
+
+    def ok(**p):
+        return ipsgpu.scratch_bytes(dtype, **p) > 0
+
+    def rejected(**p):
+        if ipsgpu.scratch_bytes(dtype, **p) != 0:
+            return False
+        with pytest.raises(ipsgpu.IpsgpuError) as e:
+            ipsgpu.Sorter(dtype, **p)
+        return e.value.code == ipsgpu.E_INVAL
+
+    for k in (4, 8, 16, 32, 64, 128, 256):
+        assert ok(k=k), k
+    for k in (2, 3, 5, 12, 255, 257, 512):
+        assert rejected(k=k), k
+    assert ok(base_case=32) and ok(base_case=cap)
+    assert rejected(base_case=31) and rejected(base_case=cap + 1)
+    # blocks: b = largest power of two with b * D <= block_bytes; b * D a
+    # multiple of 16 and k * b * D at most 160 KiB
+    for bb in (16, 64, 100, 400, 512, 1000, 1024, 2048, 4096):
+        b = _block_elems(bb, D)
+        for k in (4, 64, 256):
+            valid = (b * D) % 16 == 0 and k * b * D <= 160 * 1024
+            assert ok(k=k, block_bytes=bb) == valid, (bb, k)
+            if not valid:
+                assert rejected(k=k, block_bytes=bb), (bb, k)
+    # arena: at least (2k + 1) blocks and 1 KiB
+    b = _block_elems(512, D)
+    amin = (2 * 256 + 1) * b * D + 1024
+    assert ok(arena_bytes=amin) and rejected(arena_bytes=amin - 1)
+    assert rejected(algo=3) and rejected(algo=-1)
