@@ -312,7 +312,11 @@ typedef struct {
 
 /* Create a server on the current device: lanes, sorters (params as for
  * ipsgpu_sorter_create) and a scheduler thread.
- * Errors: E_INVAL, E_NOMEM (scratch above the budget, or allocation), E_CUDA. */
+ * Errors: E_INVAL (cfg or out NULL, hbm_budget_bytes 0, more than 64 lanes,
+ * a dtype_mask bit above IPSGPU_QUARTET, small_reserve_bytes not below the
+ * budget, params invalid for a served dtype, e.g. RADIX with F64), E_NOMEM
+ * (the sorters' scratch above the budget, or allocation), E_CUDA.  The
+ * argument checks come before any CUDA call. */
 int ipsgpu_server_create(const ipsgpu_server_config *cfg, const ipsgpu_params *params,
                          ipsgpu_server **out);
 /* Drain, stop the scheduler and free everything. */

@@ -152,3 +152,25 @@ def test_parameter_ranges_of_the_header(lib, dtype):
     amin = (2 * 256 + 1) * b * D + 1024
     assert ok(arena_bytes=amin) and rejected(arena_bytes=amin - 1)
     assert rejected(algo=3) and rejected(algo=-1)
+
+
+def test_server_config_checks_of_the_header(lib):
+    # the argument checks of ipsgpu_server_create come before any CUDA call
+    def code(budget, **kw):
+        with pytest.raises(ipsgpu.IpsgpuError) as e:
+            ipsgpu.Server(budget, **kw)
+        return e.value.code
+
+    big = 1 << 40
+    assert code(0) == ipsgpu.E_INVAL
+    assert code(big, lanes=65) == ipsgpu.E_INVAL
+    assert code(big, small_reserve_bytes=big) == ipsgpu.E_INVAL
+    assert code(big, dtypes=("u64", "f64"), algo=ipsgpu.RADIX) == ipsgpu.E_INVAL
+    assert code(big, k=3) == ipsgpu.E_INVAL
+    # a dtype_mask bit beyond the last type, through the raw call
+    cfg = ipsgpu.ServerConfig(big, 0, 0, 0, 1 << (max(ipsgpu.DTYPES.values()) + 1), 0, 0)
+    h = ctypes.c_void_p()
+    assert lib.ipsgpu_server_create(ctypes.byref(cfg), None, ctypes.byref(h)) == ipsgpu.E_INVAL
+    # scratch of the lanes' sorters above the budget
+    scratch = 4 * sum(ipsgpu.scratch_bytes(d) for d in ("u32", "u64", "pair"))
+    assert code(scratch - 1) == ipsgpu.E_NOMEM
