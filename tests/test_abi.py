@@ -174,3 +174,23 @@ def test_server_config_checks_of_the_header(lib):
     # scratch of the lanes' sorters above the budget
     scratch = 4 * sum(ipsgpu.scratch_bytes(d) for d in ("u32", "u64", "pair"))
     assert code(scratch - 1) == ipsgpu.E_NOMEM
+
+
+def test_noalloc_level_argument_checks(lib):
+    # each call below breaks one stated limit, which the library checks
+    # before any CUDA call (the pointers are placeholders, never read)
+    P = 1 << 20  # a placeholder address, aligned for every type
+    u64 = ipsgpu.DTYPES["u64"]
+    f = lib.ipsgpu_partition_level_noalloc
+    assert f(99, P, 10, P, 3, 0, P, None) == ipsgpu.E_INVAL          # no such dtype
+    assert f(u64, P, 10, None, 3, 0, P, None) == ipsgpu.E_INVAL      # no splitters
+    assert f(u64, P, 10, P, 3, 0, None, None) == ipsgpu.E_INVAL      # no bucket_begin
+    assert f(u64, P, 10, P, 0, 0, P, None) == ipsgpu.E_INVAL         # zero splitters
+    assert f(u64, P, 10, P, 128, 1, P, None) == ipsgpu.E_INVAL       # B = 512 > 256
+    assert f(u64, P, 10, P, 256, 0, P, None) == ipsgpu.E_INVAL       # K = 512 > 256
+    assert f(u64, P, 1 << 32, P, 3, 0, P, None) == ipsgpu.E_INVAL    # n > 2^32 - 1
+    assert f(u64, None, 10, P, 3, 0, P, None) == ipsgpu.E_INVAL      # no data
+    assert f(u64, P + 4, 10, P, 3, 0, P, None) == ipsgpu.E_INVAL     # misaligned data
+    assert f(u64, P, 10, P + 4, 3, 0, P, None) == ipsgpu.E_INVAL     # misaligned splitters
+    rec = ipsgpu.DTYPES["rec100"]
+    assert f(rec, P + 2, 10, P, 3, 0, P, None) == ipsgpu.E_INVAL     # records: 4-byte aligned
