@@ -194,3 +194,15 @@ def test_noalloc_level_argument_checks(lib):
     assert f(u64, P, 10, P + 4, 3, 0, P, None) == ipsgpu.E_INVAL     # misaligned splitters
     rec = ipsgpu.DTYPES["rec100"]
     assert f(rec, P + 2, 10, P, 3, 0, P, None) == ipsgpu.E_INVAL     # records: 4-byte aligned
+
+
+def test_every_status_code_of_the_header_has_its_own_message(lib):
+    with open(os.path.join(ROOT, "include", "ipsgpu.h")) as f:
+        codes = dict((name, int(v)) for name, v in
+                     re.findall(r"\b(IPSGPU_(?:OK|E_[A-Z]+))\s*=\s*(\d+)", f.read()))
+    assert len(codes) >= 9 and sorted(codes.values()) == list(range(len(codes)))
+    for name, v in codes.items():
+        assert getattr(ipsgpu, name[len("IPSGPU_"):]) == v, name
+    msgs = [ipsgpu.strerror(v) for v in codes.values()]
+    assert len(set(msgs)) == len(msgs) and "unknown status" not in msgs
+    assert ipsgpu.strerror(len(codes)) == ipsgpu.strerror(-1) == "unknown status"
