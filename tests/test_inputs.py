@@ -45,3 +45,28 @@ def test_segmented_batch_layout():
     m = int(lengths[i])
     seg = data[int(offsets[i]):int(offsets[i + 1])]
     assert torch.equal(torch.sort(seg).values, torch.arange(m, dtype=torch.int64))
+
+
+def test_splitmix64_first_outputs_for_state_zero():
+    # the generator's widely quoted first two outputs from state 0
+    assert inputs.splitmix64_py(0, 0) == 0xE220A8397B1DCDAF
+    assert inputs.splitmix64_py(1, 0) == 0x6E789E6AA1B965F4
+
+
+def test_splitmix64_tensor_matches_big_integer_arithmetic():
+    # the tensor form (int64 wrap-around, logical shifts made of arithmetic
+    # ones) against the same definition in Python's unbounded integers
+    import numpy as np
+    idx = [0, 1, 2, 3, (1 << 31) + 7, (1 << 62) + 5]
+    idx += np.random.default_rng(1).integers(0, 1 << 62, 200).tolist()
+    for seed in (0, 1, inputs.DEFAULT_SEED, (1 << 64) - 1, 1 << 63):
+        got = inputs.splitmix64(torch.tensor(idx, dtype=torch.int64), seed)
+        for i, g in zip(idx, got.tolist()):
+            assert g & ((1 << 64) - 1) == inputs.splitmix64_py(i, seed), (i, seed)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 1000, 4096, (1 << 40) + 3, (1 << 62) - 1])
+def test_unsigned_modulo_of_bit_patterns(n):
+    vals = [0, 1, 5, (1 << 63) - 1, 1 << 63, (1 << 64) - 1, 0xDEADBEEFCAFEF00D, 0x8000000000000001]
+    x = torch.tensor([inputs._s64(v) for v in vals], dtype=torch.int64)
+    assert inputs._umod(x, n).tolist() == [v % n for v in vals]
