@@ -217,4 +217,4 @@ def test_scratch_is_the_arena_plus_fixed_tables(lib):
         for arena in (256 << 20, 1 << 24):
             for k in (64, 256):
                 got = ipsgpu.scratch_bytes(dtype, arena_bytes=arena, k=k) - arena
-                assert got == int(mib * 2 ** 20), (dtype, arena, k)
+                assert got == int(mib * 2 ** 20) + 1024, (dtype, arena, k)  # + 1 KiB of state
