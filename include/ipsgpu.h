@@ -211,7 +211,8 @@ int ipsgpu_radix_level(ipsgpu_sorter *s, void *d_data, uint64_t n, uint32_t shif
  *     sorted or reversed inputs.
  *   - Kernel-side errors go to the status word (ipsgpu_status); after an
  *     error the data still holds a permutation of every segment.
- * Errors: E_INVAL (NULL or misaligned pointers, n > 2^40), E_CUDA. */
+ * Errors: E_INVAL (NULL or misaligned pointers, n > 2^40, num_segments >
+ * 2^32 - 1), E_CUDA. */
 int ipsgpu_sort_segmented(ipsgpu_sorter *s, void *d_data, uint64_t n,
                           const uint64_t *d_offsets, uint64_t num_segments, void *stream);
 
@@ -222,7 +223,8 @@ int ipsgpu_sort_segmented(ipsgpu_sorter *s, void *d_data, uint64_t n,
  * arrays must not overlap.  Asynchronous, never synchronizes; an entry with
  * a NULL or misaligned address (and n > 0) or n > 2^40 is skipped and
  * recorded as E_INVAL in the status word.
- * Errors: E_INVAL (misaligned d_segs), E_CUDA. */
+ * Errors: E_INVAL (NULL or misaligned d_segs, num_segments > 2^32 - 1),
+ * E_CUDA. */
 int ipsgpu_sort_batch(ipsgpu_sorter *s, const uint64_t *d_segs, uint64_t num_segments,
                       void *stream);
 
