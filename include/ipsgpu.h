@@ -349,8 +349,9 @@ int ipsgpu_server_times(ipsgpu_server *srv, uint64_t ticket, double *t_submit_us
                         double *t_launch_us, double *t_done_us);
 /* The clock of ipsgpu_server_times. */
 double ipsgpu_server_now_us(void);
-/* Return a request's footprint (reserved or done; E_BUSY while it runs) and
- * forget its ticket. */
+/* Return a request's footprint (reserved or done) and forget its ticket.
+ * Errors: E_INVAL (unknown ticket), E_BUSY (started and still queued or
+ * running: wait for it, or cancel it first while it is queued). */
 int ipsgpu_server_release(ipsgpu_server *srv, uint64_t ticket);
 /* Cancel a request that has not begun to run: a reserved one, or a started
  * one still waiting in the queue.  It becomes done with status
