@@ -330,7 +330,8 @@ int ipsgpu_server_create(const ipsgpu_server_config *cfg, const ipsgpu_params *p
 int ipsgpu_server_destroy(ipsgpu_server *srv);
 /* Admit a request of n elements of dtype: reserves its footprint and
  * returns a ticket.  E_BUSY: it does not fit now (retry after releases);
- * E_NOMEM: it never fits; E_UNSUPPORTED: dtype not served. */
+ * E_NOMEM: it never fits; E_UNSUPPORTED: dtype not served; E_INVAL: NULL
+ * arguments, an unknown dtype or n > 2^40. */
 int ipsgpu_server_reserve(ipsgpu_server *srv, uint64_t n, int dtype, uint64_t *ticket);
 /* Start a reserved request on d_data (n elements, aligned as for
  * ipsgpu_sort).  If ready_stream is not NULL the sort waits for the work
@@ -342,7 +343,8 @@ int ipsgpu_server_submit(ipsgpu_server *srv, void *d_data, uint64_t n, int dtype
 /* done = 1 once the request's sort has finished on the GPU; status = its
  * status code (IPSGPU_OK, or the error its run reported). */
 int ipsgpu_server_poll(ipsgpu_server *srv, uint64_t ticket, int *done, int *status);
-/* Block until the request is done; returns its status. */
+/* Block until the request is done; returns its status.  E_INVAL for an
+ * unknown ticket or one that was reserved but never started. */
 int ipsgpu_server_wait(ipsgpu_server *srv, uint64_t ticket);
 /* Host steady-clock times in microseconds: started, launched, seen done. */
 int ipsgpu_server_times(ipsgpu_server *srv, uint64_t ticket, double *t_submit_us,
