@@ -95,6 +95,11 @@ MUTANTS = [
     ("insertion sort leaves the first element", "for (uint64_t i = 1; i < n; i++) {\n        memcpy(c->swap",
      "for (uint64_t i = 2; i < n; i++) {\n        memcpy(c->swap",
      [pins.test_bruteforce_insertion_sort_all_short_sequences]),
+    ("elements equal to a splitter classed above it",
+     "            if (key_less(dt, spl + j * D, x))\n                lo = mid + 1;",
+     "            if (!key_less(dt, x, spl + j * D))\n                lo = mid + 1;",
+     [lambda: pins.test_classify_no_equality_is_searchsorted(7),
+      lambda: pins.test_classify_equality_buckets_semantics(7)]),
 ]
 
 
