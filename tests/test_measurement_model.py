@@ -49,3 +49,32 @@ def test_traffic_model_is_per_element():
     assert 14.0 < t["bytes_per_elem"] <= 16.0  # at most the 2 x 8 B of the model
     got = bench._traffic("classify", 1 << 20)
     assert got is None or got == pytest.approx(t["bytes_per_elem"] * (1 << 20))
+
+
+def test_peak_is_the_measured_copy_bandwidth_else_the_fallback(monkeypatch, tmp_path):
+    sys.path.insert(0, ROOT)
+    import bench
+    import json
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6704.5}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._peak_hbm() == (6704.5, "measured")
+    (tmp_path / "MEASURED_PEAKS.json").unlink()
+    assert bench._peak_hbm() == (6800.0, "fallback")  # the recipe's fallback figure
+    (tmp_path / "MEASURED_PEAKS.json").write_text("{}")
+    assert bench._peak_hbm() == (6800.0, "fallback")
+
+
+def test_traffic_is_null_once_the_kernel_source_changes(monkeypatch, tmp_path):
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "k.cuh"
+    src.write_text("kernel v1\n")
+    import hashlib
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "NCU_TRAFFIC", {"k": {"bytes_per_elem": 15.0, "source": "k.cuh",
+                                                     "sha256": sha}})
+    assert bench._traffic("k", 1000) == pytest.approx(15000.0)
+    src.write_text("kernel v2\n")
+    assert bench._traffic("k", 1000) is None
+    assert bench._traffic("other", 1000) is None
