@@ -90,8 +90,12 @@ enum {
  *                     k buffer blocks fit in one SM's shared memory).  A
  *                     block holds b elements, b the largest power of two
  *                     with b * element size <= block_bytes (at least 1);
- *                     b * element size must be a multiple of 16 and
- *                     k * b * element size at most 160 KiB
+ *                     b * element size must be a multiple of 16, at most
+ *                     2 KiB, and k * b * element size at most 128 KiB (the
+ *                     k buffer blocks of a classification CTA; with them
+ *                     its tile stage and tables fill 227 KiB of shared
+ *                     memory): k = 256 takes blocks up to 512 B, 128 up to
+ *                     1 KiB, 64 up to 2 KiB
  *   alpha_scale       oversampling alpha = alpha_scale * log2(n') (0.2, Sec. 5)
  *   base_case         largest segment sorted by the shared-memory base case
  *                     (elements; at least 32; default and maximum: as many
@@ -378,8 +382,9 @@ int ipsgpu_server_usage(ipsgpu_server *srv, uint64_t *used, uint64_t *budget, ui
  *     ipsgpu_partition_level; dtype is an ipsgpu_dtype.
  *   - Limits: n <= 2^32 - 1 elements and B <= 256 classes; larger requests
  *     return IPSGPU_E_INVAL.
- *   - The first call on a device looks up the array's device address and sets
- *     kernel attributes; make that first call before any stream capture.
+ *   - The first call on a device (of any dtype) looks up the array's device
+ *     address and sets the kernel attributes of every dtype; make that first
+ *     call before any stream capture.
  *   - Every call uses the same array and leaves its contents behind, so calls
  *     whose work overlaps on the GPU (other streams, other host threads) race:
  *     serialize them.

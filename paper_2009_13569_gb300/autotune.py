@@ -3,10 +3,10 @@ size and the oversampling factor, picked by timing candidate sorters on a
 sample of the workload on the GPU.
 
 The search is coordinate descent over three groups, in the order in which
-they matter most: first the (k, block_bytes) pair (k * block_bytes is kept
-at 128 KiB, the classification buffer of one CTA), then the base-case size,
-then alpha_scale (the paper's oversampling factor alpha = alpha_scale *
-log2 n).  Each candidate is timed `reps` times on fresh copies of the sample
+they matter most: first the (k, block_bytes) pair (k in {256, 128, 64},
+block bytes in {512, 1024, 2048}, k * block_bytes at most 128 KiB, the
+classification buffer one CTA can hold), then the base-case size, then
+alpha_scale (the paper's oversampling factor alpha = alpha_scale * log2 n).  Each candidate is timed `reps` times on fresh copies of the sample
 (the sort is in place) and scored by its median.  The search logic is
 independent of how a candidate is timed (search()), so it is testable on the
 CPU; tune_array() and tune_segmented() time candidates through the C ABI.
@@ -24,8 +24,9 @@ import statistics
 
 from . import ipsgpu
 
-# (k, block_bytes): 256 buckets of 512 B blocks down to 64 buckets of 2 KiB
-KB_PAIRS = ((256, 512), (128, 1024), (64, 2048))
+# (k, block_bytes) with k * block_bytes <= 128 KiB: 256 buckets of 512 B
+# blocks down to 64 buckets of 2 KiB
+KB_PAIRS = ((256, 512), (128, 1024), (64, 2048), (128, 512), (64, 1024), (64, 512))
 ALPHAS = (0.2, 0.5, 1.0)
 BASE_FRACTIONS = (1.0, 0.5, 0.25)  # of the largest base case the type allows
 BASE_SMEM_BYTES = 184 * 1024       # shared-memory element buffer of the base case

@@ -370,7 +370,9 @@ struct ClsSmem {
     static constexpr size_t o_tab = o_tot + kMaxClasses * sizeof(uint32_t);
     static constexpr size_t o_stage = a16(o_tab + kCells * sizeof(uint32_t));
     static constexpr size_t o_buf = a16(o_stage + (size_t)TILE * T::D + 16);
-    static size_t bytes(uint32_t b) { return o_buf + (size_t)kMaxClasses * b * T::D; }
+    // k buffer blocks of b elements: a level of this sorter has at most k
+    // classes (equality buckets included)
+    static size_t bytes(uint32_t k, uint32_t b) { return o_buf + (size_t)k * b * T::D; }
 };
 
 template <class T>

@@ -11,6 +11,7 @@ namespace ipsgpu {
 
 // ---------------------------------------------------------------- limits
 constexpr int kMaxClasses = 256;      // buckets per level incl. equality ones
+constexpr uint32_t kMaxBlockBytes = 2048;  // a block, held by one warp in registers
 // sample keys sorted in one CTA: the largest power of two <= 16384 whose
 // keys fit in 192 KiB (the bitonic sort pads the sample to a power of two):
 // 16384 keys of 4 or 8 bytes, 8192 of 16 or 24 bytes

@@ -25,6 +25,9 @@ struct ipsgpu_sorter {
 namespace {
 
 constexpr uint64_t kMinStripe = 1u << 15;  // elements
+// shared memory one CTA may opt in to on sm_100 / sm_103 GPUs (227 KiB)
+constexpr uint64_t kSmemOptinBytes = 227u * 1024;
+constexpr uint64_t kStaticSmemSlack = 1024;  // a kernel's static shared variables
 
 __global__ void k_debug_wait(uint32_t *flag, uint32_t limit, int *status) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -84,8 +87,13 @@ int resolve(const ipsgpu_params *p, int dtype, Resolved *r) {
     r->base_case = (p && p->base_case) ? p->base_case : cap;
     if (r->k < 4 || r->k > (uint32_t)kMaxClasses || (r->k & (r->k - 1))) return IPSGPU_E_INVAL;
     if (r->base_case < 32 || r->base_case > cap) return IPSGPU_E_INVAL;
+    // blocks: a multiple of 16 bytes, at most kMaxBlockBytes (a permutation
+    // worker holds one in registers); k of them plus the tile stage fit the
+    // shared memory of one classification CTA
     uint32_t b = block_elems(r->block_bytes, ops->D);
-    if (b == 0 || (uint64_t)b * ops->D * r->k > 160u * 1024 || (b * ops->D) % 16) return IPSGPU_E_INVAL;
+    if (b == 0 || (uint64_t)b * ops->D > kMaxBlockBytes || (b * ops->D) % 16 ||
+        ops->classify_smem_bytes(r->k, b) + kStaticSmemSlack > kSmemOptinBytes)
+        return IPSGPU_E_INVAL;
     // the arena holds at least one segment with one stripe of k classes
     if (r->arena_bytes < 2ull * r->k * b * ops->D + (uint64_t)b * ops->D + 1024) return IPSGPU_E_INVAL;
     if (r->algo != IPSGPU_SAMPLESORT && r->algo != IPSGPU_RADIX &&

@@ -346,7 +346,24 @@ static __global__ void __launch_bounds__(kAuxThreads) k_prep(LevelArgs a) {
             ar.full[j] = full;
         }
         __syncthreads();
-        cta_exclusive_scan<unsigned long long>(sz, pre, (int)B, wtmp);
+        const unsigned long long total = cta_exclusive_scan<unsigned long long>(sz, pre, (int)B, wtmp);
+        if (total != sd.n) {
+            // counts that do not add up to the segment (they would send
+            // pointers past it): report, and leave the level nothing to move
+            // (empty buckets, no blocks, no readers)
+            if (tid == 0) set_status(a.status, IPSGPU_E_INTERNAL);
+            for (uint32_t j = tid; j <= B; j += blockDim.x) {
+                ar.bb[j] = 0;
+                ar.dlm[j] = 0;
+                if (j < B) {
+                    ar.full[j] = 0;
+                    ar.readers[j] = 0;
+                    ar.ptr[j] = (unsigned long long)kRBias;
+                }
+            }
+            __syncthreads();
+            continue;
+        }
         for (uint32_t j = tid; j <= B; j += blockDim.x) {
             uint64_t bb = j < B ? pre[j] : sd.n;
             ar.bb[j] = bb;
@@ -396,42 +413,62 @@ static __global__ void __launch_bounds__(kAuxThreads) k_prep(LevelArgs a) {
 }
 
 // ------------------------------------------------------------ block copies
-// A block of BB bytes is held by one warp, 16 bytes per lane; `u` is the
-// widest access unit (16, 8 or 4 bytes) both addresses allow.
-__device__ __forceinline__ void warp_load_block(uint4 &r, const unsigned char *p, uint32_t BB,
-                                                int lane, int u) {
-    const uint32_t o = (uint32_t)lane * 16;
-    if (o >= BB) return;
-    if (u == 16) {
-        r = __ldcg(reinterpret_cast<const uint4 *>(p + o));
-    } else if (u == 8) {
-        const uint2 *q = reinterpret_cast<const uint2 *>(p + o);
-        uint2 x = __ldcg(q), y = __ldcg(q + 1);
-        r = make_uint4(x.x, x.y, y.x, y.y);
-    } else {
-        const uint32_t *q = reinterpret_cast<const uint32_t *>(p + o);
-        r = make_uint4(__ldcg(q), __ldcg(q + 1), __ldcg(q + 2), __ldcg(q + 3));
+// A block of BB bytes (a multiple of 16, at most kMaxBlockBytes) is held by
+// one warp in NV = ceil(BB / 512) 16-byte registers per lane: unit c of lane
+// l holds bytes [512 c + 16 l, 512 c + 16 l + 16), so lane 0's unit 0 (and
+// lane 1's for 32-byte elements) holds the first element.  `u` is the widest
+// access unit (16, 8 or 4 bytes) both addresses allow.
+
+template <int NV>
+struct WarpBlock {
+    uint4 v[NV];
+};
+
+template <int NV>
+__device__ __forceinline__ void warp_load_block(WarpBlock<NV> &r, const unsigned char *p,
+                                                uint32_t BB, int lane, int u) {
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+        const uint32_t o = (uint32_t)c * 512 + (uint32_t)lane * 16;
+        if (o >= BB) break;
+        if (u == 16) {
+            r.v[c] = __ldcg(reinterpret_cast<const uint4 *>(p + o));
+        } else if (u == 8) {
+            const uint2 *q = reinterpret_cast<const uint2 *>(p + o);
+            uint2 x = __ldcg(q), y = __ldcg(q + 1);
+            r.v[c] = make_uint4(x.x, x.y, y.x, y.y);
+        } else {
+            const uint32_t *q = reinterpret_cast<const uint32_t *>(p + o);
+            r.v[c] = make_uint4(__ldcg(q), __ldcg(q + 1), __ldcg(q + 2), __ldcg(q + 3));
+        }
     }
 }
 
-__device__ __forceinline__ void warp_store_block(const uint4 &r, unsigned char *p, uint32_t BB,
-                                                 int lane, int u) {
-    const uint32_t o = (uint32_t)lane * 16;
-    if (o >= BB) return;
-    if (u == 16) {
-        __stcg(reinterpret_cast<uint4 *>(p + o), r);
-    } else if (u == 8) {
-        uint2 *q = reinterpret_cast<uint2 *>(p + o);
-        __stcg(q, make_uint2(r.x, r.y));
-        __stcg(q + 1, make_uint2(r.z, r.w));
-    } else {
-        uint32_t *q = reinterpret_cast<uint32_t *>(p + o);
-        __stcg(q, r.x);
-        __stcg(q + 1, r.y);
-        __stcg(q + 2, r.z);
-        __stcg(q + 3, r.w);
+template <int NV>
+__device__ __forceinline__ void warp_store_block(const WarpBlock<NV> &r, unsigned char *p,
+                                                 uint32_t BB, int lane, int u) {
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+        const uint32_t o = (uint32_t)c * 512 + (uint32_t)lane * 16;
+        if (o >= BB) break;
+        if (u == 16) {
+            __stcg(reinterpret_cast<uint4 *>(p + o), r.v[c]);
+        } else if (u == 8) {
+            uint2 *q = reinterpret_cast<uint2 *>(p + o);
+            __stcg(q, make_uint2(r.v[c].x, r.v[c].y));
+            __stcg(q + 1, make_uint2(r.v[c].z, r.v[c].w));
+        } else {
+            uint32_t *q = reinterpret_cast<uint32_t *>(p + o);
+            __stcg(q, r.v[c].x);
+            __stcg(q + 1, r.v[c].y);
+            __stcg(q + 2, r.v[c].z);
+            __stcg(q + 3, r.v[c].w);
+        }
     }
 }
+
+// 16-byte units per lane for blocks of BB bytes
+__host__ __device__ inline int block_units(uint32_t BB) { return BB <= 512 ? 1 : (BB <= 1024 ? 2 : 4); }
 
 __device__ __forceinline__ int access_unit(uint64_t byte_off) {
     return (byte_off & 15) == 0 ? 16 : ((byte_off & 7) == 0 ? 8 : 4);
@@ -443,7 +480,7 @@ __device__ __forceinline__ unsigned char *seg_ovf(const LevelArgs &a, const SegD
 }
 
 // ------------------------------------------------------------------ fixup
-template <class T>
+template <class T, int NV>
 __global__ void __launch_bounds__(kAuxThreads) k_fixup(LevelArgs a) {
     const uint32_t nm = min(*a.nmoves, a.move_cap);
     const int lane = threadIdx.x & 31;
@@ -466,9 +503,9 @@ __global__ void __launch_bounds__(kAuxThreads) k_fixup(LevelArgs a) {
         const uint32_t BB = sd.b * T::D;
         unsigned char *base = reinterpret_cast<unsigned char *>(sd.addr);
         const int u = access_unit((uint64_t)(uintptr_t)base);
-        uint4 r;
-        warp_load_block(r, base + (uint64_t)(mv.src + k) * BB, BB, lane, u);
-        warp_store_block(r, base + (uint64_t)(mv.dst + k) * BB, BB, lane, u);
+        WarpBlock<NV> r;
+        warp_load_block<NV>(r, base + (uint64_t)(mv.src + k) * BB, BB, lane, u);
+        warp_store_block<NV>(r, base + (uint64_t)(mv.dst + k) * BB, BB, lane, u);
         // advance by nwarps blocks
         uint32_t adv = nwarps;
         while (m < nm) {
@@ -486,7 +523,7 @@ __global__ void __launch_bounds__(kAuxThreads) k_fixup(LevelArgs a) {
 
 // ---------------------------------------------------------------- permute
 // Block permutation (Sec. 3.1.3).  Each warp is one worker with two swap
-// buffers (one block per buffer, 16 bytes per lane, in registers).  Per
+// buffers (one block per buffer, NV 16-byte registers per lane).  Per
 // bucket i, ptr[i] packs the write pointer w_i (high half) and the exclusive
 // read pointer r_i + 1 (low half, biased), so that one 64-bit atomic reads
 // and modifies both consistently.  Blocks in [d_i, w_i) are correct, blocks
@@ -495,7 +532,7 @@ __global__ void __launch_bounds__(kAuxThreads) k_fixup(LevelArgs a) {
 // never wait for one another except for the bounded reader wait, so they need
 // not run at the same time.  The bucket of a block is that of its first
 // element, classified by the whole warp (LevelClassifier::warp_class).
-template <class T>
+template <class T, int NV>
 __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a) {
     typedef typename T::K K;
     typedef typename T::E E;
@@ -522,7 +559,9 @@ __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a) {
         const uint32_t wid = (v - sd.cta0) * (kPermuteThreads / 32) + warp;
         uint32_t p = (uint32_t)(((uint64_t)wid * B) / W);
         uint32_t scanned = 0;
-        uint4 A = make_uint4(0, 0, 0, 0), Bk = make_uint4(0, 0, 0, 0);
+        WarpBlock<NV> A, Bk;
+#pragma unroll
+        for (int c = 0; c < NV; c++) A.v[c] = Bk.v[c] = make_uint4(0, 0, 0, 0);
         uint32_t t = 0;
         bool hold = false;
         bool failed = false;
@@ -572,7 +611,7 @@ __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a) {
                             failed = true;
                             break;
                         }
-                        warp_load_block(A, base + (uint64_t)blk * BB, BB, lane, u);
+                        warp_load_block<NV>(A, base + (uint64_t)blk * BB, BB, lane, u);
                         __threadfence();
                         __syncwarp();
                         if (lane == 0) atomicSub(&ar.readers[p], 1u);
@@ -584,7 +623,7 @@ __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a) {
                 }
                 if (!got) break;
                 scanned = 0;
-                t = cl.warp_class(block_head<T>(A), lane);
+                t = cl.warp_class(block_head<T>(A.v[0]), lane);
                 hold = true;
             }
             // place the held block into bucket t
@@ -606,10 +645,10 @@ __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a) {
                 break;
             }
             if (unproc) {
-                warp_load_block(Bk, base + (uint64_t)slot * BB, BB, lane, u);
-                const uint32_t t2 = cl.warp_class(block_head<T>(Bk), lane);
+                warp_load_block<NV>(Bk, base + (uint64_t)slot * BB, BB, lane, u);
+                const uint32_t t2 = cl.warp_class(block_head<T>(Bk.v[0]), lane);
                 if (t2 == t) continue;  // already in place: w moved past it
-                warp_store_block(A, base + (uint64_t)slot * BB, BB, lane, u);
+                warp_store_block<NV>(A, base + (uint64_t)slot * BB, BB, lane, u);
                 A = Bk;
                 t = t2;
             } else {
@@ -628,10 +667,10 @@ __global__ void __launch_bounds__(kPermuteThreads) k_permute(LevelArgs a) {
                 }
                 if (slot >= nfs) {
                     // the last, partial block of the segment: use the overflow block
-                    warp_store_block(A, seg_ovf(a, sd, T::D), BB, lane, 16);
+                    warp_store_block<NV>(A, seg_ovf(a, sd, T::D), BB, lane, 16);
                     if (lane == 0) st->ovf_used = 1;
                 } else {
-                    warp_store_block(A, base + (uint64_t)slot * BB, BB, lane, u);
+                    warp_store_block<NV>(A, base + (uint64_t)slot * BB, BB, lane, u);
                 }
                 hold = false;
             }

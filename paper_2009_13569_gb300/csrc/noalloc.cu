@@ -15,8 +15,8 @@
 // the library until the process exits.  Its device address is obtained once
 // per device with cudaGetSymbolAddress on the first call made with that
 // device current (a host-side name of a __device__ array is not a device
-// address).  That first call also sets kernel attributes, so it should not
-// be made while a stream is being captured.
+// address).  That first call also sets the kernel attributes of every
+// element type, so it should not be made while a stream is being captured.
 //
 // All calls share the array and each leaves its contents behind; the parts
 // that must start at zero (move counter, status word) are cleared by every
@@ -65,7 +65,6 @@ struct DeviceSetup {
     bool done[kNaMaxDevices] = {};
     unsigned char *ptr[kNaMaxDevices] = {};
     int nsm[kNaMaxDevices] = {};
-    bool typed[kNaMaxDevices][kNaTypes] = {};
 };
 DeviceSetup g_setup;
 
@@ -172,13 +171,13 @@ extern "C" int ipsgpu_partition_level_noalloc(int dtype, void *d_data, uint64_t 
             int nsm = 0;
             if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
                 return IPSGPU_E_CUDA;
+            // kernel attributes of every element type now, so that no later
+            // call (of another dtype) sets any
+            for (int t = 0; t < kNaTypes; t++)
+                if (na_ops(t)->init(&s) != cudaSuccess) return IPSGPU_E_CUDA;
             g_setup.ptr[dev] = static_cast<unsigned char *>(p);
             g_setup.nsm[dev] = nsm;
             g_setup.done[dev] = true;
-        }
-        if (!g_setup.typed[dev][dtype]) {
-            if (ops->init(&s) != cudaSuccess) return IPSGPU_E_CUDA;
-            g_setup.typed[dev][dtype] = true;
         }
     }
     unsigned char *scr = g_setup.ptr[dev];

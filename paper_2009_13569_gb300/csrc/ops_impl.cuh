@@ -13,28 +13,47 @@ namespace ipsgpu {
 template <class T>
 struct OpsImpl {
     typedef typename T::K K;
-    static size_t classify_smem(const Sorter *s) { return ClsSmem<T>::bytes(s->b); }
+    static size_t classify_smem(const Sorter *s) { return ClsSmem<T>::bytes(s->k, s->b); }
+    static size_t classify_smem_bytes(uint32_t k, uint32_t b) { return ClsSmem<T>::bytes(k, b); }
     static size_t sample_smem() {
         return (max_sort_sample<K>() + kMaxClasses) * sizeof(K) +
                sizeof(uint32_t) * (2 * kMaxClasses + 34);
     }
 
-    static cudaError_t init(Sorter *s) {
-        cudaError_t e;
-        e = cudaFuncSetAttribute(k_classify<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)classify_smem(s));
+    // Raises the dynamic shared-memory limit of a kernel to the most the
+    // device allows next to its static shared memory.  The attribute
+    // belongs to the kernel (process-wide), so it is never set to what one
+    // sorter needs: a later sorter with smaller blocks would lower it under
+    // every earlier one.  Each launch still asks for its own size.
+    template <class F>
+    static cudaError_t raise_smem_limit(F *kernel, int optin) {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_sample_tree<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sample_smem());
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_base<T, BaseLarge>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)base_smem_bytes<BaseLarge>());
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_base<T, BaseSmall>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)base_smem_bytes<BaseSmall>());
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    optin - (int)fa.sharedSizeBytes);
+    }
+    static cudaError_t init(Sorter *) {
+        int dev = 0, optin = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = raise_smem_limit(k_classify<T>, optin);
+        if (e == cudaSuccess) e = raise_smem_limit(k_sample_tree<T>, optin);
+        if (e == cudaSuccess) e = raise_smem_limit(k_base<T, BaseLarge>, optin);
+        if (e == cudaSuccess) e = raise_smem_limit(k_base<T, BaseSmall>, optin);
         return e;
+    }
+
+    template <int NV>
+    static void launch_moves(Sorter *s, const LevelArgs &a, const LevelGrids &g, cudaStream_t st,
+                             double lvl) {
+        s->tbegin(KK_FIXUP, 0, st);
+        k_fixup<T, NV><<<s->nsm * 4, kAuxThreads, 0, st>>>(a);
+        s->tend(st);
+        s->tbegin(KK_PERMUTE, 2 * lvl, st);
+        k_permute<T, NV><<<g.cta, kPermuteThreads, 0, st>>>(a);
+        s->tend(st);
     }
 
     // One partitioning level.  g holds the grid of each kernel: the exact
@@ -52,15 +71,17 @@ struct OpsImpl {
         s->tbegin(KK_CLASSIFY, 2 * lvl, st);
         k_classify<T><<<g.stripe, ClsCfg<T>::NT, classify_smem(s), st>>>(a);
         s->tend(st);
+        // a classification that did not launch left no counts: stop before
+        // the kernels that would read the previous level's
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         s->tbegin(KK_PREP, 0, st);
         k_prep<<<g.seg, kAuxThreads, 0, st>>>(a);
         s->tend(st);
-        s->tbegin(KK_FIXUP, 0, st);
-        k_fixup<T><<<s->nsm * 4, kAuxThreads, 0, st>>>(a);
-        s->tend(st);
-        s->tbegin(KK_PERMUTE, 2 * lvl, st);
-        k_permute<T><<<g.cta, kPermuteThreads, 0, st>>>(a);
-        s->tend(st);
+        switch (block_units(s->b * T::D)) {
+        case 1: launch_moves<1>(s, a, g, st, lvl); break;
+        case 2: launch_moves<2>(s, a, g, st, lvl); break;
+        default: launch_moves<4>(s, a, g, st, lvl); break;
+        }
         s->tbegin(KK_STAGE, 0, st);
         k_stage<T><<<g.seg, kAuxThreads, 0, st>>>(a);
         s->tend(st);
@@ -89,7 +110,10 @@ struct OpsImpl {
         uint64_t chunks = (n + kDetectChunk - 1) / kDetectChunk;
         uint32_t grid = (uint32_t)(chunks < (uint64_t)s->nsm * 8 ? chunks : (uint64_t)s->nsm * 8);
         if (grid == 0) grid = 1;
-        s->tbegin(KK_DETECT, (double)n * T::D, st);  // one read pass
+        // with mm (radix) the pass reads every element; without it, it stops
+        // once both properties are refuted, after an amount read that only
+        // the device knows, so no bytes are attributed to the launch
+        s->tbegin(KK_DETECT, mm ? (double)n * T::D : 0.0, st);
         k_detect<T><<<grid, kDetectThreads, 0, st>>>(data, n, s->d_flags, mm);
         s->tend(st);
         return cudaGetLastError();
@@ -158,6 +182,7 @@ struct OpsImpl {
         o.D = T::D;
         o.key_bytes = sizeof(K);
         o.init = &init;
+        o.classify_smem_bytes = &classify_smem_bytes;
         o.level = &level;
         o.base = &base;
         o.detect = &detect;

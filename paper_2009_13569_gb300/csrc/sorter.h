@@ -43,7 +43,8 @@ struct LevelGrids {
 struct TypeOps {
     int D;         // element bytes
     int key_bytes; // sizeof(K)
-    cudaError_t (*init)(Sorter *);  // one-time kernel attributes
+    cudaError_t (*init)(Sorter *);  // kernel attributes (idempotent)
+    size_t (*classify_smem_bytes)(uint32_t k, uint32_t b);  // shared memory of k_classify
     cudaError_t (*level)(Sorter *, const LevelArgs &, const LevelGrids &, cudaStream_t);
     cudaError_t (*base)(Sorter *, const uint64_t *d_segs, uint32_t nsegs,
                         const uint32_t *nsegs_dev, uint32_t grid, cudaStream_t);

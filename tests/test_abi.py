@@ -139,11 +139,11 @@ def test_parameter_ranges_of_the_header(lib, dtype):
     assert ok(base_case=32) and ok(base_case=cap)
     assert rejected(base_case=31) and rejected(base_case=cap + 1)
     # blocks: b = largest power of two with b * D <= block_bytes; b * D a
-    # multiple of 16 and k * b * D at most 160 KiB
+    # multiple of 16, at most 2 KiB, and k * b * D at most 128 KiB
     for bb in (16, 64, 100, 400, 512, 1000, 1024, 2048, 4096):
         b = _block_elems(bb, D)
-        for k in (4, 64, 256):
-            valid = (b * D) % 16 == 0 and k * b * D <= 160 * 1024
+        for k in (4, 64, 128, 256):
+            valid = (b * D) % 16 == 0 and b * D <= 2048 and k * b * D <= 128 * 1024
             assert ok(k=k, block_bytes=bb) == valid, (bb, k)
             if not valid:
                 assert rejected(k=k, block_bytes=bb), (bb, k)

@@ -6,7 +6,8 @@ from paper_2009_13569_gb300 import autotune
 def test_search_finds_the_separable_minimum():
     # cost = f(kb) + g(base) + h(alpha): coordinate descent reaches the optimum
     def cost(p):
-        kb = {(256, 512): 3.0, (128, 1024): 1.0, (64, 2048): 2.0}[(p["k"], p["block_bytes"])]
+        kb = {(256, 512): 3.0, (128, 1024): 1.0, (64, 2048): 2.0, (128, 512): 2.5,
+              (64, 1024): 1.5, (64, 512): 4.0}[(p["k"], p["block_bytes"])]
         base = abs(p["base_case"] - autotune.base_cap("u64") // 2) / 1000.0
         alpha = {0.2: 0.3, 0.5: 0.1, 1.0: 0.2}[p["alpha_scale"]]
         return kb + base + alpha
@@ -17,7 +18,7 @@ def test_search_finds_the_separable_minimum():
     assert best["alpha_scale"] == 0.5
     # every candidate timed once, the starting point not twice
     keys = [tuple(sorted(p.items())) for p, _ in table]
-    assert len(keys) == len(set(keys)) == 3 + 2 + 2
+    assert len(keys) == len(set(keys)) == len(autotune.KB_PAIRS) + 2 + 2
 
 
 def test_search_skips_rejected_candidates():
@@ -29,6 +30,15 @@ def test_search_skips_rejected_candidates():
     best, table = autotune.search(cost, "u32")
     assert best["k"] == 64
     assert any(t is None for _, t in table)
+
+
+def test_every_kb_pair_fits_one_classification_cta():
+    # k * block bytes at most 128 KiB, blocks at most 2 KiB, as the library accepts
+    for k, bb in autotune.KB_PAIRS:
+        assert k * bb <= 128 * 1024 and bb <= 2048
+        for dtype in ("u32", "u64", "pair", "rec100", "quartet"):
+            from paper_2009_13569_gb300 import ipsgpu
+            assert ipsgpu.scratch_bytes(dtype, k=k, block_bytes=bb) > 0, (dtype, k, bb)
 
 
 def test_base_cap_matches_the_library_limit():

@@ -13,7 +13,10 @@ def test_autotune_segmented_params_sort_correctly():
     lengths = inputs.segment_lengths(200, 4, 17, seed=12)
     data, offsets = inputs.segmented_batch(lengths, seed=12, device=DEV)
     best, table = autotune.tune_segmented(torch, data, offsets, "u64", reps=2)
-    assert len(table) >= 3 and all(t is None or t > 0 for _, t in table)
+    # every (k, block bytes) pair of the grid is accepted and timed
+    kb = {(p["k"], p["block_bytes"]) for p, t in table}
+    assert kb == set(autotune.KB_PAIRS)
+    assert all(t is not None and t > 0 for _, t in table), table
     d = data.clone()
     with ipsgpu.Sorter("u64", **best) as s:
         s.sort_segmented(d.data_ptr(), d.numel(), offsets.data_ptr(), lengths.numel(), stream())
