@@ -145,3 +145,108 @@ def keys_nondecreasing(t, dtype, chunk=1 << 27):
         if not bool((k[1:] >= k[:-1]).all().item()):
             return False
     return True
+
+
+def record_index(a, dtype):
+    """Original index carried by every generated record (numpy): the value
+    word of pair and quartet, payload bytes 10..17 (little-endian) of
+    100-byte records."""
+    if dtype == "pair":
+        return a[:, 1].astype(np.int64)
+    if dtype == "quartet":
+        return a[:, 3].astype(np.int64)
+    if dtype == "rec100":
+        return np.ascontiguousarray(a[:, 10:18]).view("<u8").reshape(-1).astype(np.int64)
+    raise ValueError(dtype)
+
+
+def assert_records_intact(got, inp, dtype):
+    """Every output record is a whole input record, each input record
+    appears exactly once (record by record, through the original index
+    each generated record carries)."""
+    n = len(inp)
+    assert len(got) == n
+    idx = record_index(got, dtype)
+    assert idx.min() >= 0 and idx.max() < n, "index payload out of range"
+    assert np.bincount(idx, minlength=n).max() == 1, "a record lost or duplicated"
+    np.testing.assert_array_equal(got, inp[idx], err_msg="a record came apart")
+
+
+def assert_record_parity(got, inp, dtype):
+    """Sort parity for records, element by element: the key sequence equals
+    the oracle's (the sorted key sequence is unique) and the records are the
+    input's, each whole and once (any order of equal keys is correct)."""
+    ref = oracle.sort(inp, dtype)
+    np.testing.assert_array_equal(keys_of(got, dtype), keys_of(ref, dtype))
+    assert_records_intact(got, inp, dtype)
+
+
+def _mix64(z):
+    # splitmix64's finalizer (Steele, Lea, Flood 2014) on int64 bit patterns
+    z = (z ^ inputs._lsr(z, 30)) * inputs._s64(0xBF58476D1CE4E5B9)
+    z = (z ^ inputs._lsr(z, 27)) * inputs._s64(0x94D049BB133111EB)
+    return z ^ inputs._lsr(z, 31)
+
+
+def record_sig(t, dtype, chunk=1 << 24):
+    """Order-independent signature of the records of a device tensor (one
+    record per row): the words of each record are hashed together into one
+    64-bit value, and the signature is the count, sum, xor and sum of
+    squares of those values mod 2^64.  Any permutation of the records keeps
+    it; a word moved from one record to another changes it with
+    overwhelming odds (which a signature over words alone does not see)."""
+    n = t.shape[0]
+    acc = [n, 0, 0, 0]
+    m = (1 << 64) - 1
+    for a in range(0, n, chunk):
+        x = t[a:a + chunk]
+        if dtype == "rec100":
+            w = x.contiguous().view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+        else:
+            w = x.reshape(x.shape[0], -1).view(torch.int64)
+        h = torch.full((w.shape[0],), inputs._s64(0x9E3779B97F4A7C15), dtype=torch.int64,
+                       device=t.device)
+        for j in range(w.shape[1]):
+            h = _mix64(h ^ (w[:, j] + inputs._s64(0x9E3779B97F4A7C15 * (j + 1))))
+        acc[1] = (acc[1] + int(h.sum().item())) & m
+        y = h
+        while y.numel() > 1:
+            if y.numel() % 2:
+                y = torch.cat([y, torch.zeros(1, dtype=y.dtype, device=y.device)])
+            y = y[0::2] ^ y[1::2]
+        acc[2] ^= int(y[0].item()) & m
+        acc[3] = (acc[3] + int((h * h).sum().item())) & m
+    return tuple(acc)
+
+
+def records_intact_dev(got, inp, dtype, chunk=1 << 24):
+    """Device form of assert_records_intact (for inputs of many GiB):
+    True iff the original indices of got are a permutation of 0..n-1 and
+    every record of got equals the input record of its index."""
+    n = got.shape[0]
+    idx = torch.empty(n, dtype=torch.int64, device=got.device)
+    for a in range(0, n, chunk):
+        x = got[a:a + chunk]
+        if dtype == "pair":
+            idx[a:a + chunk] = x[:, 1]
+        elif dtype == "quartet":
+            idx[a:a + chunk] = x[:, 3]
+        elif dtype == "rec100":
+            b = x[:, 10:18].to(torch.int64)
+            v = torch.zeros(x.shape[0], dtype=torch.int64, device=x.device)
+            for j in range(8):
+                v |= b[:, j] << (8 * j)
+            idx[a:a + chunk] = v
+        else:
+            raise ValueError(dtype)
+    if int(idx.min().item()) < 0 or int(idx.max().item()) >= n:
+        return False
+    cnt = torch.zeros(n, dtype=torch.int32, device=got.device)
+    cnt.index_add_(0, idx, torch.ones(n, dtype=torch.int32, device=got.device))
+    if not bool((cnt == 1).all().item()):
+        return False
+    del cnt
+    for a in range(0, n, chunk):
+        if not torch.equal(got[a:a + chunk], inp[idx[a:a + chunk]]):
+            return False
+    return True

@@ -2,12 +2,18 @@
 the bench times them (ipsgpu_sort through the sorter's CUDA graph): keys
 non-decreasing and the multiset of words unchanged.  For u32 / u64 / f64
 these two properties determine the output (the sorted permutation of a
-multiset is unique), so the result equals the oracle's."""
+multiset is unique), so the result equals the oracle's.  For records (Pair,
+Quartet, 100-byte records) the check is by whole records: every output
+record equals the input record of the original index it carries, every
+index appears once, and a per-record hash signature is unchanged; with the
+keys non-decreasing that is exactly the set of correct outputs of an
+unstable sort."""
 import pytest
 import torch
 
 from paper_2009_13569_gb300 import inputs, ipsgpu
-from _util import DEV, keys_nondecreasing, multiset_sig, stream
+from _util import (DEV, keys_nondecreasing, multiset_sig, record_sig, records_intact_dev,
+                   stream)
 
 pytestmark = pytest.mark.gpu
 
@@ -25,11 +31,18 @@ def test_full_size_sort_properties(dtype, dist, log2n, algo):
     d = torch.empty(shape, dtype=torch.int32 if dtype == "u32" else torch.int64, device=DEV)
     inputs.generate_into(d, dist, dtype, seed=0x5EED)
     before = multiset_sig(d)
+    records = dtype in ("pair", "quartet")
+    if records:
+        inp = d.clone()
+        rsig = record_sig(d, dtype)
     with ipsgpu.Sorter(dtype, algo=algo) as s:
         s.sort(d.data_ptr(), n, stream())
         assert s.status(stream()) == ipsgpu.OK
     assert keys_nondecreasing(d, dtype)
     assert multiset_sig(d) == before
+    if records:
+        assert record_sig(d, dtype) == rsig
+        assert records_intact_dev(d, inp, dtype)
 
 
 @pytest.mark.parametrize("dtype,n,algo", [
@@ -49,15 +62,23 @@ def test_more_than_2_32_elements(dtype, n, algo):
     assert multiset_sig(d) == before
 
 
-@pytest.mark.parametrize("dtype,dist", [("f64", "normal"), ("rec100", "uniform")])
+@pytest.mark.parametrize("dtype,dist", [("f64", "normal"), ("rec100", "uniform"),
+                                        ("rec100", "rootdup"), ("pair", "uniform")])
 def test_wide_record_configuration_2e28(dtype, dist):
     # the wider-record plain-sort configuration at its full size: 2^28
-    # doubles (2 GiB) or 100-byte records (25 GiB)
+    # doubles (2 GiB), Pairs (4 GiB) or 100-byte records (25 GiB)
     n = 1 << 28
     d = inputs.generate(dist, dtype, n, seed=0x5EED, device=DEV)
     before = multiset_sig(d)
+    records = dtype != "f64"
+    if records:
+        inp = d.clone()
+        rsig = record_sig(d, dtype)
     with ipsgpu.Sorter(dtype) as s:
         s.sort(d.data_ptr(), n, stream())
         assert s.status(stream()) == ipsgpu.OK
     assert keys_nondecreasing(d, dtype)
     assert multiset_sig(d) == before
+    if records:
+        assert record_sig(d, dtype) == rsig
+        assert records_intact_dev(d, inp, dtype)

@@ -7,8 +7,10 @@ of a sorter's allocations.  Its result must equal the sorter-based level:
 identical bucket boundaries and, bucket by bucket, the same multiset of
 elements (the order inside a bucket is unspecified for both).  Two calls in
 a row check that the shared array's leftovers from one call do not leak into
-the next.  This file is named so that pytest collects it last; it passes
-alone in a fresh process as well.
+the next; between them a sorter with fewer classes and smaller blocks is
+created (less classification shared memory than the fixed array's level
+launches with), which must not disturb the second call.  This file is named
+so that pytest collects it last; it passes alone in a fresh process as well.
 """
 import numpy as np
 import pytest
@@ -33,6 +35,12 @@ def _rows(a, dtype):
     ("pair", 200_003, 63, False, "uniform"),
     ("quartet", 150_001, 127, True, "lexdup"),
     ("f64", 250_001, 100, False, "normal"),
+    # 100-byte records: 4-byte alignment, 4-record (400-byte) blocks
+    ("rec100", 100_003, 63, False, "uniform"),
+    ("rec100", 60_001, 31, True, "rootdup"),
+    # enough u32 keys that the fixed array's 64-stripe cap applies (a sorter
+    # would cut this level into 2 stripes per SM)
+    ("u32", 5_000_011, 255, False, "uniform"),
 ])
 def test_noalloc_matches_sorter_level_twice(dtype, n, m, eq, dist):
     dev = torch.device("cuda:0")
@@ -58,6 +66,9 @@ def test_noalloc_matches_sorter_level_twice(dtype, n, m, eq, dist):
         torch.cuda.synchronize(dev)
         bbn = bb.cpu().numpy().view(np.uint64)
         assert bbn[-1] == n, "kernel-side error reported by the no-alloc level"
+        if call == 0:
+            # a sorter whose classification needs less shared memory
+            small = ipsgpu.Sorter(dtype, k=64, block_bytes=512 if dtype == "rec100" else 256)
         np.testing.assert_array_equal(bbn, bb_ref.cpu().numpy().view(np.uint64))
         g = inputs.to_numpy(got.cpu(), dtype)
         r = inputs.to_numpy(ref.cpu(), dtype)
@@ -65,6 +76,7 @@ def test_noalloc_matches_sorter_level_twice(dtype, n, m, eq, dist):
             lo, hi = int(bbn[j]), int(bbn[j + 1])
             if hi > lo:
                 np.testing.assert_array_equal(_rows(g[lo:hi], dtype), _rows(r[lo:hi], dtype))
+    small.close()
 
 
 def test_noalloc_rejects_misaligned_splitters():
