@@ -861,9 +861,12 @@ def run_ours(args):
     graph_ms = None if args.instrumented else sum(times) / len(times)
     inst_ms = sum(itimes) / len(itimes)
     st = sorter.status(stream.cuda_stream)
-    # result check outside the timed region: non-decreasing as unsigned
+    # result check outside the timed region: non-decreasing as unsigned and
+    # the same multiset of keys as the input (which together fix the output)
     sgn = -(1 << 63)
-    ok = bool(((work[1:] ^ sgn) >= (work[:-1] ^ sgn)).all().item()) and st == ipsgpu.OK
+    src_sig = _multiset_sig(torch, src)
+    ok = (bool(((work[1:] ^ sgn) >= (work[:-1] ^ sgn)).all().item()) and st == ipsgpu.OK
+          and _multiset_sig(torch, work) == src_sig)
     ms = sum(times) / len(times)
     ms, bad = reduce_max_over_ranks(pg, [ms, 0.0 if ok else 1.0], dev)
     ok = bad == 0.0
@@ -909,7 +912,8 @@ def run_ours(args):
         sorter = sorter_saved
         rstats = rs.kernel_stats()
         rok = rs.status(stream.cuda_stream) == ipsgpu.OK and bool(
-            ((work[1:] ^ sgn) >= (work[:-1] ^ sgn)).all().item())
+            ((work[1:] ^ sgn) >= (work[:-1] ^ sgn)).all().item()) and (
+            _multiset_sig(torch, work) == src_sig)
         rms, rbad = reduce_max_over_ranks(pg, [sum(rtimes) / len(rtimes), 0.0 if rok else 1.0],
                                           dev)
         rok = rbad == 0.0
@@ -963,7 +967,8 @@ def run_ours(args):
         eok = all(s_.status(st_.cuda_stream) == ipsgpu.OK for s_, st_ in zip(sorters, streams))
         for h in hdst:  # every result buffer checked on the device
             work.copy_(h)
-            eok = eok and bool(((work[1:] ^ sgn) >= (work[:-1] ^ sgn)).all().item())
+            eok = eok and bool(((work[1:] ^ sgn) >= (work[:-1] ^ sgn)).all().item()) and (
+                _multiset_sig(torch, work) == src_sig)
         ems, sms, ebad = reduce_max_over_ranks(pg, [ems, sms, 0.0 if eok else 1.0], dev)
         eok = ebad == 0.0
         e2e = {"value": replica_value(world, n, ems), "unit": UNIT,
