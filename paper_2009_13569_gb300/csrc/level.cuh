@@ -86,7 +86,8 @@ __device__ __forceinline__ const typename T::K *seg_spl(const LevelArgs &a, cons
     return reinterpret_cast<const typename T::K *>(a.keys + sd.key_off) + sd.C;
 }
 
-// Copies the segment's tree and splitters into shared memory; callers sync.
+// Copies the segment's splitters, and its tree unless s_tree is null, into
+// shared memory; callers sync.
 template <class T>
 __device__ __forceinline__ void load_classifier(LevelClassifier<T> &c, const LevelArgs &a,
                                                 const SegDesc &sd, const SegState &st,
@@ -103,7 +104,7 @@ __device__ __forceinline__ void load_classifier(LevelClassifier<T> &c, const Lev
         const K *gt = seg_tree<T>(a, sd);
         const K *gs = seg_spl<T>(a, sd);
         for (uint32_t i = threadIdx.x; i < st.K; i += blockDim.x) {
-            s_tree[i] = gt[i];
+            if (s_tree) s_tree[i] = gt[i];
             s_spl[i] = gs[i];
         }
     }
