@@ -142,6 +142,57 @@ __device__ __forceinline__ void store_unit(unsigned char *dst, const unsigned ch
         *reinterpret_cast<uint32_t *>(dst) = *reinterpret_cast<const uint32_t *>(src);
 }
 
+// Insertion sort of r[0..c) in shared memory (one thread).
+template <class T>
+__device__ __forceinline__ void insertion_sort(typename T::E *r, uint32_t c) {
+    typedef typename T::E E;
+    typedef typename T::K K;
+    for (uint32_t i = 1; i < c; i++) {
+        const E x = r[i];
+        const K kx = T::key(x);
+        uint32_t j = i;
+        while (j > 0 && kx < T::key(r[j - 1])) {
+            r[j] = r[j - 1];
+            j--;
+        }
+        r[j] = x;
+    }
+}
+
+// Sorts r[0..c), 2 <= c <= 4, in registers with the optimal 4-input
+// network (0,1) (2,3) (0,2) (1,3) (1,2); a comparator touching position c
+// or above is skipped, which leaves the 3- and 2-input networks.
+template <class T>
+__device__ __forceinline__ void sort_upto4(typename T::E *r, uint32_t c) {
+    typedef typename T::E E;
+    typedef typename T::K K;
+    E x[4];
+    K k[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        x[i] = r[(uint32_t)i < c ? i : 0];
+        k[i] = T::key(x[i]);
+    }
+    auto ce = [&](int i, int j) {
+        if (k[j] < k[i]) {
+            const E tx = x[i];
+            x[i] = x[j];
+            x[j] = tx;
+            const K tk = k[i];
+            k[i] = k[j];
+            k[j] = tk;
+        }
+    };
+    ce(0, 1);
+    if (c > 3) ce(2, 3);
+    if (c > 2) ce(0, 2);
+    if (c > 3) ce(1, 3);
+    if (c > 2) ce(1, 2);
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+        if ((uint32_t)i < c) r[i] = x[i];
+}
+
 // Sorts each listed segment (segs[2i] = device byte address, segs[2i+1] = n,
 // n <= smax) in place; the number of segments is *nsegs_dev if given, else
 // nsegs_host.  One CTA per segment at a time; its bytes were prefetched into
@@ -187,12 +238,13 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
     constexpr int kBaseThreads = S::NT;
     // Digits per pass: about two elements per digit for keys up to 8 bytes,
     // one for wider records (whose insertion-sort moves cost more), at most
-    // 2^14 digits for 4-byte keys and 2^13 otherwise (measured optima; 2^13
-    // in the small shape) -- unless one digit per key value fits in 2^MAXB
+    // 2^MAXB digits for 4-byte keys and half that otherwise, which leaves
+    // the upper half of the counter words to the list of mid-size
+    // sub-buckets (measured optima: 2^13 digits in the large shape, 2^12 in
+    // the small one) -- unless one digit per key value fits in 2^MAXB
     // digits and at most twice that many: then the pass is final (no
-    // insertion sorts)
-    constexpr int DBITS = T::D <= 4 ? S::MAXB
-                                    : (S::MAXB < kBaseDigitBits - 1 ? S::MAXB : kBaseDigitBits - 1);
+    // finishing sorts)
+    constexpr int DBITS = T::D <= 4 ? S::MAXB : S::MAXB - 1;
     constexpr uint32_t kPerDigitLog = T::D <= 8 ? 1u : 0u;
     constexpr int ND = 1 << S::MAXB;
     constexpr int NB = T::D <= 8 ? 8 : (T::D <= 16 ? 4 : (T::D <= 32 ? 2 : 1));  // in flight per thread
@@ -208,7 +260,9 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
     uint32_t *cur = sstk + S::SSTK;                               // ND / 2
     uint32_t *wtmp = cur + ND / 2;                                         // 34
     __shared__ unsigned long long red[2][32];
-    __shared__ uint32_t sp, ssp, sh_top;
+    __shared__ uint32_t sp, ssp, sh_top, sh_nmid;
+    // sorting networks and the mid-size list for keys up to 32 bytes
+    constexpr bool kNetwork = T::D <= 32;
     constexpr uint32_t kNoRange = 0xFFFFFFFFu;  // no range has a0 = len = 65535
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = kBaseThreads / 32;
@@ -298,6 +352,7 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
         if (tid == 0) {
             sp = 1;
             ssp = 0;
+            sh_nmid = 0;
             stk[0] = (uint32_t)n;
         }
         bool first = true;
@@ -310,6 +365,7 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
                 if (sp > kBaseStack) sp = kBaseStack;  // pushes past the stack were dropped
                 sh_top = sp ? stk[sp - 1] : kNoRange;
                 if (sp) sp--;
+                sh_nmid = 0;  // the last pass's list has been read
             }
             __syncthreads();
             const uint32_t top = sh_top;
@@ -422,8 +478,15 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
             }
             __syncthreads();
             // per sub-bucket (one thread each): a large one gets another
-            // pass; a small one is finished by insertion sort in shared
-            // memory (its elements are in arbitrary order after the scatter)
+            // pass or waits for a warp; one of 2..4 elements is sorted by a
+            // 5-comparator network in registers (comparators predicated on
+            // the size, so the warp does not diverge on it); one of 5..24
+            // elements goes to a list (the counter words this pass leaves
+            // unused) that threads take one entry each afterwards, so that
+            // no warp waits for its lanes' longest insertion sort (when the
+            // list is full, or for records, insertion sort right away)
+            uint32_t *mid = cur + nw;
+            const uint32_t mid_cap = (uint32_t)(ND / 2) - nw;
             for (uint32_t d = tid; d < nd && !exact; d += kBaseThreads) {
                 const uint32_t lo = d ? dend(d - 1) : 0u, c = dend(d) - lo;
                 if (c > kBaseSmall) {
@@ -438,19 +501,21 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
                         sstk[q] = ((a0 + lo) << 16) | c;
                     else
                         set_status(status, IPSGPU_E_INTERNAL);
+                } else if (kNetwork && c <= 4) {
+                    if (c > 1) sort_upto4<T>(buf + a0 + lo, c);
                 } else if (c > 1) {
-                    E *r = buf + a0 + lo;
-                    for (uint32_t i = 1; i < c; i++) {
-                        const E x = r[i];
-                        const K kx = T::key(x);
-                        uint32_t j = i;
-                        while (j > 0 && kx < T::key(r[j - 1])) {
-                            r[j] = r[j - 1];
-                            j--;
-                        }
-                        r[j] = x;
-                    }
+                    const uint32_t q = kNetwork ? atomicAdd(&sh_nmid, 1u) : mid_cap;
+                    if (q < mid_cap)
+                        mid[q] = (lo << 16) | c;
+                    else
+                        insertion_sort<T>(buf + a0 + lo, c);
                 }
+            }
+            if (kNetwork) {
+                __syncthreads();
+                const uint32_t nmid = min(sh_nmid, mid_cap);
+                for (uint32_t q = tid; q < nmid; q += kBaseThreads)
+                    insertion_sort<T>(buf + a0 + (mid[q] >> 16), mid[q] & 0xFFFFu);
             }
             __syncthreads();
             // the range back to global memory, coalesced: final where the
