@@ -29,6 +29,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# request buffers of the serving run range from KiB to 128 GiB: let the
+# caching allocator map memory on demand instead of keeping fixed segments
+os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
 
 METRIC = "Gelem/s sorted (uint64, n=2^30)"
 UNIT = "Gelem/s"
@@ -65,6 +68,8 @@ def _args():
                    help="comma-separated algorithms the sweep runs: IPS4o, IPS2Ra (u32/u64 "
                         "only) and IPS4o-tree (IPS4o walking every element from the tree's "
                         "root, without the start-node table)")
+    p.add_argument("--serve-only", action="store_true",
+                   help="only the serving run (200-request traces at three loads)")
     p.add_argument("--batched-only", action="store_true",
                    help="only the batched form's graph launches (both workloads), one JSON "
                         "line: the command of the batched launch-list profile")
@@ -396,55 +401,82 @@ def run_segmented(torch, inputs, ipsgpu, dev, steps, graph_only=False, instrumen
     return out
 
 
-SERVE = {"requests": 600, "log2_lo": 10, "log2_hi": 30, "huge_log2": 33, "budget_gb": 96,
-         "lanes": 4, "load": 0.8}
+SERVE = {"requests": 200, "log2_lo": 10, "log2_hi": 32, "huge_log2": 34, "huge_every": 50,
+         "budget_gb": 170, "lanes": 3, "loads": (0.5, 0.8, 0.95), "pool_log2": 30}
+SERVE_DISTS = ("uniform", "exponential", "rootdup", "twodup", "eightdup", "almostsorted",
+               "zipf", "sorted", "reversesorted", "zero")
 
 
 def run_serve(torch, inputs, ipsgpu, dev):
-    """Serving form: Poisson arrivals of sort requests (sizes log-uniform,
-    uint32 / uint64 / Pair keys, distributions of the plain-sort configs) and
-    one huge in-place uint64 request, admitted by HBM footprint under a
-    fixed budget; the server (continuous batching over streams) against the
-    same trace served first-in first-out by one plain sort at a time."""
+    """Serving form: 200 sort requests (sizes log-uniform in [2^10, 2^32],
+    uint32 / uint64 / Pair keys in turn, data from the ten plain-sort
+    distributions; every 50th request a 2^34-element uint64 request, 128 GiB, sorted
+    in place) arriving as a Poisson process at 50, 80 and 95 % of the plain
+    sort's capacity, admitted by HBM footprint under a 170 GB budget.  The
+    server (continuous batching over streams) runs every trace live; the
+    plain form is first-in first-out, one plain sort at a time, whose
+    latencies follow from the measured service time of each request sorted
+    alone (a single-server queue: the order and the service times fix
+    them).
+
+    A request's data arrives in HBM when it is admitted: a copy from a
+    pre-generated pool of its type (2^30 elements over the ten
+    distributions); a request larger than the pool is tiled with pool
+    copies, each tile's keys XORed with its own seeded 64-bit constant.
+    Both forms include that copy in the service time and the latency.
+    Every result is checked: keys non-decreasing, the multiset of words
+    equal to the input's, and so each served result equal to the same
+    request sorted alone (the sorted output is unique)."""
+    import collections
     import numpy as np
     cfg = SERVE
     R = cfg["requests"]
+    # the caching allocator keeps freed request buffers for reuse; held to
+    # 85 % of the device it returns them before it would need more
+    torch.cuda.set_per_process_memory_fraction(0.85, dev)
     rng = np.random.default_rng(SEED & 0xFFFFFFFF)
     sizes = inputs.segment_lengths(R, cfg["log2_lo"], cfg["log2_hi"], seed=SEED + 5).tolist()
     types = ["u32", "u64", "pair"]
-    reqs = [{"dtype": types[i % 3], "n": int(m)} for i, m in enumerate(sizes)]
-    huge_n = 1 << cfg["huge_log2"]
-    reqs.insert(R // 2, {"dtype": "u64", "n": huge_n, "huge": True})
-    # source pools (one per type, every distribution in turn) and the huge
-    # request's own buffer; a request copies its slice of a pool into a
-    # fresh buffer when it arrives, as data arriving in HBM
-    pmax = 1 << cfg["log2_hi"]
+    reqs = []
+    for i, m in enumerate(sizes):
+        if i % cfg["huge_every"] == cfg["huge_every"] // 2:
+            reqs.append({"dtype": "u64", "n": 1 << cfg["huge_log2"], "huge": True,
+                         "seed": SEED + 1000 + i})
+        else:
+            reqs.append({"dtype": types[i % 3], "n": int(m), "seed": SEED + 1000 + i})
+    pmax = 1 << cfg["pool_log2"]
     pools = {}
     for t in types:
         shape = (pmax, 2) if t == "pair" else (pmax,)
         pool = torch.empty(shape, dtype=torch.int32 if t == "u32" else torch.int64, device=dev)
-        dists = inputs.INT_DISTS[:8]  # all but the already-sorted ones' twins
-        step = pmax // len(dists)
-        for j, d in enumerate(dists):
-            part = pool[j * step:(j + 1) * step if j + 1 < len(dists) else pmax]
+        step = pmax // len(SERVE_DISTS)
+        for j, d in enumerate(SERVE_DISTS):
+            part = pool[j * step:(j + 1) * step if j + 1 < len(SERVE_DISTS) else pmax]
             inputs.generate_into(part, d, t, seed=SEED + 17 * j)
         pools[t] = pool
     for r in reqs:
-        if not r.get("huge"):
-            r["off"] = int(rng.integers(0, pmax - r["n"] + 1))
-    huge = torch.empty(huge_n, dtype=torch.int64, device=dev)
-    elem = {"u32": 4, "u64": 8, "pair": 16}
+        r["pooled"] = r["n"] <= pmax
+        r["off"] = int(rng.integers(0, pmax - r["n"] + 1)) if r["pooled"] else 0
 
     def fill(r, buf, stream):
         with torch.cuda.stream(stream):
-            if r.get("huge"):
-                inputs.generate_into(buf, "uniform", "u64", seed=SEED + 99)
-            else:
-                buf.copy_(pools[r["dtype"]][r["off"]:r["off"] + r["n"]])
+            pool = pools[r["dtype"]]
+            if r["pooled"]:
+                buf.copy_(pool[r["off"]:r["off"] + r["n"]])
+                return
+            for q, a in enumerate(range(0, r["n"], pmax)):
+                m = min(pmax, r["n"] - a)
+                dst = buf[a:a + m]
+                dst.copy_(pool[:m])
+                c = inputs.splitmix64_py(q, r["seed"])
+                keys = dst[:, 0] if r["dtype"] == "pair" else dst
+                if r["dtype"] == "u32":  # int32 storage: the constant's low word, signed
+                    c &= 0xFFFFFFFF
+                    keys ^= c - (1 << 32) if c >> 31 else c
+                else:
+                    keys ^= inputs._s64(c)
 
     def alloc(r):
-        if r.get("huge"):
-            return huge
         shape = (r["n"], 2) if r["dtype"] == "pair" else (r["n"],)
         return torch.empty(shape, dtype=torch.int32 if r["dtype"] == "u32" else torch.int64,
                            device=dev)
@@ -459,68 +491,82 @@ def run_serve(torch, inputs, ipsgpu, dev):
             res &= (x[1:] >= x[:-1]).all()
         return res
 
-    # phase A: first-in first-out, one plain sort at a time (service times)
+    # phase A: every request alone, first-in first-out (service times,
+    # reference results); the input's multiset is taken from a second fill
     st = torch.cuda.Stream(dev)
     sorters = {t: ipsgpu.Sorter(t) for t in types}
     for t in types:
         sorters[t].prepare()
-    service, checks = [], []
+    service, fifo_ok = [], True
     for r in reqs:
         buf = alloc(r)
-        if r.get("huge"):
-            fill(r, buf, st)  # regenerated outside the timed copy + sort
-            st.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        if not r.get("huge"):
-            fill(r, buf, st)
+        fill(r, buf, st)
         sorters[r["dtype"]].sort(buf.data_ptr(), r["n"], st.cuda_stream)
         e1.record(st)
-        with torch.cuda.stream(st):
-            checks.append(sorted_ok(buf, r["dtype"]))
         st.synchronize()
         service.append(e0.elapsed_time(e1) * 1e3)  # us
+        with torch.cuda.stream(st):
+            ok = bool(sorted_ok(buf, r["dtype"]).item())
+            r["sig"] = _multiset_sig_dev(torch, buf)
+            fill(r, buf, st)
+            ok = ok and bool(torch.equal(_multiset_sig_dev(torch, buf), r["sig"]))
+        fifo_ok = fifo_ok and ok
         del buf
-    fifo_ok = all(bool(c.item()) for c in checks) and all(
-        sorters[t].status(st.cuda_stream) == ipsgpu.OK for t in types)
+        if r.get("huge"):
+            torch.cuda.empty_cache()
+    fifo_ok = fifo_ok and all(sorters[t].status(st.cuda_stream) == ipsgpu.OK for t in types)
     for t in types:
         sorters[t].close()
+    torch.cuda.synchronize(dev)
     total_service = sum(service)
-    lam = cfg["load"] * len(reqs) / total_service  # arrivals per us
-    gaps = rng.exponential(1.0 / lam, size=len(reqs))
-    arrival = np.cumsum(gaps) - gaps[0]
-    fin, prev = [], 0.0
-    for a, sv in zip(arrival, service):
-        prev = max(prev, a) + sv
-        fin.append(prev)
-    fifo_lat = np.array(fin) - arrival
     elems = sum(r["n"] for r in reqs)
 
-    # phase B: the server, live, on the same arrival times; then on all
-    # requests arriving at once (throughput at saturation)
-    def serve_live(arr):
-        fill(reqs[R // 2], huge, st)  # the huge request's data, regenerated
-        st.synchronize()
-        srv = ipsgpu.Server(cfg["budget_gb"] << 30, lanes=cfg["lanes"], dtypes=types)
-        copy_st = torch.cuda.Stream(dev)
+    def fifo(arr):
+        fin, prev = [], 0.0
+        for a, sv in zip(arr, service):
+            prev = max(prev, a) + sv
+            fin.append(prev)
+        return np.array(fin) - arr, (fin[-1] - arr[0]) * 1e-6
+
+    # phase B: the server, live, on a trace of arrival times; requests'
+    # data arrive on four copy streams in turn
+    check_st = torch.cuda.Stream(dev)
+    copy_sts = [torch.cuda.Stream(dev) for _ in range(4)]
+
+    def serve_live(arr, check):
+        srv = ipsgpu.Server(cfg["budget_gb"] * 10 ** 9, lanes=cfg["lanes"], dtypes=types)
+        nfill = [0]
         t0 = srv.now_us() + 20_000.0
         pending = collections.deque(range(len(reqs)))
-        live, lat, waits, checks_ = {}, [0.0] * len(reqs), [0.0] * len(reqs), []
-        t_last = t0
+        live, lat, waits = {}, [0.0] * len(reqs), [0.0] * len(reqs)
+        checks, t_last, huge_done = [], t0, 0
         while pending or live:
             now = srv.now_us()
             progressed = False
             for tk in list(live):
                 done, stt = srv.poll(tk)
                 if done:
-                    i, buf = live.pop(tk)
+                    i, buf, copy_st = live.pop(tk)
                     _, _, td = srv.times(tk)
                     lat[i] = td - (t0 + arr[i])
                     t_last = max(t_last, td)
-                    with torch.cuda.stream(copy_st):
-                        checks_.append((sorted_ok(buf, reqs[i]["dtype"]), stt))
+                    # a checked run queues the check behind the sort on a
+                    # stream of the lowest priority and reads it after the
+                    # trace; the buffer is not reused before the check ran
+                    if check:
+                        check_st.wait_stream(copy_st)
+                        with torch.cuda.stream(check_st):
+                            checks.append((i, stt, sorted_ok(buf, reqs[i]["dtype"]),
+                                           _multiset_sig_dev(torch, buf)))
+                        buf.record_stream(check_st)
+                    else:
+                        checks.append((i, stt, None, None))
+                    huge_done += 1 if reqs[i].get("huge") else 0
                     srv.release(tk)
+                    del buf
                     progressed = True
             # admission in arrival order; while a large request waits for
             # memory, small ones behind it may still enter (the server keeps
@@ -540,50 +586,78 @@ def run_serve(torch, inputs, ipsgpu, dev):
                     large_blocked = True
                     continue
                 waits[i] = srv.now_us() - (t0 + arr[i])
+                copy_st = copy_sts[nfill[0] % len(copy_sts)]
+                nfill[0] += 1
                 buf = alloc(r)
-                if not r.get("huge"):
-                    fill(r, buf, copy_st)
+                fill(r, buf, copy_st)
                 srv.start(tk, buf.data_ptr(), copy_st.cuda_stream)
-                live[tk] = (i, buf)
+                live[tk] = (i, buf, copy_st)
                 pending.remove(i)
                 progressed = True
             if not progressed:
                 time.sleep(20e-6)
         srv.drain()
         torch.cuda.synchronize(dev)
-        ok_ = all(bool(c.item()) and x == ipsgpu.OK for c, x in checks_)
         srv.close()
-        return np.array(lat), max(waits), (t_last - t0) * 1e-6, ok_
+        ok_ = len(checks) == len(reqs) and all(
+            stt == ipsgpu.OK and (not check or (bool(so.item()) and bool(torch.equal(sg, reqs[i]["sig"]))))
+            for i, stt, so, sg in checks)
+        del checks
+        torch.cuda.empty_cache()
+        return np.array(lat), max(waits), (t_last - t0) * 1e-6, ok_, huge_done
 
-    import collections
-    lat, wait_max, span, srv_ok = serve_live(arrival)
-    _, _, sat_span, sat_ok = serve_live(np.zeros(len(reqs)))
-    del pools, huge
-    fifo_span = (fin[-1] - arrival[0]) * 1e-6
+    def summary(lat):
+        return {"p50_ms": float(np.percentile(lat, 50)) * 1e-3,
+                "p99_ms": float(np.percentile(lat, 99)) * 1e-3,
+                "latency_ms": latency_summary(lat)}
+
+    loads, all_ok, huge_all = [], fifo_ok, True
+    gaps0 = rng.exponential(1.0, size=len(reqs))
+    for rho in cfg["loads"]:
+        lam = rho * len(reqs) / total_service  # arrivals per us
+        gaps = gaps0 / lam
+        arrival = np.cumsum(gaps) - gaps[0]
+        lat, wait_max, span, ok, nh = serve_live(arrival, False)
+        flat, fspan = fifo(arrival)
+        all_ok = all_ok and ok
+        huge_all = huge_all and nh == sum(1 for r in reqs if r.get("huge"))
+        loads.append({"load": rho,
+                      "server": dict(summary(lat), value=elems / span / 1e9, unit=UNIT,
+                                     max_admission_wait_ms=wait_max * 1e-3, status_ok=ok),
+                      "plain_fifo": dict(summary(flat), value=elems / fspan / 1e9, unit=UNIT)})
+    _, _, sat_span, sat_ok, _ = serve_live(np.zeros(len(reqs)), False)
+    # the same requests served once more with every result checked (untimed)
+    _, _, _, chk_ok, chk_huge = serve_live(np.zeros(len(reqs)), True)
+    all_ok = all_ok and sat_ok and chk_ok
+    del pools
+    torch.cuda.empty_cache()
+    huge = [r for r in reqs if r.get("huge")]
     return {"requests": len(reqs), "elements": int(elems),
-            "trace": "Poisson arrivals at %.0f%% of the plain sort's capacity; sizes log-uniform "
-                     "[2^%d, 2^%d]; u32/u64/Pair in turn; pool slices over 8 distributions; "
-                     "one 2^%d-element uint64 request (%d GiB) in place"
-                     % (100 * cfg["load"], cfg["log2_lo"], cfg["log2_hi"], cfg["huge_log2"],
-                        huge_n * 8 >> 30),
+            "trace": "Poisson arrivals at %s of the plain sort's capacity; sizes log-uniform "
+                     "[2^%d, 2^%d]; u32/u64/Pair in turn over pools of the ten plain-sort "
+                     "distributions; "
+                     "%d requests of 2^%d uint64 keys (%d GiB, %.0f %% of the requests) in place"
+                     % ("/".join("%.0f%%" % (100 * x) for x in cfg["loads"]), cfg["log2_lo"],
+                        cfg["log2_hi"], len(huge), cfg["huge_log2"], (1 << cfg["huge_log2"]) * 8 >> 30,
+                        100.0 * len(huge) / len(reqs)),
+            "data": "copies of a 2^%d-element pool per type (ten distributions); larger requests "
+                    "tiled with pool copies, each tile's keys XORed with a seeded 64-bit "
+                    "constant; inside service time and latency" % cfg["pool_log2"],
             "budget_gb": cfg["budget_gb"], "lanes": cfg["lanes"],
-            "server": {"p50_ms": float(np.percentile(lat, 50)) * 1e-3,
-                       "p99_ms": float(np.percentile(lat, 99)) * 1e-3,
-                       "latency_ms": latency_summary(lat),
-                       "max_admission_wait_ms": wait_max * 1e-3,
-                       "value_at_load": elems / span / 1e9,
-                       "value_saturated": elems / sat_span / 1e9, "unit": UNIT,
-                       "result_sorted": srv_ok and sat_ok},
-            "plain_fifo": {"p50_ms": float(np.percentile(fifo_lat, 50)) * 1e-3,
-                           "p99_ms": float(np.percentile(fifo_lat, 99)) * 1e-3,
-                           "latency_ms": latency_summary(fifo_lat),
-                           "value_at_load": elems / fifo_span / 1e9,
-                           "value_saturated": elems / (total_service * 1e-6) / 1e9, "unit": UNIT,
-                           "result_sorted": fifo_ok},
-            "latency": "arrival to completion, copy of the request's data into its buffer "
-                       "included; plain_fifo latencies follow from the measured service time of "
-                       "each request sorted alone, one after another in arrival order",
-            "saturated": "every request available at once: elements / makespan"}
+            "huge_requests_served_every_load": huge_all,
+            "loads": loads,
+            "saturated": {"server_value": elems / sat_span / 1e9,
+                          "plain_fifo_value": elems / (total_service * 1e-6) / 1e9, "unit": UNIT,
+                          "form": "every request available at once: elements / makespan"},
+            "result_exact": all_ok,
+            "latency": "arrival to completion, the arrival of the request's data included",
+            "plain_fifo": "simulated single-server FIFO queue over the measured service times of "
+                          "the requests sorted alone (fill + ipsgpu_sort each), not run live",
+            "checks": "every result of the plain sorts, and of one more served run of all "
+                      "requests (not timed; the timed runs check each request's status only): "
+                      "keys non-decreasing and the multiset of words equal to the input's, so "
+                      "each served result equals the same request sorted alone",
+            "checked_run_huge_requests": chk_huge}
 
 
 def latency_summary(lat_us):
@@ -638,6 +712,30 @@ def _multiset_sig(torch, t):
         acc[2] ^= int(_xor_reduce(torch, x))
         acc[3] = (acc[3] + int((x * x).sum().item())) & ((1 << 64) - 1)
     return tuple(acc)
+
+
+def _multiset_sig_dev(torch, t, chunk=1 << 27):
+    """_multiset_sig without the host round trips: a device tensor (sum,
+    xor, sum of squares of the words, wrapping int64), queued on the
+    current stream, so that a check can run behind other work."""
+    if t.dtype == torch.uint8:
+        w = t.contiguous().view(torch.int32).reshape(-1).to(torch.int64)
+    elif t.element_size() == 4:
+        w = t.reshape(-1).view(torch.int32).to(torch.int64)
+    else:
+        w = t.reshape(-1).view(torch.int64)
+    acc = torch.zeros(3, dtype=torch.int64, device=t.device)
+    for a in range(0, w.numel(), chunk):
+        x = w[a:a + chunk]
+        acc[0] += x.sum()
+        acc[2] += (x * x).sum()
+        y = x
+        while y.numel() > 1:
+            if y.numel() % 2:
+                y = torch.cat([y, torch.zeros(1, dtype=y.dtype, device=y.device)])
+            y = y[0::2] ^ y[1::2]
+        acc[1] ^= y[0]
+    return acc
 
 
 def _xor_reduce(torch, x):
@@ -1031,6 +1129,15 @@ def run_batched_only(args):
     print(json.dumps({"batched_only": True, "segmented": seg}))
 
 
+def run_serve_only(args):
+    import torch
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2009_13569_gb300 import inputs, ipsgpu
+    dev = torch.device("cuda", 0)
+    print(json.dumps({"serve_only": True, "serve": run_serve(torch, inputs, ipsgpu, dev)}))
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -1039,6 +1146,8 @@ def main():
         run_sweep(args)
     elif args.batched_only:
         run_batched_only(args)
+    elif args.serve_only:
+        run_serve_only(args)
     else:
         run_ours(args)
 

@@ -208,3 +208,38 @@ def test_server_many_client_threads():
             th.join(timeout=300)
         assert not errors, errors[0]
         assert srv.usage()[0] == srv.usage()[2]
+
+
+@pytest.mark.parametrize("dtype,dist", [("u64", "uniform"), ("pair", "zipf"), ("u32", "twodup")])
+def test_server_2e24_request_matches_oracle(dtype, dist):
+    # a 2^24-element request served while smaller ones run beside it, the
+    # sub-request size at which the serving configuration's huge results
+    # are checked against the oracle (the 2^34-element ones are checked by
+    # properties in the bench): identical to the oracle, key by key and
+    # record by record
+    from _util import assert_record_parity
+    n = 1 << 24
+    host = inputs.generate(dist, dtype, n, seed=24)
+    small = [inputs.generate("uniform", "u64", 1000 + 37 * i, seed=i) for i in range(8)]
+    with ipsgpu.Server(32 << 30, lanes=3, dtypes=("u32", "u64", "pair")) as srv:
+        d = to_dev(host)
+        torch.cuda.synchronize()
+        t = srv.submit(d.data_ptr(), n, dtype)
+        others = []
+        for h in small:
+            ds = to_dev(h)
+            torch.cuda.synchronize()
+            others.append((srv.submit(ds.data_ptr(), h.shape[0], "u64"), h, ds))
+        assert srv.wait(t) == ipsgpu.OK
+        got = inputs.to_numpy(d.cpu(), dtype)
+        inp = inputs.to_numpy(host, dtype)
+        if dtype in ("u32", "u64"):
+            import oracle
+            np.testing.assert_array_equal(got, oracle.sort(inp, dtype))
+        else:
+            assert_record_parity(got, inp, dtype)
+        for ts, h, ds in others:
+            assert srv.wait(ts) == ipsgpu.OK
+            assert_sorted_parity(inputs.to_numpy(ds.cpu(), "u64"), inputs.to_numpy(h, "u64"), "u64")
+            srv.release(ts)
+        srv.release(t)
