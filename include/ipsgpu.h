@@ -273,6 +273,16 @@ int ipsgpu_kernel_stats(ipsgpu_sorter *s, uint64_t *launches, double *ms,
                         double *bytes, int cap);
 const char *ipsgpu_kernel_name(int kind);
 
+/* Recursion statistics of the sorter's last sort, segmented or batched run
+ * made with timing on (the host-driven waves of the device-planned
+ * recursion, Sec. 3.2's task structure breadth-first): the number of waves,
+ * the largest number of segments waiting in the sorter's fixed ring between
+ * two waves (the task metadata the recursion keeps; App. B's strictly
+ * in-place variant keeps none), and the ring's capacity.  Zeros if the last
+ * run was not timed.  Errors: E_INVAL (s NULL). */
+int ipsgpu_wave_stats(ipsgpu_sorter *s, uint64_t *waves, uint64_t *max_pending,
+                      uint64_t *ring_capacity);
+
 /* Test hook for failure detection: launches one kernel that waits, with the
  * sorter's bounded-wait helper and at most `spin_limit` polls, on a device
  * flag that nothing sets, so the wait must give up and record

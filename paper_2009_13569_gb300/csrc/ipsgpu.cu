@@ -413,6 +413,8 @@ int graph_run(Sorter &s, const GJob &job, cudaStream_t st) {
         }
         return cuda_status(cudaGraphLaunch(s.wave_exec, st));
     }
+    s.last_waves = 0;
+    s.last_max_pending = 0;
     for (uint32_t w = 0; w < kMaxWaves; w++) {
         NvtxRange nvtx_wave("ipsgpu wave");
         const size_t l0 = s.launches.size();
@@ -422,6 +424,8 @@ int graph_run(Sorter &s, const GJob &job, cudaStream_t st) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return IPSGPU_E_CUDA;
         const GState &gs = *reinterpret_cast<const GState *>(s.h_gstate);
+        s.last_waves++;
+        s.last_max_pending = std::max<uint64_t>(s.last_max_pending, gs.tail - gs.head);
         // algorithmic bytes of the wave's launches (2 D per element moved)
         for (size_t q = l0; q < s.launches.size(); q++) {
             TimedLaunch &l = s.launches[q];
@@ -936,6 +940,15 @@ int ipsgpu_kernel_stats(ipsgpu_sorter *h, uint64_t *launches, double *ms, double
         s.stat_bytes[i] = 0;
     }
     return KK_COUNT;
+}
+
+int ipsgpu_wave_stats(ipsgpu_sorter *h, uint64_t *waves, uint64_t *max_pending,
+                      uint64_t *ring_capacity) {
+    if (!h) return IPSGPU_E_INVAL;
+    if (waves) *waves = h->s.last_waves;
+    if (max_pending) *max_pending = h->s.last_max_pending;
+    if (ring_capacity) *ring_capacity = h->s.ring_cap;
+    return IPSGPU_OK;
 }
 
 int ipsgpu_debug_bounded_wait(ipsgpu_sorter *h, uint32_t spin_limit, void *stream) {

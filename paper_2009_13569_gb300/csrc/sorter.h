@@ -149,6 +149,8 @@ struct Sorter {
     double stat_bytes[KK_COUNT] = {};
     // per-level algorithmic element count (for the byte model of a launch)
     uint64_t level_elems = 0;
+    // waves and peak ring occupancy of the last host-driven run
+    uint64_t last_waves = 0, last_max_pending = 0;
 
     void tbegin(int kind, double bytes, cudaStream_t st);
     void tend(cudaStream_t st);

@@ -68,6 +68,8 @@ def load():
         "ipsgpu_kernel_stats": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double), i32]),
         "ipsgpu_kernel_name": (ctypes.c_char_p, [i32]),
+        "ipsgpu_wave_stats": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                    ctypes.POINTER(u64)]),
         "ipsgpu_debug_bounded_wait": (i32, [vp, u32, vp]),
         "ipsgpu_debug_check_guards": (i32, [vp, ctypes.POINTER(u64)]),
         "ipsgpu_partition_level_noalloc": (i32, [i32, vp, u64, vp, u32, i32, vp, vp]),
@@ -111,6 +113,7 @@ def exported_symbols():
         "ipsgpu_sort_host",
         "ipsgpu_partition_level", "ipsgpu_radix_level", "ipsgpu_classify", "ipsgpu_status",
         "ipsgpu_strerror", "ipsgpu_set_timing", "ipsgpu_kernel_stats", "ipsgpu_kernel_name",
+        "ipsgpu_wave_stats",
         "ipsgpu_debug_bounded_wait", "ipsgpu_debug_check_guards",
         "ipsgpu_partition_level_noalloc", "ipsgpu_sort_segmented",
         "ipsgpu_sort_batch", "ipsgpu_segmented_graph_create", "ipsgpu_graph_launch",
@@ -253,6 +256,14 @@ class Sorter:
             raise IpsgpuError(-nk, "ipsgpu_kernel_stats")
         return {load().ipsgpu_kernel_name(i).decode(): (int(la[i]), float(ms[i]), float(by[i]))
                 for i in range(nk)}
+
+    def wave_stats(self):
+        """(waves, largest ring occupancy, ring capacity) of the last run made
+        with timing on (ipsgpu_wave_stats)."""
+        w, m, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().ipsgpu_wave_stats(self._h, ctypes.byref(w), ctypes.byref(m),
+                                        ctypes.byref(c)), "ipsgpu_wave_stats")
+        return int(w.value), int(m.value), int(c.value)
 
     def check_guards(self):
         """Synchronize and check the guard zones around every device buffer

@@ -82,3 +82,25 @@ def test_wide_record_configuration_2e28(dtype, dist):
     if records:
         assert record_sig(d, dtype) == rsig
         assert records_intact_dev(d, inp, dtype)
+
+
+def test_2e34_sort_and_its_task_metadata():
+    # the serving configuration's huge request sorted alone: 2^34 uint64 keys
+    # (128 GiB) in place, with the recursion's statistics: its pending
+    # segments (the task metadata of Sec. 3.2 that App. B's strictly
+    # in-place variant would keep in the array instead) stay far below the
+    # sorter's fixed ring, whatever the size
+    n = 1 << 34
+    d = torch.empty((n,), dtype=torch.int64, device=DEV)
+    inputs.generate_into(d, "uniform", "u64", seed=0x2E34)
+    before = multiset_sig(d)
+    with ipsgpu.Sorter("u64") as s:
+        s.set_timing(True)
+        s.sort(d.data_ptr(), n, stream())
+        assert s.status(stream()) == ipsgpu.OK
+        waves, pending, cap = s.wave_stats()
+        s.kernel_stats()
+    print("2^34 uint64: %d waves, at most %d segments pending (ring of %d)" % (waves, pending, cap))
+    assert 3 <= waves and 0 < pending <= 1 << 17 and cap == 1 << 20
+    assert keys_nondecreasing(d, "u64")
+    assert multiset_sig(d) == before
