@@ -22,6 +22,7 @@ constexpr int kBaseInsertion = 24;       // sub-buckets up to this size: ranked 
 constexpr int kBaseStack = 256;          // pending large ranges: >= 188416 B / 4 B / 513
 constexpr int kBaseSmall = 512;          // ranges up to this size are finished by one warp
 constexpr int kBaseSmallStack = 2048;    // pending small ranges: >= 188416 B / 4 B / 25
+constexpr uint32_t kBaseSpin = 1u << 22;  // polls of a bounded wait on a segment's bulk copy
 
 
 // Radix-key word w < T::kKeyWords of an element, most significant first
@@ -193,13 +194,15 @@ __device__ __forceinline__ void sort_upto4(typename T::E *r, uint32_t c) {
         if ((uint32_t)i < c) r[i] = x[i];
 }
 
-// Sorts each listed segment (segs[2i] = device byte address, segs[2i+1] = n,
-// n <= smax) in place; the number of segments is *nsegs_dev if given, else
-// nsegs_host.  One CTA per segment at a time; its bytes were prefetched into
-// L2 while the CTA sorted its previous segment.
+// Sorts each listed segment (segs[4i] = device byte address, segs[4i+1] = n
+// <= smax, segs[4i+2..4i+3] = bounds lo <= hi of every element's radix key
+// T::rkey, or lo > hi when not known) in place; the number of segments is
+// *nsegs_dev if given, else nsegs_host.  One CTA per segment at a time; its
+// bytes were prefetched into L2 while the CTA sorted its previous segment.
 //
-// The segment is staged into shared memory through registers, taking the
-// min/max of its radix key on the way.  A pass over a range [a0, a0+len)
+// The segment is staged into shared memory through registers; its radix
+// key range is the given bounds (a bucket's splitters, or its radix digit)
+// or, when none are known, the min/max taken on the way.  A pass over a range [a0, a0+len)
 // then counts an MSD radix digit of (key - min) (up to 2^DBITS digits,
 // packed 16-bit counters), turns the counts into cursors, and scatters the
 // range by digit from its global copy (which equals the shared one) into
@@ -250,22 +253,29 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
     constexpr int NB = T::D <= 8 ? 8 : (T::D <= 16 ? 4 : (T::D <= 32 ? 2 : 1));  // in flight per thread
     constexpr int U = T::D % 16 == 0 ? 16 : (T::D % 8 == 0 ? 8 : 4);  // copy-out unit
     extern __shared__ __align__(16) unsigned char smem[];
-    // layout: buf | stk | sstk | cur (ND/2 words, two 16-bit counters each)
-    // | wtmp.  Ranges are < 2^16 elements, so 16-bit counters and cursors
-    // suffice.
+    // layout: buf (BUF + 16 bytes: a segment is placed at its global
+    // address modulo 16, so that a bulk copy moves its aligned interior) |
+    // stk | sstk | cur (ND/2 words, two 16-bit counters each) | wtmp.
+    // Ranges are < 2^16 elements, so 16-bit counters and cursors suffice.
     // Digits 2w and 2w + 1 share word w.
-    E *buf = reinterpret_cast<E *>(smem);
-    uint32_t *stk = reinterpret_cast<uint32_t *>(smem + S::BUF);  // (a0 << 16) | len
+    uint32_t *stk = reinterpret_cast<uint32_t *>(smem + S::BUF + 16);  // (a0 << 16) | len
     uint32_t *sstk = stk + kBaseStack;                            // small ranges
     uint32_t *cur = sstk + S::SSTK;                               // ND / 2
     uint32_t *wtmp = cur + ND / 2;                                         // 34
     __shared__ unsigned long long red[2][32];
     __shared__ uint32_t sp, ssp, sh_top, sh_nmid;
+    __shared__ __align__(8) uint64_t sh_bar;  // completion of a segment's bulk copy
+    uint32_t parity = 0;
     // sorting networks and the mid-size list for keys up to 32 bytes
     constexpr bool kNetwork = T::D <= 32;
     constexpr uint32_t kNoRange = 0xFFFFFFFFu;  // no range has a0 = len = 65535
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = kBaseThreads / 32;
+    if (tid == 0) {
+        mbar_init(&sh_bar, 1);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    __syncthreads();
 
     // CTA-wide min and max of per-thread values (all threads call it)
     auto minmax = [&](unsigned long long lmin, unsigned long long lmax, uint64_t &gmn,
@@ -294,12 +304,14 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
 
     const uint32_t nsegs = nsegs_dev ? *nsegs_dev : nsegs_host;
     for (uint32_t si = blockIdx.x; si < nsegs; si += gridDim.x) {
-        const uint64_t addr = segs[2 * si], n = segs[2 * si + 1];
+        const uint64_t addr = segs[4 * si], n = segs[4 * si + 1];
+        const uint64_t rlo = segs[4 * si + 2], rhi = segs[4 * si + 3];
         if (n <= n_lo || n > n_hi) continue;  // the other shape's segment
         E *g = reinterpret_cast<E *>(addr);
+        E *buf = reinterpret_cast<E *>(smem + (addr & 15));
         if (tid == 0 && si + gridDim.x < nsegs) {
             // the CTA's next segment streams into L2 while this one is sorted
-            const uint64_t na = segs[2 * (si + gridDim.x)], nn = segs[2 * (si + gridDim.x) + 1];
+            const uint64_t na = segs[4 * (si + gridDim.x)], nn = segs[4 * (si + gridDim.x) + 1];
             const uint64_t lo = (na + 15) & ~15ull, hi = (na + nn * T::D) & ~15ull;
             if (nn > n_lo && nn <= n_hi && hi > lo) prefetch_l2(lo, (uint32_t)(hi - lo));
         }
@@ -326,8 +338,21 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
         }
         // stage the segment into shared memory through registers, with the
         // min / max of the high radix-key word
-        uint64_t seg_mn, seg_mx;
-        {
+        uint64_t seg_mn = rlo, seg_mx = rhi;
+        if (rlo <= rhi) {
+            // the key range is known: the segment arrives by one bulk copy
+            // (its unaligned ends by 4-byte copies), bounded wait
+            tile_load(reinterpret_cast<unsigned char *>(buf),
+                      reinterpret_cast<const unsigned char *>(g), (uint32_t)n * T::D, &sh_bar);
+            const bool landed = mbar_wait_bounded(&sh_bar, parity, kBaseSpin);
+            parity ^= 1;
+            cp_async_wait_all();
+            if (__syncthreads_or(!landed)) {
+                if (tid == 0) set_status(status, IPSGPU_E_TIMEOUT);
+                mbar_wait_bounded(&sh_bar, parity ^ 1, kBaseSpin);
+                return;
+            }
+        } else {
             unsigned long long lmin = ~0ull, lmax = 0;
             for (uint32_t i0 = 0; i0 < n; i0 += NB * kBaseThreads) {
                 E x[NB];
@@ -577,7 +602,7 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
 
 template <class S>
 inline size_t base_smem_bytes() {
-    return S::BUF + sizeof(uint32_t) * (kBaseStack + S::SSTK) +
+    return S::BUF + 16 + sizeof(uint32_t) * (kBaseStack + S::SSTK) +
            sizeof(uint32_t) * ((1 << S::MAXB) / 2 + 34) + 16;
 }
 

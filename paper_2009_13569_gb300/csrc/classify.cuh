@@ -144,19 +144,6 @@ __device__ __forceinline__ Key192 key_hi_of<TQuartet>(uint64_t rk) {
     k.b = k.c = ~0ull;
     return k;
 }
-template <class T>
-__device__ __forceinline__ uint64_t rk_of_key(const typename T::K &k) {
-    return (uint64_t)k;
-}
-template <>
-__device__ __forceinline__ uint64_t rk_of_key<TRec100>(const Key80 &k) {
-    return k.hi;
-}
-template <>
-__device__ __forceinline__ uint64_t rk_of_key<TQuartet>(const Key192 &k) {
-    return k.a;
-}
-
 // Cell maps of the start-node table.  A key's leading word rk picks a cell:
 //   linear:    y = rk >> shift, cell = clamp(y - bc, 0, kCells - 1), with bc
 //              = (smallest splitter's rk) >> shift and shift chosen so the

@@ -185,6 +185,25 @@ struct TQuartet {
     }
 };
 
+// The leading 64-bit word of a key (T::rkey of an element with that key),
+// and the largest value it takes.
+template <class T>
+__device__ __forceinline__ uint64_t rk_of_key(const typename T::K &k) {
+    return (uint64_t)k;
+}
+template <>
+__device__ __forceinline__ uint64_t rk_of_key<TRec100>(const Key80 &k) {
+    return k.hi;
+}
+template <>
+__device__ __forceinline__ uint64_t rk_of_key<TQuartet>(const Key192 &k) {
+    return k.a;
+}
+template <class T>
+__host__ __device__ constexpr uint64_t rk_max() {
+    return sizeof(typename T::K) == 4 ? 0xFFFFFFFFull : ~0ull;
+}
+
 // The first element of a block held by a warp, 16 bytes per lane (lane 0's
 // bytes, and lane 1's where the key reaches past them), broadcast: every
 // lane calls it and gets the element.
@@ -228,6 +247,7 @@ struct SegDesc {
     uint32_t cnt0;       // first per-class count entry of the segment's stripes
     uint32_t part0;      // balanced waves: classification part of its first stripe
     uint64_t gblk0;      // balanced waves: first block in the wave's block order
+    uint64_t rlo, rhi;   // every element's T::rkey lies in [rlo, rhi] (rlo > rhi: not known)
 };
 
 // Per-stripe plan and outputs.

@@ -32,8 +32,19 @@ constexpr uint32_t kMinStripeElems = 1u << 15;
 
 struct GList {
     uint64_t addr, n;  // device byte address of the first element, elements
+    uint64_t rlo, rhi; // bounds of the elements' leading key word (rlo > rhi: not known)
     uint32_t shift;    // radix: next digit is key bits [shift, shift + kbits)
     uint32_t pad;
+};
+
+// Bounds of every T::rkey in a child of a partitioned segment, from the
+// parent's bounds and the class's splitters (class i of the tree holds keys
+// s_{i-1} < key <= s_i; with equality buckets class 2i holds s_{i-1} < key <
+// s_i and class 2K - 1 keys above every splitter) or from its radix digit.
+// Loose bounds stay correct (every key lies inside), an unknown parent
+// bound on an edge class becomes the type's whole range.
+struct RBounds {
+    uint64_t lo, hi;
 };
 
 // What one run sorts; written by k_g_job before the run.
@@ -105,12 +116,15 @@ __device__ inline uint64_t g_al256(uint64_t x) { return (x + 255) & ~(uint64_t)2
 // so once the appending kernel has finished the count never exceeds the
 // capacity and every entry below it is written; the overflow is reported as
 // E_NOMEM.
-__device__ inline void g_push_base(const GraphArgs &g, uint64_t addr, uint64_t n) {
+__device__ inline void g_push_base(const GraphArgs &g, uint64_t addr, uint64_t n, uint64_t rlo,
+                                   uint64_t rhi) {
     GState *s = g.state;
     const uint32_t q = atomicAdd(&s->base_count, 1u);
     if (q < g.base_cap) {
-        g.base_list[2 * q] = addr;
-        g.base_list[2 * q + 1] = n;
+        g.base_list[4 * q] = addr;
+        g.base_list[4 * q + 1] = n;
+        g.base_list[4 * q + 2] = rlo;
+        g.base_list[4 * q + 3] = rhi;
         atomicAdd(reinterpret_cast<unsigned long long *>(&s->base_elems), (unsigned long long)n);
     } else {
         atomicSub(&s->base_count, 1u);
@@ -212,15 +226,21 @@ static __global__ void __launch_bounds__(256) k_g_feed(GraphArgs g) {
         // range is known, at the highest bit where the smallest and the
         // largest key differ (the bits above are common to every key)
         uint32_t shift = g.keybits > g.kbits ? g.keybits - g.kbits : 0u;
+        // an input array's key range is not known (the base case measures
+        // it), except for a radix sort's single array, whose detection pass
+        // took the smallest and largest key
+        uint64_t rlo = ~0ull, rhi = 0;
         if (j.radix_mm && g.algo == 1) {
             const unsigned long long x = j.radix_mm[0] ^ j.radix_mm[1];
             const uint32_t hb = x ? 63u - (uint32_t)__clzll((long long)x) : 0u;
             shift = hb + 1 > g.kbits ? hb + 1 - g.kbits : 0u;
+            rlo = j.radix_mm[0];
+            rhi = j.radix_mm[1];
         }
         if (n <= g.smax)
-            g_push_base(g, addr, n);
+            g_push_base(g, addr, n, rlo, rhi);
         else
-            g_push_ring(g, floor, GList{addr, n, shift, 0u});
+            g_push_ring(g, floor, GList{addr, n, rlo, rhi, shift, 0u});
     }
 }
 
@@ -454,6 +474,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_g_plan(GraphArgs g) {
             d.eq_given = 0;
             d.part0 = it.part0;
             d.gblk0 = run[8];
+            d.rlo = e.rlo;
+            d.rhi = e.rhi;
             const_cast<SegDesc *>(g.lv.seg)[i] = d;
             my_elems += e.n;
             run[0] += it.p;
@@ -541,6 +563,40 @@ __global__ void __launch_bounds__(256) k_g_fill_stripes(GraphArgs g) {
     }
 }
 
+template <class T>
+__device__ inline RBounds g_child_bounds(const GraphArgs &g, const SegDesc &sd,
+                                         const SegState &st, uint32_t j) {
+    const bool known = sd.rlo <= sd.rhi;
+    const uint64_t plo = known ? sd.rlo : 0ull, phi = known ? sd.rhi : rk_max<T>();
+    if (sd.mode == 2) {  // radix digit j at key bits [shift, shift + bits)
+        const uint32_t top = sd.radix_shift + sd.radix_bits;
+        const uint64_t above = top >= 64 ? 0ull : ~0ull << top;  // bits common to the parent
+        if (!known && above != 0 && top < (uint32_t)g.keybits) return RBounds{~0ull, 0ull};
+        const uint64_t lo = (plo & above) | ((uint64_t)j << sd.radix_shift);
+        const uint64_t below = sd.radix_shift >= 64 ? ~0ull : ((1ull << sd.radix_shift) - 1);
+        return RBounds{lo, lo | below};
+    }
+    const typename T::K *spl =
+        reinterpret_cast<const typename T::K *>(g.lv.keys + sd.key_off) + sd.C;
+    const uint32_t K = st.K;
+    uint32_t i = j, below_all = 0;
+    if (st.eq) {
+        i = j >> 1;  // class 2i: s_{i-1} < key < s_i; class 2K - 1: above every splitter
+        below_all = j == 2 * K - 1;
+    } else {
+        below_all = 0;
+    }
+    uint64_t lo, hi;
+    if (below_all) {
+        lo = rk_of_key<T>(spl[K - 1]);
+        hi = phi;
+    } else {
+        lo = i == 0 ? plo : rk_of_key<T>(spl[i - 1]);
+        hi = i >= K - 1 ? phi : rk_of_key<T>(spl[i]);
+    }
+    return RBounds{lo, hi};
+}
+
 // Children of every (segment, class) of the wave.
 template <class T>
 __global__ void __launch_bounds__(256) k_g_emit(GraphArgs g) {
@@ -571,10 +627,11 @@ __global__ void __launch_bounds__(256) k_g_emit(GraphArgs g) {
             if (sd.radix_shift == 0) continue;  // every key bit used: equal keys
             shift = sd.radix_shift >= g.kbits ? sd.radix_shift - g.kbits : 0u;
         }
+        const RBounds rb = g_child_bounds<T>(g, sd, st, j);
         if (n <= g.smax)
-            g_push_base(g, sd.addr + b0 * T::D, n);
+            g_push_base(g, sd.addr + b0 * T::D, n, rb.lo, rb.hi);
         else
-            g_push_ring(g, floor, GList{sd.addr + b0 * T::D, n, shift, 0u});
+            g_push_ring(g, floor, GList{sd.addr + b0 * T::D, n, rb.lo, rb.hi, shift, 0u});
     }
 }
 

@@ -128,7 +128,7 @@ Layout layout(const Sorter &s, int key_bytes) {
     L.arena = s.arena_bytes;
     L.moves = (uint64_t)s.move_cap * sizeof(Move);
     L.cta = (uint64_t)s.cta_cap * sizeof(uint32_t);
-    L.base = (uint64_t)s.base_cap * 2 * sizeof(uint64_t);
+    L.base = (uint64_t)s.base_cap * 4 * sizeof(uint64_t);
     L.ring = (uint64_t)s.ring_cap * sizeof(GList);
     L.misc = 1024;
     return L;
