@@ -200,9 +200,9 @@ __device__ __forceinline__ void sort_upto4(typename T::E *r, uint32_t c) {
 // *nsegs_dev if given, else nsegs_host.  One CTA per segment at a time; its
 // bytes were prefetched into L2 while the CTA sorted its previous segment.
 //
-// The segment is staged into shared memory through registers; its radix
-// key range is the given bounds (a bucket's splitters, or its radix digit)
-// or, when none are known, the min/max taken on the way.  A pass over a range [a0, a0+len)
+// The segment is staged into shared memory by one bulk copy; its radix key
+// range is the given bounds (a bucket's splitters, or its radix digit) or,
+// when none are known, the min/max of the staged keys.  A pass over a range [a0, a0+len)
 // then counts an MSD radix digit of (key - min) (up to 2^DBITS digits,
 // packed 16-bit counters), turns the counts into cursors, and scatters the
 // range by digit from its global copy (which equals the shared one) into
@@ -338,41 +338,28 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
         }
         // stage the segment into shared memory through registers, with the
         // min / max of the high radix-key word
+        // the segment arrives by one bulk copy (its unaligned ends by 4-byte
+        // copies), bounded wait; its key range is the given bounds, or the
+        // min / max of its leading key word when none are known
         uint64_t seg_mn = rlo, seg_mx = rhi;
-        if (rlo <= rhi) {
-            // the key range is known: the segment arrives by one bulk copy
-            // (its unaligned ends by 4-byte copies), bounded wait
-            tile_load(reinterpret_cast<unsigned char *>(buf),
-                      reinterpret_cast<const unsigned char *>(g), (uint32_t)n * T::D, &sh_bar);
-            const bool landed = mbar_wait_bounded(&sh_bar, parity, kBaseSpin);
-            parity ^= 1;
-            cp_async_wait_all();
-            if (__syncthreads_or(!landed)) {
-                if (tid == 0) set_status(status, IPSGPU_E_TIMEOUT);
-                mbar_wait_bounded(&sh_bar, parity ^ 1, kBaseSpin);
-                return;
-            }
-        } else {
+        tile_load(reinterpret_cast<unsigned char *>(buf),
+                  reinterpret_cast<const unsigned char *>(g), (uint32_t)n * T::D, &sh_bar);
+        const bool landed = mbar_wait_bounded(&sh_bar, parity, kBaseSpin);
+        parity ^= 1;
+        cp_async_wait_all();
+        if (__syncthreads_or(!landed)) {
+            if (tid == 0) set_status(status, IPSGPU_E_TIMEOUT);
+            mbar_wait_bounded(&sh_bar, parity ^ 1, kBaseSpin);
+            return;
+        }
+        if (rlo > rhi) {
             unsigned long long lmin = ~0ull, lmax = 0;
-            for (uint32_t i0 = 0; i0 < n; i0 += NB * kBaseThreads) {
-                E x[NB];
-#pragma unroll
-                for (int q = 0; q < NB; q++) {
-                    const uint32_t i = i0 + q * kBaseThreads + tid;
-                    if (i < n) x[q] = g[i];
-                }
-#pragma unroll
-                for (int q = 0; q < NB; q++) {
-                    const uint32_t i = i0 + q * kBaseThreads + tid;
-                    if (i < n) {
-                        const unsigned long long v = T::rkey(x[q]);
-                        lmin = min(lmin, v);
-                        lmax = max(lmax, v);
-                        buf[i] = x[q];
-                    }
-                }
+            for (uint32_t i = tid; i < n; i += kBaseThreads) {
+                const unsigned long long v = T::rkey(buf[i]);
+                lmin = min(lmin, v);
+                lmax = max(lmax, v);
             }
-            minmax(lmin, lmax, seg_mn, seg_mx);  // (its barrier also publishes buf)
+            minmax(lmin, lmax, seg_mn, seg_mx);
         }
         if (tid == 0) {
             sp = 1;
