@@ -4,9 +4,10 @@
 // One CTA owns one stripe (a run of whole blocks of its segment).  The stripe
 // is read tile by tile; the next tile streams into shared memory with
 // cp.async while the current one is processed:
-//   [B] every thread classifies its elements and takes a rank inside its
-//       class with a shared-memory atomic (one per warp when all its lanes
-//       share a class);
+//   [B] every thread classifies its elements and takes its position g in
+//       its class's buffer block with a shared-memory atomic on a counter
+//       that starts the tile at the block's fill (one atomic per warp when
+//       all its lanes share a class);
 //   [C] per class, the buffer blocks that fill up in this tile get slots at
 //       the front of the stripe (an atomic on the stripe's block counter:
 //       the order of full blocks in a stripe is free);
@@ -583,17 +584,18 @@ __global__ void __launch_bounds__(ClsCfg<T>::NT, 1) k_classify(LevelArgs a) {
             tile_load(reinterpret_cast<unsigned char *>(stage),
                       reinterpret_cast<const unsigned char *>(segbase + t0 + TILE),
                       (uint32_t)min((uint64_t)TILE, e1 - t0 - TILE) * T::D, &sh_bar);
-        // [C] per class: blocks completed in this tile and their slots at the
-        // front of the stripe; fl = fill before the tile | elements that go
-        // to completed blocks (nf b) << 16, sl = first slot; the class's
-        // buffer block, if completed, is a flush job.  B <= 256 <= NT:
-        // thread j takes class j; slots and job entries are handed out one
-        // atomic per warp
+        // [C] per class (cnt = fill before the tile + the tile's elements):
+        // blocks completed in this tile and their slots at the front of the
+        // stripe; fl = elements that go to completed blocks (nf b), sl =
+        // first slot; the class's buffer block, if completed, is a flush
+        // job; cnt restarts at the new fill.  B <= 256 <= NT: thread j takes
+        // class j; slots and job entries are handed out one atomic per warp
         if ((uint32_t)(tid & ~31) < B) {
             const uint32_t j = tid;
             const bool act = j < B;
-            const uint32_t cc = act ? cnt[j] : 0u, ff = act ? fill[j] : 0u;
-            const uint32_t nf = (ff + cc) >> lb;
+            const uint32_t ct = act ? cnt[j] : 0u, ff = act ? fill[j] : 0u;
+            const uint32_t cc = ct - ff;
+            const uint32_t nf = ct >> lb;
             uint32_t x = nf;  // inclusive warp scan of nf
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -611,31 +613,33 @@ __global__ void __launch_bounds__(ClsCfg<T>::NT, 1) k_classify(LevelArgs a) {
             const uint32_t slot = s0 + x - nf;
             if (nf) jobs[q0 + __popc(jb & ((1u << lane) - 1))] = make_uint2(j, slot);
             if (act) {
-                fl[j] = ff | ((nf << lb) << 16);
+                fl[j] = nf << lb;
                 sl[j] = slot;
-                fill[j] = (ff + cc) & (b - 1);
+                fill[j] = ct & (b - 1);
                 tot[j] += cc;
-                cnt[j] = 0;
+                cnt[j] = ct & (b - 1);
             }
         }
         __syncthreads();
-        // [D] element with in-class position g = fill + rank: g < b extends
-        // (and may complete) the class's buffer block; the later blocks a
-        // heavy class completes in this tile go straight to their slots; the
-        // rest waits until the buffer block has been flushed
+        // [D] element with in-class position g: g < b extends (and may
+        // complete) the class's buffer block; the later blocks a heavy class
+        // completes in this tile go straight to their slots; the rest waits
+        // until the buffer block has been flushed
         uint32_t gq[EPT];
 #pragma unroll
         for (int e = 0; e < EPT; e++) {
             gq[e] = 0xFFFFFFFFu;
             if (c[e] != 0xFFFFFFFFu) {
-                const uint32_t m = fl[c[e]];
-                const uint32_t g = (m & 0xFFFFu) + r[e], Lq = m >> 16;
-                if (g < b)
+                const uint32_t g = r[e];
+                if (g < b) {
                     reinterpret_cast<E *>(bufr + c[e] * pitch)[g] = v[e];
-                else if (g < Lq)
-                    out[((uint64_t)sl[c[e]] << lb) + g] = v[e];
-                else
-                    gq[e] = g - Lq;
+                } else {
+                    const uint32_t Lq = fl[c[e]];
+                    if (g < Lq)
+                        out[((uint64_t)sl[c[e]] << lb) + g] = v[e];
+                    else
+                        gq[e] = g - Lq;
+                }
             }
         }
         __syncthreads();
