@@ -146,8 +146,8 @@ int ipsgpu_sorter_destroy(ipsgpu_sorter *s);
  * segment of a wave its cleanup staging, per stripe its leftover buffer
  * blocks) plus tables of fixed capacity for one wave (2^16 segments and
  * stripes, 2^20 (segment, class) pairs, 2^21 base-case entries, 2^22 fix-up
- * moves, a ring of 2^20 waiting segments): 178 MiB for U32, 186 MiB for
- * 8- and 16-byte elements, 202 MiB for REC100, 218 MiB for QUARTET.  The
+ * moves, a ring of 2^20 waiting segments): 227 MiB for U32, 235 MiB for
+ * 8- and 16-byte elements, 251 MiB for REC100, 267 MiB for QUARTET.  The
  * sorter allocates under 64 KiB more (fixed-size state, guard zones).
  * 0 if the parameters are invalid for the dtype. */
 uint64_t ipsgpu_scratch_bytes(const ipsgpu_params *params, int dtype);

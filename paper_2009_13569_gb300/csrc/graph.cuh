@@ -89,6 +89,7 @@ struct GraphArgs {
     uint32_t pad2;
     uint32_t ring_cap, base_cap, feed_cap, seg_cap, stripe_cap, cta_cap, cls_cap, cnt_cap;
     uint32_t smax, k, b, nsm, kbits, keybits, elem_bytes, elem_align;
+    uint32_t perm_ctas;      // permutation CTAs resident at once (the wave's grid)
     uint64_t arena_bytes, sarr_bytes, keys_bytes;
     int algo;  // 0 samplesort, 1 radix
     int pad;
@@ -260,8 +261,19 @@ struct GLayout {
     bool balanced;
     uint64_t Q;             // balanced: blocks per part
     uint64_t stripe_elems;  // otherwise
-    uint64_t bpc;           // blocks per permutation CTA
+    uint64_t R;             // virtual permutation CTAs of the window (kPermRounds rounds)
+    uint64_t tb;            // blocks waiting in the window
 };
+
+// The permutation's virtual CTAs are kPermRounds times the resident ones:
+// segments then get kPermRounds times their share of the resident workers
+// and run about R / kPermRounds of them at a time.  Measured on 2^30 uint64
+// keys (256 segments of 2^22 in the second wave): the wave takes 6.25 ms
+// with every segment running at once (3 CTAs each), 4.5 ms with 32 at a
+// time; a single segment gets every resident CTA.  Fewer segments at once
+// keep fewer bucket fronts open (each bucket's write and read pointers walk
+// its region block by block), so DRAM pages and translations are reused.
+constexpr uint64_t kPermRounds = 8;
 
 template <class T>
 __device__ inline GPlanItem g_item(const GraphArgs &g, uint64_t n, uint64_t gblk0,
@@ -287,7 +299,13 @@ __device__ inline GPlanItem g_item(const GraphArgs &g, uint64_t n, uint64_t gblk
         if (p > nb) p = nb;
         if (p < 1) p = 1;
     }
-    uint64_t nc = (nb + ly.bpc - 1) / ly.bpc;
+    // the permutation's virtual CTAs: the window's R shared in proportion
+    // to the blocks (a segment gets the CTAs whose share of the block order
+    // starts inside it), at least one, at most one per 32 blocks and at most
+    // the resident CTAs
+    uint64_t nc = (gblk0 + nb) * ly.R / ly.tb - gblk0 * ly.R / ly.tb;
+    if (nc > (nb + 31) / 32) nc = (nb + 31) / 32;
+    if (nc > g.perm_ctas) nc = g.perm_ctas;
     if (nc > g.cta_cap) nc = g.cta_cap;
     if (nc < 1) nc = 1;
     it.p = (uint32_t)p;
@@ -348,8 +366,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_g_plan(GraphArgs g) {
     ly.stripe_elems = te / (2 * (uint64_t)g.nsm);
     if (ly.stripe_elems < kMinStripeElems) ly.stripe_elems = kMinStripeElems;
     ly.stripe_elems = (ly.stripe_elems + g.b - 1) / g.b * g.b;
-    ly.bpc = tb / (8 * (uint64_t)g.nsm);
-    if (ly.bpc < 32) ly.bpc = 32;
+    ly.R = (g.perm_ctas > 0 ? g.perm_ctas : 1) * kPermRounds;
+    ly.tb = tb > 0 ? tb : 1;
     const uint32_t per = (nin + kPlanThreads - 1) / kPlanThreads;
     const uint32_t r0 = min(nin, tid * per), r1 = min(nin, r0 + per);
     const unsigned long long cap[NV] = {g.stripe_cap,  g.cta_cap,    g.cls_cap,

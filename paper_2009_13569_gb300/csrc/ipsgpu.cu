@@ -270,7 +270,9 @@ void level_sizes(const Sorter &s, uint64_t tot, uint64_t &stripe_elems, uint64_t
     const uint64_t blocks = (tot + s.b - 1) / s.b;
     stripe_elems = std::max<uint64_t>(kMinStripe, tot / (2 * (uint64_t)s.nsm));
     stripe_elems = align_up(stripe_elems, s.b);
-    blocks_per_cta = std::max<uint64_t>(32, blocks / (8 * (uint64_t)s.nsm));
+    // one virtual permutation CTA per resident CTA
+    const uint64_t pc = std::max<uint64_t>(1, s.perm_ctas);
+    blocks_per_cta = std::max<uint64_t>(32, (blocks + pc - 1) / pc);
 }
 
 int read_status(Sorter &s, cudaStream_t st, int *code) {
@@ -310,6 +312,7 @@ GraphArgs graph_args(Sorter &s) {
     ga.k = s.k;
     ga.b = s.b;
     ga.nsm = (uint32_t)s.nsm;
+    ga.perm_ctas = s.perm_ctas;
     ga.kbits = (uint32_t)__builtin_ctz(s.k);
     ga.keybits = s.ops->D == 4 ? 32 : 64;
     ga.elem_bytes = (uint32_t)s.ops->D;

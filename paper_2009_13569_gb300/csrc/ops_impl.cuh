@@ -33,7 +33,10 @@ struct OpsImpl {
         return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     optin - (int)fa.sharedSizeBytes);
     }
-    static cudaError_t init(Sorter *) {
+    // Kernel attributes; for a sorter (nsm and b set) also the number of
+    // permutation CTAs that are resident at once, which sizes the level's
+    // virtual CTAs.
+    static cudaError_t init(Sorter *s) {
         int dev = 0, optin = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess)
@@ -42,6 +45,17 @@ struct OpsImpl {
         if (e == cudaSuccess) e = raise_smem_limit(k_sample_tree<T>, optin);
         if (e == cudaSuccess) e = raise_smem_limit(k_base<T, BaseLarge>, optin);
         if (e == cudaSuccess) e = raise_smem_limit(k_base<T, BaseSmall>, optin);
+        if (e == cudaSuccess && s && s->nsm > 0 && s->b > 0) {
+            int occ = 0;
+            const int nv = block_units(s->b * T::D);
+            if (nv == 1)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_permute<T, 1>, kPermuteThreads, 0);
+            else if (nv == 2)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_permute<T, 2>, kPermuteThreads, 0);
+            else
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_permute<T, 4>, kPermuteThreads, 0);
+            s->perm_ctas = (uint32_t)s->nsm * (uint32_t)(occ > 0 ? occ : 1);
+        }
         return e;
     }
 
@@ -164,7 +178,7 @@ struct OpsImpl {
         LevelGrids g;
         g.seg = (uint32_t)s->nsm * 4;
         g.stripe = ga.nparts;  // one classification part per CTA
-        g.cta = (uint32_t)s->nsm * 8;
+        g.cta = s->perm_ctas;
         g.cls = big;
         cudaError_t e;
         if ((e = level(s, a, g, st)) != cudaSuccess) return e;

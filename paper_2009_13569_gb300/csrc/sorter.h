@@ -80,6 +80,7 @@ struct Sorter {
     int dtype = 0;
     int device = 0;
     int nsm = 0;
+    uint32_t perm_ctas = 0;  // k_permute CTAs resident at once on the device (set by ops->init)
     const TypeOps *ops = nullptr;
     // parameters (defaults resolved)
     uint32_t k = 256;
