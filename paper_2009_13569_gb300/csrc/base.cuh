@@ -416,18 +416,30 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
             while (want < (uint32_t)DBITS && ((1u << kPerDigitLog) << want) < len) want++;
             const uint32_t dbits =
                 (nbits <= (uint32_t)S::MAXB && nbits <= want + 1) ? nbits : min(nbits, want);
-            const uint32_t shift = nbits - dbits;
             const uint32_t nd = 1u << dbits;
             const uint32_t nw = (nd + 1) >> 1;  // counter words in use
-            // with shift 0 a digit is the whole key word; in the last word
-            // (the words before it are constant) each sub-bucket then holds
-            // one key, so it is final
-            const bool exact = shift == 0 && mode == T::kKeyWords - 1;
+            // A digit is the whole offset v - mn when the range has at most
+            // 2^dbits values; otherwise the offset scaled to [0, nd): its top
+            // 32 bits (below bit nbits) times m / 2^32, m = nd 2^32 / (top
+            // of the range + 1) -- nondecreasing in v, below nd, and spread
+            // over all nd digits (a power-of-two shift would leave up to
+            // half of them empty and crowd the rest)
+            const bool whole = nbits == dbits;
+            const uint32_t s2 = nbits > 32 ? nbits - 32 : 0u;
+            const uint32_t m =
+                whole ? 0u
+                      : (uint32_t)(((uint64_t)nd << 32) / ((uint64_t)(uint32_t)(rng >> s2) + 1));
+            auto digit = [&](uint64_t v) -> uint32_t {
+                return whole ? (uint32_t)(v - mn) : __umulhi((uint32_t)((v - mn) >> s2), m);
+            };
+            // with whole offsets in the last word (the words before it are
+            // constant) each sub-bucket holds one key, so it is final
+            const bool exact = whole && mode == T::kKeyWords - 1;
             for (uint32_t w = tid; w < nw; w += kBaseThreads) cur[w] = 0;
             __syncthreads();
             for (uint32_t i = tid; i < len; i += kBaseThreads) {
                 const uint64_t v = rk_word<T>(buf[a0 + i], mode);
-                const uint32_t d = (uint32_t)((v - mn) >> shift);
+                const uint32_t d = digit(v);
                 atomicAdd(&cur[word(d)], 1u << (16 * (d & 1)));
             }
             __syncthreads();
@@ -481,7 +493,7 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
                     const uint32_t i = i0 + q * kBaseThreads + tid;
                     if (i < len) {
                         const uint64_t v = rk_word<T>(x[q], mode);
-                        const uint32_t d = (uint32_t)((v - mn) >> shift);
+                        const uint32_t d = digit(v);
                         const uint32_t h = 16 * (d & 1);
                         const uint32_t p = (atomicAdd(&cur[word(d)], 1u << h) >> h) & 0xFFFFu;
                         buf[a0 + p] = x[q];
