@@ -73,6 +73,10 @@ def _args():
     p.add_argument("--batched-only", action="store_true",
                    help="only the batched form's graph launches (both workloads), one JSON "
                         "line: the command of the batched launch-list profile")
+    p.add_argument("--base-only", action="store_true",
+                   help="only the base case: one ipsgpu_sort_batch of 8,192 arrays of 16,384 "
+                        "uint64 Uniform keys (1 GiB; every array goes straight to the base "
+                        "case), timed per kernel; the command of the base-case profile")
     p.add_argument("--instrumented", action="store_true",
                    help="run every sort from the host-driven wave loop (the same kernels, no "
                         "CUDA graph): the form the ncu captures in profiles/ use")
@@ -1129,6 +1133,45 @@ def run_batched_only(args):
     print(json.dumps({"batched_only": True, "segmented": seg}))
 
 
+def run_base_only(args, nseg=8192, seglen=16384):
+    """The base case alone: arrays of seglen keys (the size of a 2^30 sort's
+    last-level buckets) sorted by one ipsgpu_sort_batch; every step restores
+    the input, sorts with per-kernel timing and checks the result (each
+    array non-decreasing, the multiset unchanged) outside the timed part."""
+    import torch
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2009_13569_gb300 import inputs, ipsgpu
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    n = nseg * seglen
+    src = inputs.generate("uniform", "u64", n, seed=SEED, device=dev)
+    work = src.clone()
+    segs = torch.stack([torch.arange(nseg, dtype=torch.int64, device=dev) * (seglen * 8)
+                        + work.data_ptr(),
+                        torch.full((nseg,), seglen, dtype=torch.int64, device=dev)], 1).contiguous()
+    sig0 = _multiset_sig(torch, src)
+    ms, ok = [], True
+    with ipsgpu.Sorter("u64") as s:
+        s.set_timing(True)
+        for i in range(args.warmup + args.steps):
+            work.copy_(src)
+            torch.cuda.synchronize(dev)
+            s.kernel_stats()
+            s.sort_batch(segs.data_ptr(), nseg, st)
+            if s.status(st) != ipsgpu.OK:
+                raise SystemExit("base-only: sort failed")
+            k = s.kernel_stats().get("base_case", (0, 0.0, 0.0))
+            if i >= args.warmup:
+                ms.append(k[1])
+            u = work.view(nseg, seglen) ^ (-0x8000000000000000)
+            ok = ok and bool((u[:, 1:] >= u[:, :-1]).all()) and _multiset_sig(torch, work) == sig0
+    mean = sum(ms) / len(ms)
+    print(json.dumps({"base_only": True, "arrays": nseg, "keys_per_array": seglen,
+                      "base_case_ms": mean, "GBps": 2.0 * 8 * n / (mean * 1e-3) / 1e9,
+                      "steps": args.steps, "warmup": args.warmup, "result_sorted": ok}))
+
+
 def run_serve_only(args):
     import torch
     import __graft_entry__ as entry
@@ -1148,6 +1191,8 @@ def main():
         run_batched_only(args)
     elif args.serve_only:
         run_serve_only(args)
+    elif args.base_only:
+        run_base_only(args)
     else:
         run_ours(args)
 

@@ -194,6 +194,41 @@ __device__ __forceinline__ void sort_upto4(typename T::E *r, uint32_t c) {
         if ((uint32_t)i < c) r[i] = x[i];
 }
 
+// Sorts r[0..c), 5 <= c <= 8, in registers with Batcher's odd-even merge
+// network for 8 inputs (19 comparators); as above, a comparator touching
+// position c or above is skipped, which leaves a network for the first c.
+template <class T>
+__device__ __forceinline__ void sort_upto8(typename T::E *r, uint32_t c) {
+    typedef typename T::E E;
+    typedef typename T::K K;
+    E x[8];
+    K k[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        x[i] = r[(uint32_t)i < c ? i : 0];
+        k[i] = T::key(x[i]);
+    }
+    auto ce = [&](int i, int j) {
+        if ((uint32_t)j < c && k[j] < k[i]) {
+            const E tx = x[i];
+            x[i] = x[j];
+            x[j] = tx;
+            const K tk = k[i];
+            k[i] = k[j];
+            k[j] = tk;
+        }
+    };
+    ce(0, 1), ce(2, 3), ce(4, 5), ce(6, 7);
+    ce(0, 2), ce(1, 3), ce(4, 6), ce(5, 7);
+    ce(1, 2), ce(5, 6);
+    ce(0, 4), ce(1, 5), ce(2, 6), ce(3, 7);
+    ce(2, 4), ce(3, 5);
+    ce(1, 2), ce(3, 4), ce(5, 6);
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+        if ((uint32_t)i < c) r[i] = x[i];
+}
+
 // Sorts each listed segment (segs[4i] = device byte address, segs[4i+1] = n
 // <= smax, segs[4i+2..4i+3] = bounds lo <= hi of every element's radix key
 // T::rkey, or lo > hi when not known) in place; the number of segments is
@@ -208,7 +243,8 @@ __device__ __forceinline__ void sort_upto4(typename T::E *r, uint32_t c) {
 // range by digit from its global copy (which equals the shared one) into
 // shared memory; afterwards the cursor of digit d is the end of its
 // sub-bucket.  Sub-buckets of at most kBaseInsertion elements are finished
-// by insertion sort in shared memory, one thread per sub-bucket; those of at
+// in shared memory, one thread per sub-bucket (by a sorting network for up
+// to 4, or up to 8 elements of at most 16 bytes, else insertion sort); those of at
 // most kBaseSmall elements wait for one warp each once every larger range is
 // done (many of them hold equal keys only); larger ones get another pass
 // (with their own min/max).  Every pass writes its range back to global
@@ -538,8 +574,18 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
             if (kNetwork) {
                 __syncthreads();
                 const uint32_t nmid = min(sh_nmid, mid_cap);
-                for (uint32_t q = tid; q < nmid; q += kBaseThreads)
-                    insertion_sort<T>(buf + a0 + (mid[q] >> 16), mid[q] & 0xFFFFu);
+                for (uint32_t q = tid; q < nmid; q += kBaseThreads) {
+                    // up to 8 elements of at most 16 bytes: a network in
+                    // registers, whose lanes run in step; else insertion sort
+                    const uint32_t lo = mid[q] >> 16, c = mid[q] & 0xFFFFu;
+                    if constexpr (T::D <= 16) {
+                        if (c <= 8) {
+                            sort_upto8<T>(buf + a0 + lo, c);
+                            continue;
+                        }
+                    }
+                    insertion_sort<T>(buf + a0 + lo, c);
+                }
             }
             __syncthreads();
             // the range back to global memory, coalesced: final where the
