@@ -224,13 +224,13 @@ class ClockSampler:
 NCU_TRAFFIC = {
     "classify": {"bytes_per_elem": 15.16,
                  "source": "paper_2009_13569_gb300/csrc/classify.cuh",
-                 "sha256": "217f874a56bbf29af09547ba7213c038d224373a19cf2c3dc7a115bbb5be36ef"},
+                 "sha256": "987d25a05e74fffd3fc40b6044cc30d029428705bf53674636adc3b685abd0a7"},
     "permute": {"bytes_per_elem": 14.79,
                 "source": "paper_2009_13569_gb300/csrc/level.cuh",
-                "sha256": "1ff600e02d09ef4a2376787df01db9966d6ee2b1ee140d57684ae59b2c5fd67d"},
+                "sha256": "e0dfcfa463e31f64219e4668129a2e3a788106ba97e8e639e19837cc3ca7e880"},
     "base_case": {"bytes_per_elem": 15.11,
                   "source": "paper_2009_13569_gb300/csrc/base.cuh",
-                  "sha256": "c3e034fc3bf68f743fe8b4fdd4d89f712152ff2f1af49a634bb2185f108073e6"},
+                  "sha256": "5cccd74924ea3ca59a0efbb8052a834a145853c84f3d757a5967503e70fccf28"},
 }
 
 
