@@ -543,8 +543,12 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
             // the size, so the warp does not diverge on it); one of 5..24
             // elements goes to a list (the counter words this pass leaves
             // unused) that threads take one entry each afterwards, so that
-            // no warp waits for its lanes' longest insertion sort (when the
-            // list is full, or for records, insertion sort right away)
+            // no warp waits for its lanes' longest insertion sort; when the
+            // list is full (always for 4-byte keys, whose digits take every
+            // counter word), or for records, it is sorted right away: by the
+            // 8-input network up to 8 elements of at most 16 bytes (keys
+            // with many duplicates fill such sub-buckets), else by insertion
+            // sort
             uint32_t *mid = cur + nw;
             const uint32_t mid_cap = (uint32_t)(ND / 2) - nw;
             for (uint32_t d = tid; d < nd && !exact; d += kBaseThreads) {
@@ -564,11 +568,19 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
                 } else if (kNetwork && c <= 4) {
                     if (c > 1) sort_upto4<T>(buf + a0 + lo, c);
                 } else if (c > 1) {
-                    const uint32_t q = kNetwork ? atomicAdd(&sh_nmid, 1u) : mid_cap;
-                    if (q < mid_cap)
+                    const uint32_t q = kNetwork && mid_cap ? atomicAdd(&sh_nmid, 1u) : mid_cap;
+                    if (q < mid_cap) {
                         mid[q] = (lo << 16) | c;
-                    else
-                        insertion_sort<T>(buf + a0 + lo, c);
+                    } else {
+                        bool done = false;
+                        if constexpr (T::D <= 16) {
+                            if (c <= 8) {
+                                sort_upto8<T>(buf + a0 + lo, c);
+                                done = true;
+                            }
+                        }
+                        if (!done) insertion_sort<T>(buf + a0 + lo, c);
+                    }
                 }
             }
             if (kNetwork) {
