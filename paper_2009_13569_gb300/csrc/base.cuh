@@ -22,6 +22,7 @@ constexpr int kBaseInsertion = 24;       // sub-buckets up to this size: ranked 
 constexpr int kBaseStack = 256;          // pending large ranges: >= 188416 B / 4 B / 513
 constexpr int kBaseSmall = 512;          // ranges up to this size are finished by one warp
 constexpr int kBaseSmallStack = 2048;    // pending small ranges: >= 188416 B / 4 B / 25
+constexpr int kBasePeel = 4;             // distinct keys a small range is peeled by
 constexpr uint32_t kBaseSpin = 1u << 22;  // polls of a bounded wait on a segment's bulk copy
 
 
@@ -611,9 +612,12 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
             }
         }
         // the small ranges, one warp each: a range of equal keys is final;
-        // otherwise each element goes to its rank within the range (ties by
-        // position), straight to global memory.  Shared memory holds the
-        // range as the last pass grouped it, like its global copy.
+        // a range of at most kBasePeel distinct keys (duplicates) is peeled
+        // smallest key first, each key's elements to the next positions in
+        // their order; otherwise each element goes to its rank within the
+        // range (ties by position).  Either way straight to global memory.
+        // Shared memory holds the range as the last pass grouped it, like
+        // its global copy.
         const uint32_t nsmall = min(ssp, (uint32_t)S::SSTK);
         for (uint32_t r = warp; r < nsmall; r += NW) {
             const uint32_t top = sstk[r];
@@ -642,6 +646,33 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
                 all_equal = all_equal && mn[w] == mx[w];
             }
             if (all_equal) continue;  // all keys equal
+            uint32_t done = 0;  // elements placed (warp-uniform)
+            K last = T::max_key();
+            for (int it = 0; it < kBasePeel && done < c; it++) {
+                // the smallest key above the last one peeled
+                K v = T::max_key();
+                for (uint32_t p = lane; p < c; p += 32) {
+                    const K k = T::key(buf[a0 + p]);
+                    if ((it == 0 || last < k) && k < v) v = k;
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const K ov = shfl_key<T>(v, lane ^ o);
+                    if (ov < v) v = ov;
+                }
+                for (uint32_t p0 = 0; p0 < c; p0 += 32) {
+                    const uint32_t p = p0 + (uint32_t)lane;
+                    bool eq = false;
+                    if (p < c) {
+                        const K k = T::key(buf[a0 + p]);
+                        eq = !(k < v) && !(v < k);
+                    }
+                    const uint32_t m = __ballot_sync(0xffffffffu, eq);
+                    if (eq) g[a0 + done + __popc(m & ((1u << lane) - 1u))] = buf[a0 + p];
+                    done += __popc(m);
+                }
+                last = v;
+            }
+            if (done >= c) continue;  // every key peeled
             for (uint32_t p = lane; p < c; p += 32) {
                 const E x = buf[a0 + p];
                 const K kx = T::key(x);
