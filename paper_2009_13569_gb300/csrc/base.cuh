@@ -255,8 +255,8 @@ __device__ __forceinline__ void sort_upto8(typename T::E *r, uint32_t c) {
 // Two shapes share the code (BaseShape): one 1024-thread CTA per SM with
 // 184 KiB of elements, and two 512-thread CTAs per SM with 88 KiB each, which
 // take the segments that fit so that one CTA's loads and stores overlap the
-// other's counting and scattering.  A launch sorts the listed segments with
-// n_lo < n <= n_hi.
+// other's counting and scattering.  Each launch sorts the listed segments
+// of its shape (base_goes_large).
 template <int NT_, int BUF_, int MAXB_, int SSTK_>
 struct BaseShape {
     static constexpr int NT = NT_;          // threads of a CTA
@@ -267,6 +267,21 @@ struct BaseShape {
 };
 typedef BaseShape<1024, kBaseSmemBytes, kBaseDigitBits, kBaseSmallStack> BaseLarge;
 typedef BaseShape<512, 88 * 1024, kBaseDigitBits - 1, 1024> BaseSmall;
+
+// Whether a segment goes to the large shape: above the small shape's
+// capacity, and also a segment of 4-byte keys whose known key range holds
+// more than 2^13 and at most 2^14 values, when it is large enough for one
+// exact pass there (one digit per key value among the large shape's 2^14
+// digits; the small shape's 2^13 would put two values into each digit and
+// leave their duplicates to be finished apart).
+template <class T>
+__device__ __forceinline__ bool base_goes_large(uint64_t n, uint64_t rlo, uint64_t rhi,
+                                                uint64_t small_cap) {
+    if (n > small_cap) return true;
+    if (T::D > 4 || rlo > rhi || n <= (1ull << BaseSmall::MAXB)) return false;
+    const uint64_t r = rhi - rlo;
+    return r >= (1ull << BaseSmall::MAXB) && r < (1ull << BaseLarge::MAXB);
+}
 
 template <class T, class S>
 __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
@@ -340,17 +355,25 @@ __global__ void __launch_bounds__(S::NT, S::CTAS) k_base(const uint64_t *segs,
     auto dend = [&](uint32_t d) -> uint32_t { return (cur[word(d)] >> (16 * (d & 1))) & 0xFFFFu; };
 
     const uint32_t nsegs = nsegs_dev ? *nsegs_dev : nsegs_host;
+    // the small shape's launch takes n in (n_lo = 0, n_hi = its capacity],
+    // the large one's (n_lo = that capacity, n_hi = ~0), both refined by
+    // base_goes_large
+    constexpr bool kLarge = S::NT == BaseLarge::NT;
+    const uint64_t small_cap = kLarge ? n_lo : n_hi;
     for (uint32_t si = blockIdx.x; si < nsegs; si += gridDim.x) {
         const uint64_t addr = segs[4 * si], n = segs[4 * si + 1];
         const uint64_t rlo = segs[4 * si + 2], rhi = segs[4 * si + 3];
-        if (n <= n_lo || n > n_hi) continue;  // the other shape's segment
+        if (base_goes_large<T>(n, rlo, rhi, small_cap) != kLarge) continue;  // the other shape's
         E *g = reinterpret_cast<E *>(addr);
         E *buf = reinterpret_cast<E *>(smem + (addr & 15));
         if (tid == 0 && si + gridDim.x < nsegs) {
             // the CTA's next segment streams into L2 while this one is sorted
             const uint64_t na = segs[4 * (si + gridDim.x)], nn = segs[4 * (si + gridDim.x) + 1];
             const uint64_t lo = (na + 15) & ~15ull, hi = (na + nn * T::D) & ~15ull;
-            if (nn > n_lo && nn <= n_hi && hi > lo) prefetch_l2(lo, (uint32_t)(hi - lo));
+            if (base_goes_large<T>(nn, segs[4 * (si + gridDim.x) + 2], segs[4 * (si + gridDim.x) + 3],
+                                   small_cap) == kLarge &&
+                hi > lo)
+                prefetch_l2(lo, (uint32_t)(hi - lo));
         }
         if (n <= 1) continue;
         if (n <= 32) {
