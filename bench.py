@@ -224,7 +224,7 @@ class ClockSampler:
 NCU_TRAFFIC = {
     "classify": {"bytes_per_elem": 15.16,
                  "source": "paper_2009_13569_gb300/csrc/classify.cuh",
-                 "sha256": "987d25a05e74fffd3fc40b6044cc30d029428705bf53674636adc3b685abd0a7"},
+                 "sha256": "ed48567bb31a5be2e150d35747a43430c93d2bff2ee380beb86623724baeec42"},
     "permute": {"bytes_per_elem": 14.79,
                 "source": "paper_2009_13569_gb300/csrc/level.cuh",
                 "sha256": "e0dfcfa463e31f64219e4668129a2e3a788106ba97e8e639e19837cc3ca7e880"},

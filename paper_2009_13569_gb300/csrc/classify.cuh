@@ -2,8 +2,8 @@
 // al.), the first half of every partitioning level.
 //
 // One CTA owns one stripe (a run of whole blocks of its segment).  The stripe
-// is read tile by tile; the next tile streams into shared memory with
-// cp.async while the current one is processed:
+// is read tile by tile; the next tile streams into shared memory by one
+// bulk copy (cp.async.bulk, mbarrier) while the current one is processed:
 //   [B] every thread classifies its elements and takes its position g in
 //       its class's buffer block with a shared-memory atomic on a counter
 //       that starts the tile at the block's fill (one atomic per warp when
@@ -23,7 +23,7 @@
 // Classification counts the splitters below the key (the class of Sec. 2's
 // branchless tree) through a lookup table addressed by the key's leading
 // bits -- the table of start nodes Sec. 8 proposes, in its shortest exact
-// form: the splitter range is cut into 2^13 cells (2^12 for wider keys); a
+// form: the splitter range is cut into 2^12 cells; a
 // cell's entry holds ja, the number of splitters below every key of the
 // cell, and cnt, the number of splitters inside the cell's key range.  The
 // class index is ja plus the number of those cnt splitters below the key:
