@@ -314,7 +314,9 @@ int ipsgpu_debug_check_guards(ipsgpu_sorter *s, uint64_t *first_bad);
  *     at most batch_max_requests) into one ipsgpu_sort_batch run at high
  *     stream priority, preferably on the last lane, which takes nothing
  *     else; larger ones run alone (ipsgpu_sort) at low priority on any other
- *     free lane.  A request that cannot run yet does not hold back those
+ *     free lane, except a request holding at least half of hbm_budget_bytes,
+ *     which runs at high priority (requests waiting for admission wait for
+ *     its memory).  A request that cannot run yet does not hold back those
  *     behind it.
  *   - Each request's result is exactly what ipsgpu_sort gives for it alone
  *     (for PAIR_U64, REC100 and QUARTET: the same keys, records with equal

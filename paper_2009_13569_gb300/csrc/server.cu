@@ -20,7 +20,9 @@
 // on the last lane.  Each lane has a low-priority stream for large runs and
 // a high-priority one for batches, so the blocks of a batch are scheduled
 // ahead of a large sort's whenever SMs free up, and large sorts share the
-// GPU instead of queueing behind one another.  The queue is scanned past
+// GPU instead of queueing behind one another.  A run that holds at least
+// half the memory budget also takes the high-priority stream: requests
+// waiting for admission wait for its memory.  The queue is scanned past
 // requests that cannot run yet, so a large request waiting for a lane does
 // not hold back small ones, nor the reverse.  A host callback after each run
 // wakes the scheduler, which reads the run's status and marks its requests
@@ -196,7 +198,11 @@ bool choose(ipsgpu_server *s, Plan &plan) {
     plan.lane->dtype = plan.dtype;
     plan.lane->tickets = plan.tickets;
     const bool alone = plan.tickets.size() == 1 && plan.ns[0] > lim;
-    plan.lane->st = alone ? plan.lane->st_lo : plan.lane->st_hi;
+    // a run holding at least half the memory budget goes at high priority
+    // too: every request waiting for admission waits for its memory
+    const bool holds_half =
+        alone && 2 * plan.ns[0] * (uint64_t)elem_bytes(plan.dtype) >= s->cfg.hbm_budget_bytes;
+    plan.lane->st = alone && !holds_half ? plan.lane->st_lo : plan.lane->st_hi;
     return true;
 }
 
