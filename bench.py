@@ -225,9 +225,9 @@ NCU_TRAFFIC = {
     "classify": {"bytes_per_elem": 15.16,
                  "source": "paper_2009_13569_gb300/csrc/classify.cuh",
                  "sha256": "ed48567bb31a5be2e150d35747a43430c93d2bff2ee380beb86623724baeec42"},
-    "permute": {"bytes_per_elem": 14.79,
+    "permute": {"bytes_per_elem": 15.31,
                 "source": "paper_2009_13569_gb300/csrc/level.cuh",
-                "sha256": "e0dfcfa463e31f64219e4668129a2e3a788106ba97e8e639e19837cc3ca7e880"},
+                "sha256": "b5623d4103c1706c66f1c80072bf3a4a49dfa222ba120374bbe295643b21cd47"},
     "base_case": {"bytes_per_elem": 15.11,
                   "source": "paper_2009_13569_gb300/csrc/base.cuh",
                   "sha256": "5cccd74924ea3ca59a0efbb8052a834a145853c84f3d757a5967503e70fccf28"},

@@ -1,11 +1,12 @@
-"""ipsgpu_partition_level_noalloc against ipsgpu_partition_level.
+"""ipsgpu_partition_level_noalloc against ipsgpu_partition_level and the oracle.
 
 The no-alloc entry point serves callers that cannot allocate device memory
 (graph capture, allocator callbacks, services that reserve all memory up
 front): it keeps its scratch in a fixed device array of the library instead
 of a sorter's allocations.  Its result must equal the sorter-based level:
-identical bucket boundaries and, bucket by bucket, the same multiset of
-elements (the order inside a bucket is unspecified for both).  Two calls in
+identical bucket boundaries (also equal to the oracle's classification
+counts) and, bucket by bucket, the same multiset of elements (the order
+inside a bucket is unspecified for both).  Two calls in
 a row check that the shared array's leftovers from one call do not leak into
 the next; between them a sorter with fewer classes and smaller blocks is
 created (less classification shared memory than the fixed array's level
@@ -51,7 +52,12 @@ def test_noalloc_matches_sorter_level_twice(dtype, n, m, eq, dist):
         host = inputs.generate(dist, dtype, n, seed=100 + call)
         a = inputs.to_numpy(host, dtype)
         pick = a[np.random.default_rng(call).integers(0, n, size=m)]
-        spl = inputs.from_numpy(oracle.sort(pick, dtype), dtype).to(dev)
+        spl_np = oracle.sort(pick, dtype)
+        spl = inputs.from_numpy(spl_np, dtype).to(dev)
+        # the bucket boundaries the paper's classification gives (the oracle)
+        cls, B_or = oracle.classify(a, dtype, spl_np, eq)
+        assert B_or == B
+        bb_oracle = np.concatenate([[0], np.cumsum(np.bincount(cls, minlength=B))]).astype(np.uint64)
 
         ref = host.to(dev)
         bb_ref = torch.zeros(B + 1, dtype=torch.int64, device=dev)
@@ -70,6 +76,7 @@ def test_noalloc_matches_sorter_level_twice(dtype, n, m, eq, dist):
             # a sorter whose classification needs less shared memory
             small = ipsgpu.Sorter(dtype, k=64, block_bytes=512 if dtype == "rec100" else 256)
         np.testing.assert_array_equal(bbn, bb_ref.cpu().numpy().view(np.uint64))
+        np.testing.assert_array_equal(bbn, bb_oracle)
         g = inputs.to_numpy(got.cpu(), dtype)
         r = inputs.to_numpy(ref.cpu(), dtype)
         for j in range(B):
