@@ -215,6 +215,40 @@ def test_sort_radix_variant(dtype, dist):
     assert_sorted_parity(got, inputs.to_numpy(host, dtype), dtype)
 
 
+@pytest.mark.parametrize("algo", [ipsgpu.SAMPLESORT, ipsgpu.RADIX])
+@pytest.mark.parametrize("dist", ["uniform", "twodup", "eightdup"])
+def test_sort_u32_buckets_of_2e14_key_values(algo, dist):
+    # 2^22 keys below 2^22: the first level's children hold about 16,000 keys
+    # over 2^13..2^14 key values each, which the base case sorts in one exact
+    # pass in its large shape rather than in two-value digits in the small one
+    host = inputs.generate(dist, "u32", 1 << 22, seed=21) & ((1 << 22) - 1)
+    got = run_sort("u32", host, algo=algo)
+    assert_sorted_parity(got, inputs.to_numpy(host, "u32"), "u32")
+
+
+@pytest.mark.parametrize("pattern", ["pool", "clusters"])
+@pytest.mark.parametrize("dtype", ["u64", "pair"])
+def test_sort_duplicate_runs_in_small_ranges(pattern, dtype):
+    # keys repeated many times: "pool" draws 2^22 keys from 2^22 / 50 random
+    # 64-bit values, so a base-case digit often holds two or three values and
+    # tens of copies (a small range peeled key by key); "clusters" draws runs
+    # of 8 consecutive values, 8 copies each, so such ranges hold more
+    # distinct keys than are peeled and fall back to ranking
+    n = 1 << 22
+    rng = np.random.default_rng(5 if pattern == "pool" else 6)
+    if pattern == "pool":
+        keys = rng.integers(0, 2 ** 64, size=n // 50, dtype=np.uint64)[rng.integers(0, n // 50, size=n)]
+    else:
+        base = rng.integers(0, 2 ** 63, size=n // 64, dtype=np.uint64)
+        keys = base[rng.integers(0, n // 64, size=n)] + rng.integers(0, 8, size=n).astype(np.uint64)
+    if dtype == "pair":
+        a = np.stack([keys, np.arange(n, dtype=np.uint64)], axis=1)
+    else:
+        a = keys
+    got = run_sort(dtype, inputs.from_numpy(a, dtype))
+    assert_sorted_parity(got, a, dtype)
+
+
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 31, 32, 33, 63, 64, 65, 1000, 23551, 23552, 23553, 24577,
                                49_155, 2 ** 17, 2 ** 17 + 1])
 def test_sort_sizes(n):
