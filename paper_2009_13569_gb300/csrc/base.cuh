@@ -238,19 +238,21 @@ __device__ __forceinline__ void sort_upto8(typename T::E *r, uint32_t c) {
 //
 // The segment is staged into shared memory by one bulk copy; its radix key
 // range is the given bounds (a bucket's splitters, or its radix digit) or,
-// when none are known, the min/max of the staged keys.  A pass over a range [a0, a0+len)
-// then counts an MSD radix digit of (key - min) (up to 2^DBITS digits,
-// packed 16-bit counters), turns the counts into cursors, and scatters the
-// range by digit from its global copy (which equals the shared one) into
-// shared memory; afterwards the cursor of digit d is the end of its
-// sub-bucket.  Sub-buckets of at most kBaseInsertion elements are finished
-// in shared memory, one thread per sub-bucket (by a sorting network for up
-// to 4, or up to 8 elements of at most 16 bytes, else insertion sort); those of at
-// most kBaseSmall elements wait for one warp each once every larger range is
-// done (many of them hold equal keys only); larger ones get another pass
-// (with their own min/max).  Every pass writes its range back to global
-// memory (coalesced), so the global copy of a pending range always matches
-// the shared one.
+// when none are known, the min/max of the staged keys.  A pass over a range
+// [a0, a0+len) then counts an MSD radix digit of (key - min) (up to 2^DBITS
+// digits, packed 16-bit counters; the offset itself when the range has
+// that few values, else scaled to the digits), turns the counts into
+// cursors, and scatters the range by digit from its global copy (which
+// equals the shared one) into shared memory; afterwards the cursor of digit
+// d is the end of its sub-bucket.  Sub-buckets of at most kBaseInsertion
+// elements are finished in shared memory, one thread per sub-bucket (by a
+// sorting network for up to 4, or up to 8 elements of at most 16 bytes,
+// else insertion sort); those of at most kBaseSmall elements wait for one
+// warp each once every larger range is done (equal keys skipped, few
+// distinct keys peeled, others ranked); larger ones get another pass (with
+// their own min/max).  Every pass writes its range back to global memory
+// (coalesced), so the global copy of a pending range always matches the
+// shared one.
 //
 // Two shapes share the code (BaseShape): one 1024-thread CTA per SM with
 // 184 KiB of elements, and two 512-thread CTAs per SM with 88 KiB each, which
